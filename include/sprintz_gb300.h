@@ -1,0 +1,131 @@
+/*
+ * sprintz_gb300.h — C ABI of the GB300 (sm_103a) Sprintz codec.
+ *
+ * Sprintz (Blalock, Madden, Guttag, "Sprintz: Time Series Compression for the
+ * Internet of Things", IMWUT 2018) compresses a multivariate integer time
+ * series — T samples of D columns, every element a w-bit integer, stored
+ * row-major (Sec. 2.1, Definitions 2.1-2.3) — in blocks of B = 8 rows:
+ * forecast each sample (delta coding, Sec. 3.2.1, or the FIRE online
+ * forecaster, Sec. 3.2.2 / Algorithm 3), zigzag the errors, store each
+ * column's bit width in a header and bit-pack the errors (Sec. 3.3), replace
+ * runs of all-zero blocks by their count (Sec. 3.1, Algorithm 1), and
+ * optionally Huffman-code the packed bytes (Sec. 3.4).  Decoding inverts each
+ * step (Algorithm 2).
+ *
+ * Conventions for every entry point:
+ *   - Data pointers (src, dst, workspace, out_size) are DEVICE pointers
+ *     owned by the caller; the library never allocates on these calls and
+ *     never frees caller memory.
+ *   - Samples are little-endian, row-major, w in {8, 16} bits, 1 <= D <= 1024.
+ *     Their signedness does not matter: all arithmetic is modulo 2^w.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream).  Argument checks are synchronous and return a
+ *     negative SPRINTZ_ERR_* code before anything is enqueued.  Errors that
+ *     depend on the data (a corrupt stream, a wait that timed out) are
+ *     recorded in the context's device status word, read by
+ *     sprintz_get_status().
+ *   - The stream format is fixed: a 64-byte header, a 16-byte entry per chunk
+ *     of `chunk_rows` rows (the forecaster restarts at each chunk), the chunk
+ *     bodies (groups of `group_blocks` record headers, then their payloads),
+ *     then the rows % 8 trailing rows stored raw.  The same input and options
+ *     always give the same bytes.
+ */
+#ifndef SPRINTZ_GB300_H
+#define SPRINTZ_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPRINTZ_OK 0
+#define SPRINTZ_ERR_INVALID_ARG (-1)   /* a null pointer, bad D, bad option */
+#define SPRINTZ_ERR_UNSUPPORTED_W (-2) /* w is not 8 or 16 */
+#define SPRINTZ_ERR_DST_TOO_SMALL (-3) /* dst_cap below what the call may write */
+#define SPRINTZ_ERR_WS_TOO_SMALL (-4)  /* workspace below the *_workspace_size() */
+#define SPRINTZ_ERR_CORRUPT (-5)       /* a stream that is not a valid Sprintz stream */
+#define SPRINTZ_ERR_TIMEOUT (-6)       /* a bounded device wait gave up */
+#define SPRINTZ_ERR_CUDA (-7)          /* a CUDA runtime call failed */
+#define SPRINTZ_ERR_UNSUPPORTED (-8)   /* a valid option this build does not run */
+
+/* Codec options (the paper's knobs, Sec. 3.1 and 4.2: SprintzDelta,
+ * SprintzFIRE, SprintzFIRE+Huf). */
+typedef struct {
+  uint8_t forecaster;   /* 0 = delta coding (Sec. 3.2.1), 1 = FIRE (Sec. 3.2.2) */
+  uint8_t huffman;      /* 1 = Huffman-code the bit-packed bytes (Sec. 3.4) */
+  uint8_t group_blocks; /* G, 1..8: record headers stored together (Sec. 3.3); the paper uses 2 */
+  uint8_t learn_shift;  /* FIRE: alpha = accumulator >> learn_shift; 1 gives eta = 1/2 (Sec. 3.2.2) */
+  uint32_t chunk_rows;  /* rows per chunk, multiple of 8; the forecaster restarts at each chunk;
+                           0 = one chunk for the whole series (the paper's single stream) */
+  uint32_t huff_chunks; /* consecutive chunks sharing one Huffman table (huffman = 1), >= 1 */
+} sprintz_opts;
+
+/* Shape and options of a stream, as recorded in its 64-byte header. */
+typedef struct {
+  uint64_t rows;
+  uint32_t D;
+  uint32_t w;
+  sprintz_opts opts;
+  uint32_t n_chunks;
+  uint32_t tail_rows;
+  uint64_t data_off;    /* first chunk body */
+  uint64_t tail_off;    /* the raw trailing rows */
+  uint64_t total_bytes; /* stream size */
+} sprintz_info;
+
+typedef struct sprintz_ctx sprintz_ctx;
+
+/* Create a context on `device` (allocates its 4-byte device status word and
+ * queries the device).  Returns SPRINTZ_OK and sets *out, or an error. */
+int sprintz_ctx_create(sprintz_ctx **out, int device);
+void sprintz_ctx_destroy(sprintz_ctx *ctx);
+
+/* Largest stream sprintz_compress() can write for this shape and options:
+ * header + chunk table (+ Huffman tables) + for each chunk, one header group
+ * per G records and D*w bytes per block + the raw tail.  0 if the arguments
+ * are invalid. */
+uint64_t sprintz_max_compressed_size(uint64_t rows, uint32_t D, uint32_t w,
+                                     const sprintz_opts *opts);
+
+/* Device workspace bytes sprintz_compress() / sprintz_decompress() need for
+ * this shape and options (may be 0).  Workspace contents need not be
+ * initialised and are not preserved. */
+uint64_t sprintz_compress_workspace_size(uint64_t rows, uint32_t D, uint32_t w,
+                                         const sprintz_opts *opts);
+uint64_t sprintz_decompress_workspace_size(const sprintz_info *info);
+
+/* Compress `rows` x `D` samples at `src` (Algorithm 1 over every chunk).
+ * Writes the stream to dst (capacity dst_cap >= sprintz_max_compressed_size)
+ * and its size in bytes to the device uint64 *d_out_size.  The workspace must
+ * hold sprintz_compress_workspace_size() bytes.  src and dst must not
+ * overlap. */
+int sprintz_compress(sprintz_ctx *ctx, const void *src, uint64_t rows, uint32_t D, uint32_t w,
+                     const sprintz_opts *opts, void *dst, uint64_t dst_cap,
+                     uint64_t *d_out_size, void *workspace, uint64_t ws_bytes, void *stream);
+
+/* Decompress a stream of src_size bytes at src (Algorithm 2 over every
+ * chunk) into dst (rows x D samples, capacity dst_cap bytes).  `info` is the
+ * stream's header as parsed on the host by sprintz_query() (the caller keeps
+ * a host copy of the first 64 bytes; the host reads no device data here); the
+ * device checks it against the stream and flags SPRINTZ_ERR_CORRUPT on a
+ * mismatch. */
+int sprintz_decompress(sprintz_ctx *ctx, const void *src, uint64_t src_size,
+                       const sprintz_info *info, void *dst, uint64_t dst_cap, void *workspace,
+                       uint64_t ws_bytes, void *stream);
+
+/* Parse a HOST copy of a stream's first n >= 64 bytes. */
+int sprintz_query(const void *host_header, uint64_t n, sprintz_info *out);
+
+/* Wait for `stream`, return the first data-dependent error recorded since
+ * the last call (SPRINTZ_OK if none) and clear it. */
+int sprintz_get_status(sprintz_ctx *ctx, void *stream);
+
+/* Static description of an error code. */
+const char *sprintz_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

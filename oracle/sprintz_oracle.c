@@ -642,10 +642,19 @@ static uint64_t max_body_bytes(uint64_t n_blocks, uint32_t D, uint32_t w, uint32
   return (n_blocks + G - 1) / G * hdr + n_blocks * (uint64_t)D * w;
 }
 
+/* A chunk body's size is stored in 32 bits and the chunk count in 32 bits. */
+static int check_layout(const layout *L, uint32_t D, uint32_t w, uint32_t G) {
+  if (L->n_chunks > 0xFFFFFFFFull) return SPO_ERR_INVALID_ARG;
+  if (L->n_chunks && max_body_bytes(chunk_blocks(L, 0), D, w, G) > 0xFFFFFFFFull)
+    return SPO_ERR_INVALID_ARG;
+  return SPO_OK;
+}
+
 uint64_t spo_max_compressed_size(uint64_t rows, uint32_t D, uint32_t w, const spo_opts *o) {
   if (check_opts(D, w, o) != SPO_OK) return 0;
   layout L;
   make_layout(rows, o, &L);
+  if (check_layout(&L, D, w, (uint32_t)o->group_blocks) != SPO_OK) return 0;
   uint64_t total = L.data_off;
   for (uint64_t c = 0; c < L.n_chunks; ++c)
     total += max_body_bytes(chunk_blocks(&L, c), D, w, (uint32_t)o->group_blocks);
@@ -728,6 +737,8 @@ int64_t spo_compress(const void *src_v, uint64_t rows, uint32_t D, uint32_t w,
   if (rc != SPO_OK) return rc;
   layout L;
   make_layout(rows, o, &L);
+  rc = check_layout(&L, D, w, (uint32_t)o->group_blocks);
+  if (rc != SPO_OK) return rc;
   if (dst_cap < L.data_off) return SPO_ERR_DST_TOO_SMALL;
   memset(dst, 0, L.data_off);
 

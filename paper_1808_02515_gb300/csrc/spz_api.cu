@@ -1,0 +1,227 @@
+// C ABI of the CUDA Sprintz codec: argument checks, stream geometry, sizes,
+// header parsing and the device status word.  Every compute step runs in the
+// kernels of spz_encode.cu and spz_decode.cu; there is no CPU fallback.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include "spz_common.cuh"
+
+struct sprintz_ctx {
+  int device;
+  int *d_status;
+  int *h_status;  // pinned
+  spz::LaunchCfg cfg;
+};
+
+namespace spz {
+
+// Stream geometry from shape and options; the same rules the format states:
+// full_rows = rows - rows % 8, chunks of chunk_rows rows (0 = one chunk),
+// Huffman segments of huff_chunks chunks, and every chunk body must fit the
+// table's 32-bit size field.
+int make_geom(uint64_t rows, uint32_t D, uint32_t w, const sprintz_opts *o, Geom *g) {
+  if (!o) return SPRINTZ_ERR_INVALID_ARG;
+  if (w != 8 && w != 16) return SPRINTZ_ERR_UNSUPPORTED_W;
+  if (D < 1 || D > kMaxD) return SPRINTZ_ERR_INVALID_ARG;
+  if (o->forecaster > 1 || o->huffman > 1) return SPRINTZ_ERR_INVALID_ARG;
+  if (o->group_blocks < 1 || o->group_blocks > 8) return SPRINTZ_ERR_INVALID_ARG;
+  if (o->learn_shift > 2 * w - 1) return SPRINTZ_ERR_INVALID_ARG;
+  if (o->chunk_rows % kBlockRows) return SPRINTZ_ERR_INVALID_ARG;
+  if (o->huffman && o->huff_chunks < 1) return SPRINTZ_ERR_INVALID_ARG;
+  memset(g, 0, sizeof(*g));
+  g->rows = rows;
+  g->tail_rows = rows % kBlockRows;
+  g->full_rows = rows - g->tail_rows;
+  uint64_t n_chunks =
+      g->full_rows == 0 ? 0 : (o->chunk_rows == 0 ? 1 : (g->full_rows + o->chunk_rows - 1) / o->chunk_rows);
+  if (n_chunks > 0xFFFFFFFFull) return SPRINTZ_ERR_INVALID_ARG;
+  g->n_chunks = (uint32_t)n_chunks;
+  g->chunk_rows = o->chunk_rows ? o->chunk_rows : (g->full_rows ? g->full_rows : kBlockRows);
+  g->chunk_rows_opt = o->chunk_rows;
+  g->D = D;
+  g->w = w;
+  g->wb = w / 8;
+  g->G = o->group_blocks;
+  g->hb = w == 8 ? 3 : 4;
+  g->hdr_bytes = (g->G * D * g->hb + 7) / 8;
+  g->col_major = D * w <= 32;
+  g->forecaster = o->forecaster;
+  g->learn_shift = o->learn_shift;
+  g->huffman = o->huffman;
+  g->huff_chunks = o->huffman ? o->huff_chunks : 0;
+  g->n_segments = o->huffman ? (uint32_t)((n_chunks + o->huff_chunks - 1) / o->huff_chunks) : 0;
+  g->data_off = kHdrBytes + (uint64_t)kEntryBytes * n_chunks + (uint64_t)kHuffTableBytes * g->n_segments;
+  uint64_t max_rows = g->full_rows < g->chunk_rows ? g->full_rows : g->chunk_rows;
+  g->max_blocks = (uint32_t)(max_rows / kBlockRows);
+  g->max_body = max_body_bytes(g->max_blocks, D, w, g->G);
+  if (g->max_body > 0xFFFFFFFFull) return SPRINTZ_ERR_INVALID_ARG;
+  return SPRINTZ_OK;
+}
+
+}  // namespace spz
+
+using spz::Geom;
+
+static uint64_t le(const uint8_t *p, int n) {
+  uint64_t v = 0;
+  for (int k = 0; k < n; ++k) v |= (uint64_t)p[k] << (8 * k);
+  return v;
+}
+
+extern "C" {
+
+int sprintz_ctx_create(sprintz_ctx **out, int device) {
+  if (!out) return SPRINTZ_ERR_INVALID_ARG;
+  *out = nullptr;
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  sprintz_ctx *c = new sprintz_ctx();
+  c->device = device;
+  int rc = SPRINTZ_OK;
+  if (cudaDeviceGetAttribute(&c->cfg.sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->cfg.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) !=
+          cudaSuccess ||
+      cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&c->h_status, sizeof(int)) != cudaSuccess)
+    rc = SPRINTZ_ERR_CUDA;
+  cudaSetDevice(prev);
+  if (rc != SPRINTZ_OK) {
+    sprintz_ctx_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return SPRINTZ_OK;
+}
+
+void sprintz_ctx_destroy(sprintz_ctx *c) {
+  if (!c) return;
+  if (c->d_status) cudaFree(c->d_status);
+  if (c->h_status) cudaFreeHost(c->h_status);
+  delete c;
+}
+
+uint64_t sprintz_max_compressed_size(uint64_t rows, uint32_t D, uint32_t w, const sprintz_opts *o) {
+  Geom g;
+  if (spz::make_geom(rows, D, w, o, &g) != SPRINTZ_OK) return 0;
+  uint64_t total = g.data_off;
+  if (g.n_chunks) {
+    uint64_t full = g.full_rows / g.chunk_rows;  // chunks with chunk_rows rows
+    uint64_t last_rows = g.full_rows - full * g.chunk_rows;
+    total += full * spz::max_body_bytes(g.chunk_rows / 8, D, w, g.G);
+    if (last_rows) total += spz::max_body_bytes(last_rows / 8, D, w, g.G);
+  }
+  return total + g.tail_rows * D * g.wb;
+}
+
+static spz::LaunchCfg default_cfg() {
+  spz::LaunchCfg cfg{152, 232448};
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    cudaDeviceGetAttribute(&cfg.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&cfg.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  return cfg;
+}
+
+uint64_t sprintz_compress_workspace_size(uint64_t rows, uint32_t D, uint32_t w, const sprintz_opts *o) {
+  Geom g;
+  if (spz::make_geom(rows, D, w, o, &g) != SPRINTZ_OK) return 0;
+  return spz::encode_workspace_bytes(g, default_cfg());
+}
+
+uint64_t sprintz_decompress_workspace_size(const sprintz_info *info) {
+  if (!info) return 0;
+  Geom g;
+  if (spz::make_geom(info->rows, info->D, info->w, &info->opts, &g) != SPRINTZ_OK) return 0;
+  return spz::decode_workspace_bytes(g, default_cfg());
+}
+
+int sprintz_compress(sprintz_ctx *ctx, const void *src, uint64_t rows, uint32_t D, uint32_t w,
+                     const sprintz_opts *opts, void *dst, uint64_t dst_cap, uint64_t *d_out_size,
+                     void *workspace, uint64_t ws_bytes, void *stream) {
+  if (!ctx || !dst || !d_out_size || (rows && !src)) return SPRINTZ_ERR_INVALID_ARG;
+  Geom g;
+  int rc = spz::make_geom(rows, D, w, opts, &g);
+  if (rc != SPRINTZ_OK) return rc;
+  if (opts->huffman) return SPRINTZ_ERR_UNSUPPORTED;
+  if (dst_cap < sprintz_max_compressed_size(rows, D, w, opts)) return SPRINTZ_ERR_DST_TOO_SMALL;
+  if (ws_bytes < spz::encode_workspace_bytes(g, ctx->cfg)) return SPRINTZ_ERR_WS_TOO_SMALL;
+  if (!workspace && ws_bytes) return SPRINTZ_ERR_INVALID_ARG;
+  return spz::launch_encode(g, ctx->cfg, (const uint8_t *)src, (uint8_t *)dst, dst_cap, d_out_size,
+                            (uint8_t *)workspace, ws_bytes, ctx->d_status, (cudaStream_t)stream);
+}
+
+int sprintz_query(const void *host_header, uint64_t n, sprintz_info *out) {
+  if (!host_header || !out) return SPRINTZ_ERR_INVALID_ARG;
+  const uint8_t *h = (const uint8_t *)host_header;
+  if (n < spz::kHdrBytes) return SPRINTZ_ERR_CORRUPT;
+  if (h[0] != 'S' || h[1] != 'P' || h[2] != 'Z' || h[3] != '1' || h[4] != 1) return SPRINTZ_ERR_CORRUPT;
+  if (h[7] & ~1u) return SPRINTZ_ERR_CORRUPT;
+  memset(out, 0, sizeof(*out));
+  out->w = h[5];
+  out->opts.forecaster = h[6];
+  out->opts.huffman = h[7] & 1;
+  out->D = (uint32_t)le(h + 8, 2);
+  out->opts.group_blocks = h[10];
+  out->opts.learn_shift = h[11];
+  out->opts.chunk_rows = (uint32_t)le(h + 12, 4);
+  out->opts.huff_chunks = (uint32_t)le(h + 16, 4);
+  out->n_chunks = (uint32_t)le(h + 20, 4);
+  out->rows = le(h + 24, 8);
+  out->tail_rows = (uint32_t)le(h + 32, 4);
+  out->data_off = le(h + 40, 8);
+  out->tail_off = le(h + 48, 8);
+  out->total_bytes = le(h + 56, 8);
+  Geom g;
+  if (spz::make_geom(out->rows, out->D, out->w, &out->opts, &g) != SPRINTZ_OK) return SPRINTZ_ERR_CORRUPT;
+  if (g.n_chunks != out->n_chunks || g.tail_rows != out->tail_rows || g.data_off != out->data_off ||
+      le(h + 36, 4) != 0 || out->tail_off < out->data_off)
+    return SPRINTZ_ERR_CORRUPT;
+  return SPRINTZ_OK;
+}
+
+int sprintz_decompress(sprintz_ctx *ctx, const void *src, uint64_t src_size, const sprintz_info *info,
+                       void *dst, uint64_t dst_cap, void *workspace, uint64_t ws_bytes, void *stream) {
+  if (!ctx || !src || !info) return SPRINTZ_ERR_INVALID_ARG;
+  Geom g;
+  if (spz::make_geom(info->rows, info->D, info->w, &info->opts, &g) != SPRINTZ_OK)
+    return SPRINTZ_ERR_INVALID_ARG;
+  if (g.n_chunks != info->n_chunks || g.data_off != info->data_off) return SPRINTZ_ERR_INVALID_ARG;
+  if (info->opts.huffman) return SPRINTZ_ERR_UNSUPPORTED;
+  if (src_size < g.data_off) return SPRINTZ_ERR_CORRUPT;
+  uint64_t need = info->rows * info->D * g.wb;
+  if (need && !dst) return SPRINTZ_ERR_INVALID_ARG;
+  if (dst_cap < need) return SPRINTZ_ERR_DST_TOO_SMALL;
+  if (ws_bytes < spz::decode_workspace_bytes(g, ctx->cfg)) return SPRINTZ_ERR_WS_TOO_SMALL;
+  return spz::launch_decode(g, ctx->cfg, (const uint8_t *)src, src_size, (uint8_t *)dst, dst_cap,
+                            (uint8_t *)workspace, ws_bytes, ctx->d_status, (cudaStream_t)stream);
+}
+
+int sprintz_get_status(sprintz_ctx *ctx, void *stream) {
+  if (!ctx) return SPRINTZ_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return SPRINTZ_ERR_CUDA;
+  if (cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  return *ctx->h_status;
+}
+
+const char *sprintz_strerror(int code) {
+  switch (code) {
+    case SPRINTZ_OK: return "ok";
+    case SPRINTZ_ERR_INVALID_ARG: return "invalid argument";
+    case SPRINTZ_ERR_UNSUPPORTED_W: return "bit width must be 8 or 16";
+    case SPRINTZ_ERR_DST_TOO_SMALL: return "destination buffer too small";
+    case SPRINTZ_ERR_WS_TOO_SMALL: return "workspace too small";
+    case SPRINTZ_ERR_CORRUPT: return "corrupt stream";
+    case SPRINTZ_ERR_TIMEOUT: return "a bounded device wait timed out";
+    case SPRINTZ_ERR_CUDA: return "CUDA runtime error";
+    case SPRINTZ_ERR_UNSUPPORTED: return "option not supported by this build";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// Shared definitions of the CUDA Sprintz codec (sm_103a).
+//
+// Stream format (identical bytes for every implementation of it):
+//   [0, 64)         header: "SPZ1", version 1, w, forecaster, flags (bit 0 =
+//                   Huffman), D (u16), G, learn_shift, chunk_rows (u32),
+//                   huff_chunks (u32), n_chunks (u32), rows (u64), tail_rows
+//                   (u32), reserved (u32), data_off, tail_off, total (u64)
+//   [64, +16/chunk) chunk table: u64 body offset from data_off, u32 record
+//                   count, u32 packed bytes
+//   Huffman tables  128 bytes per segment of huff_chunks chunks (flag set)
+//   data_off        chunk bodies; each body is groups of G records: the G
+//                   records' width codes (log2(w) bits each, record s column j
+//                   at bit (s*D + j)*log2(w), LSB first, zero padded to a byte),
+//                   then the records' payloads
+//   tail_off        rows % 8 trailing rows, raw
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sprintz_gb300.h"
+
+namespace spz {
+
+constexpr int kBlockRows = 8;          // B (Sec. 3.1)
+constexpr uint32_t kHdrBytes = 64;
+constexpr uint32_t kEntryBytes = 16;
+constexpr uint32_t kHuffTableBytes = 128;
+constexpr uint32_t kMaxRun = 65535;    // run counts are 16-bit
+constexpr uint32_t kMaxD = 1024;
+constexpr int kFcDelta = 0;
+constexpr int kFcFire = 1;
+
+// Everything about a stream's layout that the host knows before launch.
+struct Geom {
+  uint64_t rows;
+  uint64_t full_rows;      // rows - rows % 8
+  uint64_t chunk_rows;     // rows per chunk (the last may be shorter)
+  uint32_t chunk_rows_opt; // the option as given (0 = one chunk)
+  uint64_t data_off;
+  uint64_t tail_rows;
+  uint32_t n_chunks;
+  uint32_t D;
+  uint32_t w;
+  uint32_t wb;             // bytes per element
+  uint32_t G;
+  uint32_t hb;             // header bits per code: log2(w)
+  uint32_t hdr_bytes;      // ceil(G*D*hb/8)
+  uint32_t col_major;      // D*w <= 32
+  uint32_t forecaster;
+  uint32_t learn_shift;
+  uint32_t huffman;
+  uint32_t huff_chunks;
+  uint32_t n_segments;
+  uint32_t max_blocks;     // blocks in the largest chunk
+  uint64_t max_body;       // largest possible body of one chunk
+};
+
+__host__ __device__ inline uint64_t max_body_bytes(uint64_t n_blocks, uint32_t D, uint32_t w,
+                                                   uint32_t G) {
+  uint64_t hdr = ((uint64_t)G * D * (w == 8 ? 3u : 4u) + 7) / 8;
+  return (n_blocks + G - 1) / G * hdr + n_blocks * (uint64_t)D * w;
+}
+
+// Bytes of a chunk's rows as stored in the uncompressed series.
+__host__ __device__ inline uint64_t chunk_raw_bytes(const Geom &g, uint64_t rows) {
+  return rows * g.D * g.wb;
+}
+
+__device__ __forceinline__ void set_status(int *status, int code) {
+  atomicCAS(status, 0, code);
+}
+
+// Width code <-> stored width (a width of w-1 is promoted to w; code w-1
+// means w).
+__device__ __forceinline__ uint32_t code_to_width(uint32_t c, uint32_t w) {
+  return c == w - 1 ? w : c;
+}
+__device__ __forceinline__ uint32_t width_to_code(uint32_t n, uint32_t w) {
+  return n == w ? w - 1 : n;
+}
+
+// Sign-extend the low W bits.
+template <int W>
+__device__ __forceinline__ int32_t sext(uint32_t v) {
+  return (int32_t)(v << (32 - W)) >> (32 - W);
+}
+
+__device__ __forceinline__ int32_t sign_of(int32_t v) { return (v > 0) - (v < 0); }
+
+// Zigzag of a signed W-bit value (Sec. 3.3) as an unsigned W-bit value.
+template <int W>
+__device__ __forceinline__ uint32_t zigzag(int32_t e) {
+  return ((uint32_t)e << 1 ^ (uint32_t)(e >> 31)) & ((1u << W) - 1u);
+}
+template <int W>
+__device__ __forceinline__ int32_t unzigzag(uint32_t z) {
+  return (int32_t)(z >> 1) ^ -(int32_t)(z & 1u);
+}
+
+// Bits needed for v (0 for 0).
+__device__ __forceinline__ uint32_t bit_len(uint32_t v) { return 32u - __clz(v); }
+
+// Little-endian loads/stores of one w-bit sample from byte memory.
+template <int W>
+__device__ __forceinline__ uint32_t load_sample(const uint8_t *p) {
+  if (W == 8) return p[0];
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8);
+}
+template <int W>
+__device__ __forceinline__ void store_sample(uint8_t *p, uint32_t v) {
+  p[0] = (uint8_t)v;
+  if (W == 16) p[1] = (uint8_t)(v >> 8);
+}
+
+// Read `n` (<= 25) bits starting at bit position `bit` of a byte array.
+__device__ __forceinline__ uint32_t read_bits(const uint8_t *base, uint64_t bit, uint32_t n) {
+  const uint8_t *p = base + (bit >> 3);
+  uint32_t s = (uint32_t)(bit & 7);
+  uint32_t need = (s + n + 7) >> 3;  // 0..4 bytes
+  uint32_t v = 0;
+  for (uint32_t k = 0; k < need; ++k) v |= (uint32_t)p[k] << (8 * k);
+  return n ? (v >> s) & (0xFFFFFFFFu >> (32 - n)) : 0u;
+}
+
+// FIRE fixed-point step shared by encoder and decoder: floor(wrap_2w(alpha *
+// delta) / 2^w) modulo 2^w, returned unreduced in its low w bits.
+template <int W>
+__device__ __forceinline__ uint32_t fire_pred_delta(int32_t alpha, int32_t delta) {
+  return (uint32_t)((uint32_t)alpha * (uint32_t)delta) >> W;
+}
+
+// The accumulator is a signed 2w-bit integer (wraps at 2w bits).
+template <int W>
+__device__ __forceinline__ int32_t wrap_acc(int32_t v) {
+  if (W == 16) return v;
+  return (int32_t)(int16_t)v;
+}
+
+// Relaxed/acquire 64-bit global accesses for the encoder's offset scan.
+__device__ __forceinline__ void st_release_u64(uint64_t *p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Host helpers --------------------------------------------------------------
+
+struct LaunchCfg {
+  int sm_count;
+  int max_smem_optin;
+};
+
+int make_geom(uint64_t rows, uint32_t D, uint32_t w, const sprintz_opts *o, Geom *g);
+
+// Encoder / decoder launchers (spz_encode.cu, spz_decode.cu).
+uint64_t encode_workspace_bytes(const Geom &g, const LaunchCfg &cfg);
+int launch_encode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint8_t *dst,
+                  uint64_t dst_cap, uint64_t *d_out_size, uint8_t *ws, uint64_t ws_bytes,
+                  int *d_status, cudaStream_t stream);
+uint64_t decode_workspace_bytes(const Geom &g, const LaunchCfg &cfg);
+int launch_decode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint64_t src_size,
+                  uint8_t *dst, uint64_t dst_cap, uint8_t *ws, uint64_t ws_bytes, int *d_status,
+                  cudaStream_t stream);
+
+}  // namespace spz

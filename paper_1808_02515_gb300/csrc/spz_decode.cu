@@ -1,0 +1,467 @@
+// Sprintz decoder on sm_103a.
+//
+// Chunks are independent (the forecaster restarts at each one), and the
+// chunk table gives every body's offset, so one CTA decodes one chunk with no
+// inter-CTA communication.  Per chunk:
+//   1. the chunk's body is staged in shared memory;
+//   2. one thread walks the groups of record headers (the only serial part:
+//      each group's position depends on the sizes of the records before it)
+//      and lays out every record's first block, run length and payload
+//      offset, validating every count and offset against the body;
+//   3. all threads unpack the payloads in parallel — column-major items are
+//      (record, column), row-major items are (record, row) — and un-zigzag
+//      them into a shared tile of errors (runs leave zeros);
+//   4. the forecast is inverted in place: delta as a per-column wrap-around
+//      prefix sum split across threads; FIRE as one serial recurrence per
+//      column (Algorithm 2 with Algorithm 3's predict/train, alpha fixed per
+//      block, one averaged update per block — Sec. 3.2.2);
+//   5. the tile is stored with 128-bit stores.
+// CTA 0 also checks the stream header against the host's view of it and
+// copies the raw trailing rows.  Chunks too large for shared memory use a
+// per-CTA global scratch slot for the record arrays and work directly in the
+// source and destination.
+#include <algorithm>
+
+#include "spz_common.cuh"
+
+namespace spz {
+
+constexpr int kDecThreads = 256;
+
+struct DecLayout {
+  uint64_t body, x, rec_first, rec_run, rec_off, grp_off, part, total;
+};
+
+__host__ __device__ inline DecLayout dec_layout(const Geom &g, bool staged) {
+  DecLayout L;
+  uint64_t o = 0;
+  uint64_t nb = g.max_blocks;
+  auto take = [&](uint64_t bytes) {
+    uint64_t r = o;
+    o += (bytes + 15) & ~15ull;
+    return r;
+  };
+  L.body = staged ? take(g.max_body + 32) : 0;
+  L.x = staged ? take(nb * kBlockRows * g.D * g.wb) : 0;
+  L.rec_first = take(nb * 4);
+  L.rec_run = take(nb * 4);
+  L.rec_off = take(nb * 4);
+  L.grp_off = take(nb * 4);
+  L.part = take((uint64_t)kDecThreads * 4);
+  L.total = o;
+  return L;
+}
+
+struct DecParams {
+  const uint8_t *src;
+  uint64_t src_size;
+  uint8_t *dst;
+  uint64_t dst_cap;
+  int *status;
+  uint8_t *scratch;
+  uint64_t scratch_per_cta;
+  uint32_t staged;
+  Geom g;
+};
+
+__device__ __forceinline__ uint64_t le_u64(const uint8_t *p) {
+  uint64_t v = 0;
+  for (int k = 0; k < 8; ++k) v |= (uint64_t)p[k] << (8 * k);
+  return v;
+}
+__device__ __forceinline__ uint32_t le_u32(const uint8_t *p) {
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+
+// Copy n bytes with the whole CTA (16-byte vectors when both ends allow).
+__device__ void cta_copy_dec(uint8_t *dst, const uint8_t *src, uint64_t n) {
+  uint64_t head = (16 - ((uintptr_t)dst & 15)) & 15;
+  if (head > n) head = n;
+  bool vec = (((uintptr_t)src + head) & 15) == 0;
+  if (!vec) {
+    for (uint64_t k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+    return;
+  }
+  for (uint64_t k = threadIdx.x; k < head; k += blockDim.x) dst[k] = src[k];
+  uint64_t n16 = (n - head) / 16;
+  const uint4 *s4 = reinterpret_cast<const uint4 *>(src + head);
+  uint4 *d4 = reinterpret_cast<uint4 *>(dst + head);
+  for (uint64_t k = threadIdx.x; k < n16; k += blockDim.x) d4[k] = s4[k];
+  for (uint64_t k = head + n16 * 16 + threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+}
+
+// Copy n bytes from a source of any alignment into a 16-byte-aligned
+// destination, 16-byte loads of the aligned source span.
+__device__ void cta_copy_from_unaligned(uint8_t *dst, const uint8_t *src, uint64_t n) {
+  const uint32_t mis = (uint32_t)((uintptr_t)src & 15);
+  if (mis == 0) {
+    cta_copy_dec(dst, src, n);
+    return;
+  }
+  // dst[k] = src[k] for k < n, via aligned 16-byte source words: source word
+  // t covers src[16t - mis, 16t - mis + 16).
+  const uint8_t *a = src - mis;
+  uint64_t nw = (n + mis + 15) / 16;
+  for (uint64_t t = threadIdx.x; t < nw; t += blockDim.x) {
+    uint64_t lo = t * 16;  // offset from a
+    if (t == 0 || t == nw - 1) {
+      for (uint32_t k = 0; k < 16; ++k) {
+        uint64_t o = lo + k;
+        if (o >= mis && o - mis < n) dst[o - mis] = a[o];
+      }
+      continue;
+    }
+    uint4 v = *reinterpret_cast<const uint4 *>(a + lo);
+    uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 16; ++k) dst[lo + k - mis] = (uint8_t)(w[k >> 2] >> (8 * (k & 3)));
+  }
+}
+
+template <int W>
+__device__ __forceinline__ uint32_t tile_get(const uint8_t *X, uint32_t D, uint64_t r, uint32_t j) {
+  return load_sample<W>(X + ((uint64_t)r * D + j) * (W / 8));
+}
+template <int W>
+__device__ __forceinline__ void tile_put(uint8_t *X, uint32_t D, uint64_t r, uint32_t j, uint32_t v) {
+  store_sample<W>(X + ((uint64_t)r * D + j) * (W / 8), v);
+}
+
+__device__ __forceinline__ uint32_t header_code(const uint8_t *hdr, uint32_t idx, uint32_t hb) {
+  return read_bits(hdr, (uint64_t)idx * hb, hb);
+}
+
+template <int W>
+__device__ void decode_chunk(const DecParams &p, uint8_t *mem, uint32_t c, uint64_t data_bytes) {
+  const Geom &g = p.g;
+  const uint32_t D = g.D;
+  const uint32_t wb = W / 8;
+  const DecLayout L = dec_layout(g, p.staged != 0);
+  __shared__ uint32_t s_bad;
+  __shared__ uint32_t s_nrec;
+
+  const uint64_t row0 = (uint64_t)c * g.chunk_rows;
+  const uint64_t rows_c = min(g.chunk_rows, g.full_rows - row0);
+  const uint32_t nb = (uint32_t)(rows_c / kBlockRows);
+  uint8_t *dst_c = p.dst + row0 * D * wb;
+  const uint64_t bytes_c = rows_c * D * wb;
+
+  uint32_t *rec_first = reinterpret_cast<uint32_t *>(mem + L.rec_first);
+  uint32_t *rec_run = reinterpret_cast<uint32_t *>(mem + L.rec_run);
+  uint32_t *rec_off = reinterpret_cast<uint32_t *>(mem + L.rec_off);
+  uint32_t *grp_off = reinterpret_cast<uint32_t *>(mem + L.grp_off);
+  uint32_t *part = reinterpret_cast<uint32_t *>(mem + L.part);
+  __syncthreads();  // the previous chunk's readers of s_bad / s_nrec are done
+
+  // Chunk entry: body offset, record count, packed bytes; the body ends where
+  // the next one starts (or at the tail).
+  const uint8_t *e = p.src + kHdrBytes + (uint64_t)c * kEntryBytes;
+  const uint64_t off = le_u64(e);
+  const uint32_t nrec = le_u32(e + 8);
+  const uint32_t packed = le_u32(e + 12);
+  const uint64_t end = c + 1 < g.n_chunks ? le_u64(e + kEntryBytes) : data_bytes;
+  if (threadIdx.x == 0) {
+    bool bad = off > end || end > data_bytes || end - off != packed || nrec < 1 || nrec > nb ||
+               packed > g.max_body;
+    s_bad = bad;
+    if (bad) set_status(p.status, SPRINTZ_ERR_CORRUPT);
+  }
+  __syncthreads();
+  if (s_bad) return;
+
+  // 1. body
+  const uint8_t *src_body = p.src + g.data_off + off;
+  const uint8_t *body = src_body;
+  if (p.staged) {
+    cta_copy_from_unaligned(mem + L.body, src_body, packed);
+    body = mem + L.body;
+  }
+  uint8_t *X = p.staged ? mem + L.x : dst_c;
+  // errors start at zero (run blocks keep them)
+  if (p.staged) {
+    uint4 z = make_uint4(0, 0, 0, 0);
+    for (uint64_t k = threadIdx.x; k < (bytes_c + 15) / 16; k += blockDim.x)
+      reinterpret_cast<uint4 *>(X)[k] = z;
+  } else {
+    for (uint64_t k = threadIdx.x; k < bytes_c; k += blockDim.x) X[k] = 0;
+  }
+  __syncthreads();
+
+  // 2. walk the header groups
+  if (threadIdx.x == 0) {
+    uint64_t pos = 0;
+    uint32_t blk = 0;
+    bool bad = false;
+    const uint32_t ngroups = (nrec + g.G - 1) / g.G;
+    for (uint32_t q = 0; q < ngroups && !bad; ++q) {
+      const uint64_t h = pos;
+      grp_off[q] = (uint32_t)h;
+      pos += g.hdr_bytes;
+      if (pos > packed) {
+        bad = true;
+        break;
+      }
+      const uint8_t *hdr = body + h;
+      for (uint32_t s = 0; s < g.G; ++s) {
+        const uint32_t r = q * g.G + s;
+        uint32_t sum = 0, any = 0;
+        for (uint32_t j = 0; j < D; ++j) {
+          uint32_t code = header_code(hdr, s * D + j, g.hb);
+          any |= code;
+          sum += code_to_width(code, W);
+        }
+        if (r >= nrec) {
+          if (any) bad = true;  // unused slots hold zero codes
+          continue;
+        }
+        rec_first[r] = blk;
+        rec_off[r] = (uint32_t)pos;
+        if (!any) {
+          if (pos + 2 > packed) {
+            bad = true;
+            break;
+          }
+          uint32_t cnt = (uint32_t)body[pos] | ((uint32_t)body[pos + 1] << 8);
+          pos += 2;
+          if (cnt == 0 || blk + cnt > nb) {
+            bad = true;
+            break;
+          }
+          rec_run[r] = cnt;
+          blk += cnt;
+        } else {
+          pos += g.col_major ? sum : 8 * ((sum + 7) / 8);
+          if (pos > packed || blk + 1 > nb) {
+            bad = true;
+            break;
+          }
+          rec_run[r] = 0;
+          blk += 1;
+        }
+      }
+    }
+    if (blk != nb || pos != packed) bad = true;
+    s_bad = bad;
+    s_nrec = nrec;
+    if (bad) set_status(p.status, SPRINTZ_ERR_CORRUPT);
+  }
+  __syncthreads();
+  if (s_bad) return;
+
+  // 3. unpack + un-zigzag into the tile
+  const uint32_t per = g.col_major ? D : kBlockRows;
+  for (uint64_t q = threadIdx.x; q < (uint64_t)nrec * per; q += blockDim.x) {
+    const uint32_t r = (uint32_t)(q / per), k = (uint32_t)(q % per);
+    if (rec_run[r]) continue;
+    const uint32_t b = rec_first[r];
+    const uint8_t *hdr = body + grp_off[r / g.G];
+    const uint32_t s = r % g.G;
+    if (g.col_major) {
+      uint32_t offb = 0;
+      for (uint32_t j = 0; j < k; ++j) offb += code_to_width(header_code(hdr, s * D + j, g.hb), W);
+      const uint32_t n = code_to_width(header_code(hdr, s * D + k, g.hb), W);
+      if (!n) continue;
+      const uint64_t bit0 = ((uint64_t)rec_off[r] + offb) * 8;
+#pragma unroll
+      for (int i = 0; i < kBlockRows; ++i) {
+        uint32_t z = read_bits(body, bit0 + (uint64_t)i * n, n);
+        tile_put<W>(X, D, (uint64_t)b * kBlockRows + i, k, (uint32_t)unzigzag<W>(z));
+      }
+    } else {
+      uint32_t sum = 0;
+      for (uint32_t j = 0; j < D; ++j) sum += code_to_width(header_code(hdr, s * D + j, g.hb), W);
+      const uint32_t R = (sum + 7) / 8;
+      uint64_t bit = ((uint64_t)rec_off[r] + (uint64_t)k * R) * 8;
+      const uint64_t row = (uint64_t)b * kBlockRows + k;
+      for (uint32_t j = 0; j < D; ++j) {
+        const uint32_t n = code_to_width(header_code(hdr, s * D + j, g.hb), W);
+        if (!n) continue;
+        uint32_t z = read_bits(body, bit, n);
+        bit += n;
+        tile_put<W>(X, D, row, j, (uint32_t)unzigzag<W>(z));
+      }
+    }
+  }
+  __syncthreads();
+
+  // 4. invert the forecast
+  if (g.forecaster == kFcDelta) {
+    // x_r = sum_{k <= r} e_k mod 2^w per column: segment sums, a scan of the
+    // segment sums, then each segment re-summed from its offset.
+    const uint32_t S = D >= blockDim.x ? 1u : blockDim.x / D;
+    const uint64_t seg = (rows_c + S - 1) / S;
+    const uint64_t items = (uint64_t)D * S;
+    for (uint64_t t = threadIdx.x; t < items; t += blockDim.x) {
+      const uint32_t j = (uint32_t)(t % D), sg = (uint32_t)(t / D);
+      const uint64_t r0 = (uint64_t)sg * seg, r1 = min(rows_c, r0 + seg);
+      uint32_t acc = 0;
+      for (uint64_t r = r0; r < r1; ++r) acc += tile_get<W>(X, D, r, j);
+      if (S > 1) part[t] = acc;
+    }
+    __syncthreads();
+    if (S > 1) {
+      for (uint32_t j = threadIdx.x; j < D; j += blockDim.x) {
+        uint32_t run = 0;
+        for (uint32_t sg = 0; sg < S; ++sg) {
+          uint32_t v = part[sg * D + j];
+          part[sg * D + j] = run;
+          run += v;
+        }
+      }
+    }
+    __syncthreads();
+    for (uint64_t t = threadIdx.x; t < items; t += blockDim.x) {
+      const uint32_t j = (uint32_t)(t % D), sg = (uint32_t)(t / D);
+      const uint64_t r0 = (uint64_t)sg * seg, r1 = min(rows_c, r0 + seg);
+      uint32_t acc = S > 1 ? part[t] : 0u;
+      for (uint64_t r = r0; r < r1; ++r) {
+        acc += tile_get<W>(X, D, r, j);
+        tile_put<W>(X, D, r, j, acc);
+      }
+    }
+  } else {
+    // FIRE: per column, delta_i = wrap_w(floor(alpha * delta_{i-1} / 2^w) + e_i)
+    // computed as one multiply-add and shift in 32 bits, x_i = x_{i-1} + delta_i.
+    for (uint32_t j = threadIdx.x; j < D; j += blockDim.x) {
+      int32_t acc = 0, dp = 0;
+      uint32_t xp = 0;
+      for (uint32_t b = 0; b < nb; ++b) {
+        const int32_t a = acc >> g.learn_shift;
+        const uint32_t A = (uint32_t)a << (32 - 2 * W);
+        int32_t gsum = 0;
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) {
+          const uint64_t r = (uint64_t)b * kBlockRows + i;
+          const int32_t ev = sext<W>(tile_get<W>(X, D, r, j));
+          const int32_t d = (int32_t)(A * (uint32_t)dp + ((uint32_t)ev << (32 - W))) >> (32 - W);
+          if ((i & 1) == 0) gsum += sign_of(ev) * dp;
+          xp += (uint32_t)d;
+          tile_put<W>(X, D, r, j, xp);
+          dp = d;
+        }
+        acc = wrap_acc<W>((int32_t)((uint32_t)acc + (uint32_t)(gsum >> 2)));
+      }
+    }
+  }
+  __syncthreads();
+
+  // 5. store
+  if (p.staged) {
+    if (row0 * D * wb + bytes_c <= p.dst_cap) cta_copy_dec(dst_c, X, bytes_c);
+  }
+  __syncthreads();
+}
+
+template <int W>
+__global__ void __launch_bounds__(kDecThreads) k_decode(DecParams p) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ uint64_t s_data_bytes;
+  uint8_t *mem = p.staged ? smem : p.scratch + (uint64_t)blockIdx.x * p.scratch_per_cta;
+  const Geom &g = p.g;
+  if (threadIdx.x == 0) {
+    // the chunk bodies end at tail_off; check it before trusting it
+    uint64_t tail_off = le_u64(p.src + 48);
+    uint64_t db = tail_off >= g.data_off && tail_off <= p.src_size ? tail_off - g.data_off : 0;
+    if (!(tail_off >= g.data_off && tail_off <= p.src_size))
+      set_status(p.status, SPRINTZ_ERR_CORRUPT);
+    s_data_bytes = db;
+  }
+  __syncthreads();
+  const uint64_t data_bytes = s_data_bytes;
+  for (uint32_t c = blockIdx.x; c < g.n_chunks; c += gridDim.x) decode_chunk<W>(p, mem, c, data_bytes);
+}
+
+// Check the device header against the host's geometry and copy the tail.
+__global__ void k_decode_header_tail(DecParams p) {
+  const Geom &g = p.g;
+  __shared__ uint32_t s_ok;
+  __shared__ uint64_t s_tail_off;
+  if (threadIdx.x == 0) {
+    const uint8_t *h = p.src;
+    bool ok = h[0] == 'S' && h[1] == 'P' && h[2] == 'Z' && h[3] == '1' && h[4] == 1 &&
+              h[5] == g.w && h[6] == g.forecaster && h[7] == (g.huffman ? 1 : 0) &&
+              (h[8] | (h[9] << 8)) == g.D && h[10] == g.G && h[11] == g.learn_shift &&
+              le_u32(h + 12) == g.chunk_rows_opt && le_u32(h + 16) == (g.huffman ? g.huff_chunks : 0) &&
+              le_u32(h + 20) == g.n_chunks && le_u64(h + 24) == g.rows &&
+              le_u32(h + 32) == g.tail_rows && le_u32(h + 36) == 0 && le_u64(h + 40) == g.data_off;
+    uint64_t tail_off = le_u64(h + 48), total = le_u64(h + 56);
+    ok = ok && tail_off >= g.data_off && total <= p.src_size &&
+         total == tail_off + g.tail_rows * g.D * g.wb;
+    s_ok = ok;
+    s_tail_off = tail_off;
+    if (!ok) set_status(p.status, SPRINTZ_ERR_CORRUPT);
+  }
+  __syncthreads();
+  if (!s_ok) return;
+  const uint64_t tail_bytes = g.tail_rows * g.D * g.wb;
+  uint8_t *d = p.dst + g.full_rows * g.D * g.wb;
+  const uint8_t *s = p.src + s_tail_off;
+  for (uint64_t k = threadIdx.x; k < tail_bytes; k += blockDim.x) d[k] = s[k];
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+static uint64_t align256d(uint64_t v) { return (v + 255) & ~255ull; }
+
+struct DecPlan {
+  bool staged;
+  uint64_t smem;
+  uint32_t grid;
+  uint64_t scratch_per_cta;
+};
+
+static DecPlan dec_plan(const Geom &g, const LaunchCfg &cfg) {
+  DecPlan pl{};
+  DecLayout Ls = dec_layout(g, true);
+  const uint64_t smem_limit = std::min<uint64_t>((uint64_t)cfg.max_smem_optin, 200u * 1024);
+  pl.staged = Ls.total <= smem_limit;
+  if (pl.staged) {
+    pl.smem = Ls.total;
+    const void *fn = g.w == 8 ? (const void *)k_decode<8> : (const void *)k_decode<16>;
+    if (pl.smem > 48 * 1024)
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+    pl.grid = (uint32_t)std::min<uint64_t>(g.n_chunks, 1u << 30);
+    pl.scratch_per_cta = 0;
+  } else {
+    pl.smem = 0;
+    pl.grid = (uint32_t)std::min<uint64_t>(g.n_chunks, (uint64_t)cfg.sm_count * 2);
+    pl.scratch_per_cta = align256d(dec_layout(g, false).total);
+  }
+  if (pl.grid == 0) pl.grid = 1;
+  return pl;
+}
+
+uint64_t decode_workspace_bytes(const Geom &g, const LaunchCfg &cfg) {
+  if (g.n_chunks == 0) return 0;
+  DecPlan pl = dec_plan(g, cfg);
+  return (uint64_t)pl.grid * pl.scratch_per_cta;
+}
+
+int launch_decode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint64_t src_size,
+                  uint8_t *dst, uint64_t dst_cap, uint8_t *ws, uint64_t ws_bytes, int *d_status,
+                  cudaStream_t stream) {
+  DecParams p{};
+  p.src = src;
+  p.src_size = src_size;
+  p.dst = dst;
+  p.dst_cap = dst_cap;
+  p.status = d_status;
+  p.g = g;
+  k_decode_header_tail<<<1, 128, 0, stream>>>(p);
+  if (g.n_chunks > 0) {
+    DecPlan pl = dec_plan(g, cfg);
+    if (ws_bytes < (uint64_t)pl.grid * pl.scratch_per_cta) return SPRINTZ_ERR_WS_TOO_SMALL;
+    p.scratch = ws;
+    p.scratch_per_cta = pl.scratch_per_cta;
+    p.staged = pl.staged ? 1 : 0;
+    if (g.w == 8)
+      k_decode<8><<<pl.grid, kDecThreads, pl.smem, stream>>>(p);
+    else
+      k_decode<16><<<pl.grid, kDecThreads, pl.smem, stream>>>(p);
+  }
+  return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
+}
+
+}  // namespace spz

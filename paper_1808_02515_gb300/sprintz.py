@@ -1,0 +1,245 @@
+"""Python binding of the CUDA Sprintz codec (libsprintz_gb300.so).
+
+Argument marshalling only: every step of compression and decompression runs
+in the library's CUDA kernels. PyTorch supplies device memory and streams.
+If the library is missing the binding raises; there is no CPU fallback.
+
+The entry points mirror the C ABI in include/sprintz_gb300.h:
+    sprintz_compress / sprintz_decompress / sprintz_query /
+    sprintz_max_compressed_size / sprintz_*_workspace_size /
+    sprintz_get_status / sprintz_strerror
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libsprintz_gb300.so")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_UNSUPPORTED_W = -2
+ERR_DST_TOO_SMALL = -3
+ERR_WS_TOO_SMALL = -4
+ERR_CORRUPT = -5
+ERR_TIMEOUT = -6
+ERR_CUDA = -7
+ERR_UNSUPPORTED = -8
+
+DELTA, FIRE = 0, 1
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("forecaster", ctypes.c_uint8), ("huffman", ctypes.c_uint8),
+                ("group_blocks", ctypes.c_uint8), ("learn_shift", ctypes.c_uint8),
+                ("chunk_rows", ctypes.c_uint32), ("huff_chunks", ctypes.c_uint32)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_uint64), ("D", ctypes.c_uint32), ("w", ctypes.c_uint32),
+                ("opts", _Opts), ("n_chunks", ctypes.c_uint32), ("tail_rows", ctypes.c_uint32),
+                ("data_off", ctypes.c_uint64), ("tail_off", ctypes.c_uint64),
+                ("total_bytes", ctypes.c_uint64)]
+
+
+@dataclass(frozen=True)
+class Opts:
+    forecaster: int = FIRE
+    huffman: int = 0
+    group_blocks: int = 2
+    learn_shift: int = 1
+    chunk_rows: int = 1024
+    huff_chunks: int = 64
+
+    def c(self) -> _Opts:
+        return _Opts(self.forecaster, self.huffman, self.group_blocks, self.learn_shift,
+                     self.chunk_rows, self.huff_chunks)
+
+
+class SprintzError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        u64, u32, i32, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_void_p
+        PO, PI = ctypes.POINTER(_Opts), ctypes.POINTER(_Info)
+        L.sprintz_ctx_create.restype = i32
+        L.sprintz_ctx_create.argtypes = [ctypes.POINTER(vp), i32]
+        L.sprintz_ctx_destroy.restype = None
+        L.sprintz_ctx_destroy.argtypes = [vp]
+        L.sprintz_max_compressed_size.restype = u64
+        L.sprintz_max_compressed_size.argtypes = [u64, u32, u32, PO]
+        L.sprintz_compress_workspace_size.restype = u64
+        L.sprintz_compress_workspace_size.argtypes = [u64, u32, u32, PO]
+        L.sprintz_decompress_workspace_size.restype = u64
+        L.sprintz_decompress_workspace_size.argtypes = [PI]
+        L.sprintz_compress.restype = i32
+        L.sprintz_compress.argtypes = [vp, vp, u64, u32, u32, PO, vp, u64, vp, vp, u64, vp]
+        L.sprintz_decompress.restype = i32
+        L.sprintz_decompress.argtypes = [vp, vp, u64, PI, vp, u64, vp, u64, vp]
+        L.sprintz_query.restype = i32
+        L.sprintz_query.argtypes = [vp, u64, PI]
+        L.sprintz_get_status.restype = i32
+        L.sprintz_get_status.argtypes = [vp, vp]
+        L.sprintz_strerror.restype = ctypes.c_char_p
+        L.sprintz_strerror.argtypes = [i32]
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().sprintz_strerror(code).decode()
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != OK:
+        raise SprintzError(rc, what)
+
+
+def max_compressed_size(rows: int, D: int, w: int, opts: Opts) -> int:
+    o = opts.c()
+    return int(lib().sprintz_max_compressed_size(rows, D, w, ctypes.byref(o)))
+
+
+def compress_workspace_size(rows: int, D: int, w: int, opts: Opts) -> int:
+    o = opts.c()
+    return int(lib().sprintz_compress_workspace_size(rows, D, w, ctypes.byref(o)))
+
+
+@dataclass(frozen=True)
+class Info:
+    rows: int
+    D: int
+    w: int
+    opts: Opts
+    n_chunks: int
+    tail_rows: int
+    data_off: int
+    tail_off: int
+    total_bytes: int
+
+    def c(self) -> _Info:
+        return _Info(self.rows, self.D, self.w, self.opts.c(), self.n_chunks, self.tail_rows,
+                     self.data_off, self.tail_off, self.total_bytes)
+
+
+def query(header: bytes) -> Info:
+    """Parse a host copy of a stream's first 64 (or more) bytes."""
+    buf = ctypes.create_string_buffer(bytes(header), len(header))
+    info = _Info()
+    _check(lib().sprintz_query(buf, len(header), ctypes.byref(info)), "sprintz_query")
+    o = info.opts
+    return Info(info.rows, info.D, info.w,
+                Opts(o.forecaster, o.huffman, o.group_blocks, o.learn_shift, o.chunk_rows,
+                     o.huff_chunks),
+                info.n_chunks, info.tail_rows, info.data_off, info.tail_off, info.total_bytes)
+
+
+def decompress_workspace_size(info: Info) -> int:
+    ci = info.c()
+    return int(lib().sprintz_decompress_workspace_size(ctypes.byref(ci)))
+
+
+class Codec:
+    """A library context on one device plus the torch-side plumbing.
+
+    compress()/decompress() take device tensors and enqueue the library's
+    kernels on the current torch stream (or the stream given)."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        self.torch = torch
+        self.device = device
+        ctx = ctypes.c_void_p()
+        _check(lib().sprintz_ctx_create(ctypes.byref(ctx), device), "sprintz_ctx_create")
+        self.ctx = ctx
+
+    def close(self) -> None:
+        if self.ctx:
+            lib().sprintz_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self, stream):
+        s = stream if stream is not None else self.torch.cuda.current_stream(self.device)
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def compress_into(self, src, rows: int, D: int, w: int, opts: Opts, dst, out_size, ws,
+                      stream=None) -> None:
+        """Raw entry point: src/dst/out_size/ws are device tensors (or None
+        for an empty workspace)."""
+        o = opts.c()
+        rc = lib().sprintz_compress(self.ctx, ctypes.c_void_p(src.data_ptr() if rows else 0),
+                                    rows, D, w, ctypes.byref(o), ctypes.c_void_p(dst.data_ptr()),
+                                    dst.numel() * dst.element_size(),
+                                    ctypes.c_void_p(out_size.data_ptr()),
+                                    ctypes.c_void_p(ws.data_ptr() if ws is not None else 0),
+                                    ws.numel() if ws is not None else 0, self._stream(stream))
+        _check(rc, "sprintz_compress")
+
+    def compress(self, x, opts: Opts = Opts(), stream=None):
+        """Compress a (rows, D) uint8 / uint16 (or int16) CUDA tensor.
+        Returns (dst, size): the stream buffer and a device uint64 size."""
+        torch = self.torch
+        if x.dim() == 1:
+            x = x.view(-1, 1)
+        if x.dtype not in (torch.uint8, torch.int16, torch.uint16):
+            raise TypeError("samples must be uint8 or 16-bit")
+        x = x.contiguous()
+        rows, D = x.shape
+        w = 8 if x.dtype == torch.uint8 else 16
+        cap = max_compressed_size(rows, D, w, opts)
+        if cap == 0:
+            raise SprintzError(ERR_INVALID_ARG, "sprintz_max_compressed_size")
+        dst = torch.empty(cap, dtype=torch.uint8, device=x.device)
+        size = torch.zeros(1, dtype=torch.int64, device=x.device)
+        wsn = compress_workspace_size(rows, D, w, opts)
+        ws = torch.empty(wsn, dtype=torch.uint8, device=x.device) if wsn else None
+        self.compress_into(x, rows, D, w, opts, dst, size, ws, stream)
+        return dst, size
+
+    def decompress_into(self, src, src_size: int, info: Info, dst, ws, stream=None) -> None:
+        ci = info.c()
+        rc = lib().sprintz_decompress(self.ctx, ctypes.c_void_p(src.data_ptr()), src_size,
+                                      ctypes.byref(ci),
+                                      ctypes.c_void_p(dst.data_ptr() if dst.numel() else 0),
+                                      dst.numel() * dst.element_size(),
+                                      ctypes.c_void_p(ws.data_ptr() if ws is not None else 0),
+                                      ws.numel() if ws is not None else 0, self._stream(stream))
+        _check(rc, "sprintz_decompress")
+
+    def decompress(self, src, info: Info, src_size: int | None = None, stream=None):
+        """Decompress a device stream; `info` comes from query() on a host copy
+        of its header. Returns a (rows, D) uint8 / int16 tensor."""
+        torch = self.torch
+        dt = torch.uint8 if info.w == 8 else torch.int16
+        dst = torch.empty((info.rows, info.D), dtype=dt, device=src.device)
+        wsn = decompress_workspace_size(info)
+        ws = torch.empty(wsn, dtype=torch.uint8, device=src.device) if wsn else None
+        n = src_size if src_size is not None else src.numel()
+        self.decompress_into(src, n, info, dst, ws, stream)
+        return dst
+
+    def status(self, stream=None) -> int:
+        return int(lib().sprintz_get_status(self.ctx, self._stream(stream)))
+
+    def check(self, stream=None) -> None:
+        _check(self.status(stream), "device status")
