@@ -400,6 +400,208 @@ __global__ void k_decode_header_tail(DecParams p) {
 }
 
 // ---------------------------------------------------------------------------
+// Lane-per-column decoder (D <= 32)
+//
+// A warp decodes K = floor(32 / D) consecutive chunks; lane k*D + j owns
+// column j of chunk k for the whole chunk.  The D lanes of a chunk walk its
+// header groups together (each reads its own width code; a segmented warp
+// scan gives every lane its bit offset and the record's size), read their
+// column's bits straight from the stream through L1, and run the inverse
+// forecast in registers: FIRE's step delta_i = wrap_w(floor(alpha *
+// delta_{i-1} / 2^w) + e_i) is one 32-bit multiply-add and one arithmetic
+// shift (alpha pre-shifted by 32 - 2w, e_i by 32 - w).  Each block's rows are
+// staged per warp in shared memory and written with 8-byte stores.
+// ---------------------------------------------------------------------------
+
+
+constexpr int kLaneThreads = 128;
+constexpr int kLaneWarps = kLaneThreads / 32;
+constexpr uint32_t kStageBytes = 512;  // K * 8 rows * D columns * 2 bytes <= 512
+
+// n (<= 16) bits at bit position `bit` of 4-byte-aligned memory `w`.
+__device__ __forceinline__ uint32_t bits_at(const uint32_t *w, uint64_t bit, uint32_t n) {
+  const uint32_t *p = w + (bit >> 5);
+  uint32_t lo = __ldg(p), hi = __ldg(p + 1);
+  return __funnelshift_r(lo, hi, (uint32_t)bit & 31u) & ((1u << n) - 1u);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p) {
+  const Geom &g = p.g;
+  const uint32_t D = g.D;
+  const uint32_t K = 32 / D;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t kk = lane / D, j = lane % D;
+  const uint32_t seg0 = lane - j;  // first lane of this chunk's segment
+  const uint64_t warp_id = (uint64_t)blockIdx.x * kLaneWarps + warp;
+  const uint64_t c64 = warp_id * K + kk;
+  __shared__ __align__(16) uint8_t stage_all[kLaneWarps][kStageBytes];
+  uint8_t *stage = stage_all[warp];
+  const uint32_t wb = W / 8;
+  const uint32_t blk_bytes = kBlockRows * D * wb;  // one chunk's block of output
+
+  // the chunk bodies end at tail_off
+  const uint64_t tail_off = le_u64(p.src + 48);
+  const bool hdr_ok = tail_off >= g.data_off && tail_off <= p.src_size;
+  const uint64_t data_bytes = hdr_ok ? tail_off - g.data_off : 0;
+
+  bool live = kk < K && c64 < g.n_chunks && hdr_ok;
+  const uint32_t c = (uint32_t)c64;
+  uint64_t off = 0, end = 0;
+  uint32_t nrec = 0, packed = 0, nb = 0;
+  uint64_t row0 = 0;
+  if (live) {
+    const uint8_t *e = p.src + kHdrBytes + (uint64_t)c * kEntryBytes;
+    off = le_u64(e);
+    nrec = le_u32(e + 8);
+    packed = le_u32(e + 12);
+    end = c + 1 < g.n_chunks ? le_u64(e + kEntryBytes) : data_bytes;
+    row0 = (uint64_t)c * g.chunk_rows;
+    nb = (uint32_t)(min(g.chunk_rows, g.full_rows - row0) / kBlockRows);
+    if (off > end || end > data_bytes || end - off != packed || nrec < 1 || nrec > nb) {
+      live = false;
+      if (j == 0) set_status(p.status, SPRINTZ_ERR_CORRUPT);
+    }
+  }
+  const uint8_t *body = p.src + g.data_off + off;
+  // aligned word view of the stream; words near the buffer end are read bytewise
+  const uint32_t *wbase = reinterpret_cast<const uint32_t *>((uintptr_t)p.src & ~(uintptr_t)3);
+  const uint64_t body_bit0 = ((uint64_t)((uintptr_t)body - (uintptr_t)wbase)) * 8;
+  const bool fast = (uintptr_t)body + packed + 8 <= (uintptr_t)p.src + p.src_size;
+
+  // walk state
+  uint64_t gpos = 0, hdr = 0;
+  uint32_t gslot = g.G, rec = 0, rem = 0;
+  bool run = true;
+  uint64_t pbit = 0;  // bit of this lane's value in row 0 of the current block (from body)
+  uint32_t stride = 0, n = 0;
+  // forecaster state
+  uint32_t xp = 0;
+  int32_t dp = 0, acc = 0;
+
+  const uint32_t nb_max = (uint32_t)(min(g.chunk_rows, g.full_rows) / kBlockRows);
+  for (uint32_t b = 0; b < nb_max; ++b) {
+    const bool here = live && b < nb;
+    const bool need = here && rem == 0;
+    const uint32_t need_mask = __ballot_sync(0xFFFFFFFFu, need);
+    if (need) {
+      bool bad = rec >= nrec;
+      if (gslot == g.G) {
+        hdr = gpos;
+        gpos += g.hdr_bytes;
+        gslot = 0;
+      }
+      const bool hdr_in = hdr + g.hdr_bytes <= packed;
+      bad |= !hdr_in;
+      const uint32_t code =
+          hdr_in ? read_bits(body, hdr * 8 + (uint64_t)(gslot * D + j) * g.hb, g.hb) : 0u;
+      const uint32_t nw = code_to_width(code, W);
+      uint32_t v = nw;
+      for (uint32_t o = 1; o < D; o <<= 1) {
+        uint32_t t = __shfl_up_sync(need_mask, v, o);
+        if (j >= o) v += t;
+      }
+      const uint32_t total = __shfl_sync(need_mask, v, seg0 + D - 1);
+      const uint32_t prefix = v - nw;
+      if (total == 0) {
+        uint32_t cnt = 0;
+        if (gpos + 2 <= packed) cnt = (uint32_t)body[gpos] | ((uint32_t)body[gpos + 1] << 8);
+        gpos += 2;
+        run = true;
+        rem = cnt;
+        bad |= cnt == 0 || b + cnt > nb;
+      } else {
+        const uint64_t pay = gpos;
+        const uint32_t size = g.col_major ? total : 8 * ((total + 7) / 8);
+        gpos += size;
+        run = false;
+        rem = 1;
+        n = nw;
+        if (g.col_major) {
+          pbit = (pay + prefix) * 8;
+          stride = nw;
+        } else {
+          pbit = pay * 8 + prefix;
+          stride = size;  // 8 * R bits between rows
+        }
+      }
+      bad |= gpos > packed;
+      gslot++;
+      rec++;
+      if (bad) {
+        live = false;
+        if (j == 0) set_status(p.status, SPRINTZ_ERR_CORRUPT);
+      }
+    }
+    const bool emit = here && live;
+    uint32_t out[kBlockRows];
+    if (emit) {
+      int32_t ev[kBlockRows];
+      if (run || n == 0) {
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) ev[i] = 0;
+      } else if (fast) {
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i)
+          ev[i] = unzigzag<W>(bits_at(wbase, body_bit0 + pbit + (uint64_t)i * stride, n));
+      } else {
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i)
+          ev[i] = unzigzag<W>(read_bits(body, pbit + (uint64_t)i * stride, n));
+      }
+      if (g.forecaster == kFcDelta) {
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) {
+          xp += (uint32_t)ev[i];
+          out[i] = xp;
+        }
+      } else {
+        const int32_t a = acc >> g.learn_shift;
+        const uint32_t A = (uint32_t)a << (32 - 2 * W);
+        int32_t gsum = 0;
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) {
+          const int32_t d = (int32_t)(A * (uint32_t)dp + ((uint32_t)ev[i] << (32 - W))) >> (32 - W);
+          if ((i & 1) == 0) gsum += sign_of(ev[i]) * dp;
+          xp += (uint32_t)d;
+          out[i] = xp;
+          dp = d;
+        }
+        acc = wrap_acc<W>((int32_t)((uint32_t)acc + (uint32_t)(gsum >> 2)));
+      }
+#pragma unroll
+      for (int i = 0; i < kBlockRows; ++i)
+        store_sample<W>(stage + kk * blk_bytes + (i * D + j) * wb, out[i]);
+      rem--;
+    }
+    __syncwarp();
+    // write the block rows of every chunk of the warp: 8-byte words
+    const uint32_t words_per = blk_bytes / 8;
+    const uint32_t total_words = K * words_per;
+    for (uint32_t q0 = 0; q0 < total_words; q0 += 32) {  // same trip count in every lane
+      const uint32_t qq = q0 + lane;
+      const uint32_t k2 = min(qq / words_per, K - 1);
+      const bool e2 = __shfl_sync(0xFFFFFFFFu, emit, k2 * D);
+      if (qq < total_words && e2) {
+        const uint64_t c2 = warp_id * K + k2;
+        const uint64_t r2 = c2 * g.chunk_rows + (uint64_t)b * kBlockRows;
+        uint64_t *d8 = reinterpret_cast<uint64_t *>(p.dst + r2 * D * wb) + (qq % words_per);
+        *d8 = *reinterpret_cast<const uint64_t *>(stage + (uint64_t)qq * 8);
+      }
+    }
+    __syncwarp();
+  }
+  // every record consumed, the body used up, unused slots of the last group zero
+  if (live) {
+    bool bad = rec != nrec || gpos != packed;
+    for (uint32_t s = gslot; s < g.G && !bad; ++s)
+      bad |= read_bits(body, hdr * 8 + (uint64_t)(s * D + j) * g.hb, g.hb) != 0;
+    if (bad) set_status(p.status, SPRINTZ_ERR_CORRUPT);
+  }
+}
+
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 
@@ -450,7 +652,16 @@ int launch_decode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint6
   p.status = d_status;
   p.g = g;
   k_decode_header_tail<<<1, 128, 0, stream>>>(p);
-  if (g.n_chunks > 0) {
+  if (g.n_chunks > 0 && g.D <= 32 && ((uintptr_t)dst & 7) == 0) {
+    const uint64_t K = 32 / g.D;
+    const uint64_t warps = (g.n_chunks + K - 1) / K;
+    const uint64_t grid = (warps + kLaneWarps - 1) / kLaneWarps;
+    if (grid > 0x7FFFFFFFull) return SPRINTZ_ERR_INVALID_ARG;
+    if (g.w == 8)
+      k_decode_lanes<8><<<(uint32_t)grid, kLaneThreads, 0, stream>>>(p);
+    else
+      k_decode_lanes<16><<<(uint32_t)grid, kLaneThreads, 0, stream>>>(p);
+  } else if (g.n_chunks > 0) {
     DecPlan pl = dec_plan(g, cfg);
     if (ws_bytes < (uint64_t)pl.grid * pl.scratch_per_cta) return SPRINTZ_ERR_WS_TOO_SMALL;
     p.scratch = ws;

@@ -124,7 +124,8 @@ def test_parity_long_run_split(codec, oracle_mod):
     x = np.full((8 * 70000 + 3, 1), 9, dtype=np.uint8)
     x[:8, 0] = np.arange(8)
     s = roundtrip(codec, oracle_mod, x, forecaster=0, chunk_rows=0)
-    assert int.from_bytes(s[64 + 8:64 + 12].tobytes(), "little") == 3  # block, run 65535, run rest
+    # block 0 (0..7), block 1 (7 -> 9), a run of 65535 blocks, a run of the rest
+    assert int.from_bytes(s[64 + 8:64 + 12].tobytes(), "little") == 4
 
 
 def test_parity_random_walk_100k(codec, oracle_mod):
@@ -157,33 +158,62 @@ def test_repeat_calls_identical(codec, oracle_mod):
     assert n == int(s2.item()) and torch.equal(d1[:n], d2[:n])
 
 
-def test_corrupt_streams_flag_errors(codec, oracle_mod):
-    """Byte flips in a stream either decode or set ERR_CORRUPT in the device
-    status; the decoder's bounds checks keep every access inside the stream."""
+def _decode_rc(codec, s, src_size=None):
     spz = _spz()
-    rng = np.random.default_rng(7)
-    x = gen("walk", 4000 + 3, 3, 16, seed=11)
+    try:
+        inf = spz.query(s[:64].tobytes())
+    except spz.SprintzError as e:
+        return e.code
+    if inf.rows * inf.D > 10_000_000:
+        return None
+    st = torch.from_numpy(np.ascontiguousarray(s)).cuda()
+    codec.decompress(st, inf, src_size=s.size if src_size is None else src_size)
+    return codec.status()
+
+
+@pytest.mark.parametrize("D,w", [(3, 16), (8, 16), (1, 8), (40, 8)])
+def test_corrupt_streams_flag_errors(codec, oracle_mod, D, w):
+    """Corrupted streams either decode or set ERR_CORRUPT in the device
+    status, in agreement with the oracle; the decoder's bounds checks keep
+    every access inside the stream. Covers random byte flips, chunk-table
+    fields (offset, record count, packed size), zeroed run counts and group
+    headers, and a truncated stream size."""
+    import struct
+    spz = _spz()
+    rng = np.random.default_rng(7 + D)
+    x = gen("sparse", 4000 + 3, D, w, seed=11)
     ref = oracle_mod.compress(x, forecaster=1, chunk_rows=256)
     info = spz.query(ref[:64].tobytes())
-    seen_corrupt = 0
-    for trial in range(60):
+    assert _decode_rc(codec, ref) == spz.OK
+    corrupt = 0
+    for trial in range(48):
         s = ref.copy()
-        lo = 64 if trial % 2 else info.data_off
-        for _ in range(int(rng.integers(1, 4))):
-            pos = int(rng.integers(lo, s.size))
-            s[pos] ^= np.uint8(1 << int(rng.integers(0, 8)))
-        try:
-            inf = spz.query(s[:64].tobytes())
-        except spz.SprintzError:
-            continue
-        if inf.rows * inf.D > 10_000_000:
-            continue
-        st = torch.from_numpy(s).cuda()
-        codec.decompress(st, inf, src_size=s.size)
-        rc = codec.status()
-        assert rc in (spz.OK, spz.ERR_CORRUPT)
-        ok_oracle = oracle_mod.decompress_rc(s)
-        if ok_oracle == oracle_mod.ERR_CORRUPT:
+        kind = trial % 4
+        c = int(rng.integers(0, info.n_chunks))
+        e = 64 + 16 * c
+        if kind == 0:  # random flips anywhere after the header
+            for _ in range(int(rng.integers(1, 4))):
+                pos = int(rng.integers(64, s.size))
+                s[pos] ^= np.uint8(1 << int(rng.integers(0, 8)))
+        elif kind == 1:  # one chunk-table field
+            field = int(rng.integers(0, 3))
+            off = e + (0, 8, 12)[field]
+            s[off + int(rng.integers(0, 2))] ^= np.uint8(1 << int(rng.integers(0, 8)))
+        elif kind == 2:  # a chunk's first group header zeroed: records become runs
+            body = info.data_off + struct.unpack_from("<Q", s, e)[0]
+            hdr = (2 * D * (3 if w == 8 else 4) + 7) // 8
+            s[body:body + hdr] = 0
+        else:  # a stream shorter than its header says
+            rc = _decode_rc(codec, s, src_size=int(rng.integers(info.data_off, s.size)))
             assert rc == spz.ERR_CORRUPT
-        seen_corrupt += rc == spz.ERR_CORRUPT
-    assert seen_corrupt > 10
+            corrupt += 1
+            continue
+        rc = _decode_rc(codec, s)
+        if rc is None:
+            continue
+        assert rc in (spz.OK, spz.ERR_CORRUPT)
+        if oracle_mod.decompress_rc(s) == oracle_mod.ERR_CORRUPT:
+            assert rc == spz.ERR_CORRUPT, (trial, kind)
+        corrupt += rc == spz.ERR_CORRUPT
+    assert corrupt >= 12
+    assert _decode_rc(codec, ref) == spz.OK
