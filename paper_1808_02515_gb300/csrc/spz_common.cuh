@@ -147,6 +147,21 @@ __device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t *p) {
   return v;
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (TMA unit; p and bytes multiples of 16).
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Prefetch the 16-byte-aligned part of [lo, hi) that lies inside [buf_lo, buf_hi).
+__device__ __forceinline__ void prefetch_l2_range(uintptr_t lo, uintptr_t hi, uintptr_t buf_lo,
+                                                  uintptr_t buf_hi) {
+  uintptr_t a = (lo > buf_lo ? lo : buf_lo);
+  a = (a + 15) & ~(uintptr_t)15;
+  uintptr_t b = hi < buf_hi ? hi : buf_hi;
+  b &= ~(uintptr_t)15;
+  if (b > a) prefetch_l2_bulk((const void *)a, (uint32_t)(b - a));
+}
+
 // Host helpers --------------------------------------------------------------
 
 struct LaunchCfg {

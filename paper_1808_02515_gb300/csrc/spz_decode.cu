@@ -425,6 +425,23 @@ __device__ __forceinline__ uint32_t bits_at(const uint32_t *w, uint64_t bit, uin
   return __funnelshift_r(lo, hi, (uint32_t)bit & 31u) & ((1u << n) - 1u);
 }
 
+// Bits [bit, bit + n) (n <= 16) of a word array (two aligned 32-bit loads).
+__device__ __forceinline__ uint32_t wbits(const uint32_t *w, uint32_t bit, uint32_t mask) {
+  const uint32_t *q = w + (bit >> 5);
+  return __funnelshift_r(__ldg(q), __ldg(q + 1), bit) & mask;
+}
+
+// Bits [bit, bit + n) read bytewise (no byte outside [0, (bit + n + 7) / 8) touched).
+__device__ __forceinline__ uint32_t bbits(const uint8_t *b, uint32_t bit, uint32_t mask) {
+  const uint8_t *q = b + (bit >> 3);
+  const uint32_t n = 32 - __clz(mask);
+  const uint32_t s = bit & 7;
+  uint32_t v = q[0];
+  if (s + n > 8) v |= (uint32_t)q[1] << 8;
+  if (s + n > 16) v |= (uint32_t)q[2] << 16;
+  return (v >> s) & mask;
+}
+
 template <int W>
 __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p) {
   const Geom &g = p.g;
@@ -433,11 +450,13 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p) {
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t kk = lane / D, j = lane % D;
   const uint32_t seg0 = lane - j;  // first lane of this chunk's segment
+  const uint32_t last = seg0 + D - 1;
   const uint64_t warp_id = (uint64_t)blockIdx.x * kLaneWarps + warp;
   const uint64_t c64 = warp_id * K + kk;
   __shared__ __align__(16) uint8_t stage_all[kLaneWarps][kStageBytes];
   uint8_t *stage = stage_all[warp];
   const uint32_t wb = W / 8;
+  const uint32_t hb = g.hb, G = g.G;
   const uint32_t blk_bytes = kBlockRows * D * wb;  // one chunk's block of output
 
   // the chunk bodies end at tail_off
@@ -449,14 +468,13 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p) {
   const uint32_t c = (uint32_t)c64;
   uint64_t off = 0, end = 0;
   uint32_t nrec = 0, packed = 0, nb = 0;
-  uint64_t row0 = 0;
   if (live) {
     const uint8_t *e = p.src + kHdrBytes + (uint64_t)c * kEntryBytes;
     off = le_u64(e);
     nrec = le_u32(e + 8);
     packed = le_u32(e + 12);
     end = c + 1 < g.n_chunks ? le_u64(e + kEntryBytes) : data_bytes;
-    row0 = (uint64_t)c * g.chunk_rows;
+    const uint64_t row0 = (uint64_t)c * g.chunk_rows;
     nb = (uint32_t)(min(g.chunk_rows, g.full_rows - row0) / kBlockRows);
     if (off > end || end > data_bytes || end - off != packed || nrec < 1 || nrec > nb) {
       live = false;
@@ -464,17 +482,47 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p) {
     }
   }
   const uint8_t *body = p.src + g.data_off + off;
-  // aligned word view of the stream; words near the buffer end are read bytewise
-  const uint32_t *wbase = reinterpret_cast<const uint32_t *>((uintptr_t)p.src & ~(uintptr_t)3);
-  const uint64_t body_bit0 = ((uint64_t)((uintptr_t)body - (uintptr_t)wbase)) * 8;
+  // aligned word view of the chunk: bit positions below are relative to wc
+  const uint32_t *wc = reinterpret_cast<const uint32_t *>((uintptr_t)body & ~(uintptr_t)3);
+  const uint32_t sh0 = (uint32_t)((uintptr_t)body & 3) * 8;  // body bit 0 inside wc
+  // word loads may touch up to 8 bytes past the body: only where they stay in the buffer
   const bool fast = (uintptr_t)body + packed + 8 <= (uintptr_t)p.src + p.src_size;
 
-  // walk state
-  uint64_t gpos = 0, hdr = 0;
-  uint32_t gslot = g.G, rec = 0, rem = 0;
+  // L2 prefetch window ahead of this chunk's read position (segment leader)
+  constexpr uint32_t kPrefetchWin = 2048;
+  const uintptr_t buf_lo = (uintptr_t)p.src, buf_hi = (uintptr_t)p.src + p.src_size;
+  const uintptr_t body_end = (uintptr_t)body + packed;
+  uintptr_t pf_end = (uintptr_t)body;
+  if (live && j == 0) {
+    uintptr_t e2 = min(body_end, pf_end + 2 * kPrefetchWin);
+    prefetch_l2_range(pf_end, e2, buf_lo, buf_hi);
+    pf_end = e2;
+  }
+
+  // output mapping of this lane's (up to two) 8-byte words of each block step
+  uint64_t *dptr[2];
+  uint32_t src_word[2], from_lane[2];
+  bool has[2];
+  const uint32_t words_per = blk_bytes / 8, total_words = K * words_per;
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const uint32_t q = lane + 32 * t;
+    has[t] = q < total_words;
+    const uint32_t k2 = has[t] ? q / words_per : 0;
+    const uint32_t wq = has[t] ? q % words_per : 0;
+    from_lane[t] = k2 * D;
+    src_word[t] = q;
+    const uint64_t r2 = (warp_id * K + k2) * g.chunk_rows;
+    dptr[t] = reinterpret_cast<uint64_t *>(p.dst + r2 * D * wb) + wq;
+  }
+  uint8_t *my_stage = stage + kk * blk_bytes + j * wb;
+  const uint32_t row_stride = D * wb;
+
+  // walk state (bit positions relative to wc)
+  uint32_t gpos = 0, hdr = 0;  // body bytes
+  uint32_t gslot = G, rec = 0, rem = 0;
   bool run = true;
-  uint64_t pbit = 0;  // bit of this lane's value in row 0 of the current block (from body)
-  uint32_t stride = 0, n = 0;
+  uint32_t pbit = 0, stride = 0, mask = 0;
   // forecaster state
   uint32_t xp = 0;
   int32_t dp = 0, acc = 0;
@@ -486,44 +534,49 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p) {
     const uint32_t need_mask = __ballot_sync(0xFFFFFFFFu, need);
     if (need) {
       bool bad = rec >= nrec;
-      if (gslot == g.G) {
+      if (gslot == G) {
         hdr = gpos;
         gpos += g.hdr_bytes;
         gslot = 0;
       }
-      const bool hdr_in = hdr + g.hdr_bytes <= packed;
+      const bool hdr_in = gpos <= packed;
       bad |= !hdr_in;
-      const uint32_t code =
-          hdr_in ? read_bits(body, hdr * 8 + (uint64_t)(gslot * D + j) * g.hb, g.hb) : 0u;
-      const uint32_t nw = code_to_width(code, W);
+      const uint32_t cbit = hdr * 8 + (gslot * D + j) * hb;
+      const uint32_t hmask = (1u << hb) - 1u;
+      uint32_t code = 0;
+      if (hdr_in) code = fast ? wbits(wc, sh0 + cbit, hmask) : bbits(body, cbit, hmask);
+      const uint32_t nw = code == (uint32_t)W - 1 ? (uint32_t)W : code;
       uint32_t v = nw;
-      for (uint32_t o = 1; o < D; o <<= 1) {
-        uint32_t t = __shfl_up_sync(need_mask, v, o);
-        if (j >= o) v += t;
+#pragma unroll
+      for (uint32_t o = 1; o < 32; o <<= 1) {
+        if (o < D) {
+          const uint32_t t = __shfl_up_sync(need_mask, v, o);
+          if (j >= o) v += t;
+        }
       }
-      const uint32_t total = __shfl_sync(need_mask, v, seg0 + D - 1);
-      const uint32_t prefix = v - nw;
+      const uint32_t total = __shfl_sync(need_mask, v, last);
       if (total == 0) {
         uint32_t cnt = 0;
-        if (gpos + 2 <= packed) cnt = (uint32_t)body[gpos] | ((uint32_t)body[gpos + 1] << 8);
+        if (gpos + 2 <= packed)
+          cnt = fast ? wbits(wc, sh0 + gpos * 8, 0xFFFFu) : bbits(body, gpos * 8, 0xFFFFu);
         gpos += 2;
         run = true;
         rem = cnt;
         bad |= cnt == 0 || b + cnt > nb;
       } else {
-        const uint64_t pay = gpos;
+        const uint32_t prefix = v - nw;
         const uint32_t size = g.col_major ? total : 8 * ((total + 7) / 8);
-        gpos += size;
         run = false;
         rem = 1;
-        n = nw;
+        mask = (1u << nw) - 1u;
         if (g.col_major) {
-          pbit = (pay + prefix) * 8;
+          pbit = (gpos + prefix) * 8;
           stride = nw;
         } else {
-          pbit = pay * 8 + prefix;
+          pbit = gpos * 8 + prefix;
           stride = size;  // 8 * R bits between rows
         }
+        gpos += size;
       }
       bad |= gpos > packed;
       gslot++;
@@ -533,73 +586,70 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p) {
         if (j == 0) set_status(p.status, SPRINTZ_ERR_CORRUPT);
       }
     }
+    if (live && j == 0 && pf_end < body_end && (uintptr_t)body + gpos + kPrefetchWin > pf_end) {
+      uintptr_t e2 = min(body_end, pf_end + kPrefetchWin);
+      prefetch_l2_range(pf_end & ~(uintptr_t)15, e2, buf_lo, buf_hi);
+      pf_end = e2;
+    }
     const bool emit = here && live;
-    uint32_t out[kBlockRows];
     if (emit) {
-      int32_t ev[kBlockRows];
-      if (run || n == 0) {
+      // zigzagged errors of this lane's column, 8 rows
+      uint32_t z[kBlockRows];
+      if (run || mask == 0) {
 #pragma unroll
-        for (int i = 0; i < kBlockRows; ++i) ev[i] = 0;
+        for (int i = 0; i < kBlockRows; ++i) z[i] = 0;
       } else if (fast) {
+        const uint32_t b0 = sh0 + pbit;
 #pragma unroll
-        for (int i = 0; i < kBlockRows; ++i)
-          ev[i] = unzigzag<W>(bits_at(wbase, body_bit0 + pbit + (uint64_t)i * stride, n));
+        for (int i = 0; i < kBlockRows; ++i) z[i] = wbits(wc, b0 + i * stride, mask);
       } else {
 #pragma unroll
-        for (int i = 0; i < kBlockRows; ++i)
-          ev[i] = unzigzag<W>(read_bits(body, pbit + (uint64_t)i * stride, n));
+        for (int i = 0; i < kBlockRows; ++i) z[i] = bbits(body, pbit + i * stride, mask);
       }
       if (g.forecaster == kFcDelta) {
 #pragma unroll
         for (int i = 0; i < kBlockRows; ++i) {
-          xp += (uint32_t)ev[i];
-          out[i] = xp;
+          xp += (z[i] >> 1) ^ (0u - (z[i] & 1u));
+          store_sample<W>(my_stage + i * row_stride, xp);
         }
       } else {
-        const int32_t a = acc >> g.learn_shift;
-        const uint32_t A = (uint32_t)a << (32 - 2 * W);
+        // delta_i = wrap_w(floor(alpha * delta_{i-1} / 2^w) + e_i): one
+        // multiply-add and one shift on 32-bit values pre-shifted by 32 - w
+        const uint32_t A = (uint32_t)(acc >> g.learn_shift) << (32 - 2 * W);
         int32_t gsum = 0;
 #pragma unroll
         for (int i = 0; i < kBlockRows; ++i) {
-          const int32_t d = (int32_t)(A * (uint32_t)dp + ((uint32_t)ev[i] << (32 - W))) >> (32 - W);
-          if ((i & 1) == 0) gsum += sign_of(ev[i]) * dp;
+          const uint32_t ev = (z[i] >> 1) ^ (0u - (z[i] & 1u));  // e_i, two's complement
+          const int32_t d = (int32_t)(A * (uint32_t)dp + (ev << (32 - W))) >> (32 - W);
+          if ((i & 1) == 0) gsum += z[i] == 0 ? 0 : ((z[i] & 1u) ? -dp : dp);
           xp += (uint32_t)d;
-          out[i] = xp;
+          store_sample<W>(my_stage + i * row_stride, xp);
           dp = d;
         }
         acc = wrap_acc<W>((int32_t)((uint32_t)acc + (uint32_t)(gsum >> 2)));
       }
-#pragma unroll
-      for (int i = 0; i < kBlockRows; ++i)
-        store_sample<W>(stage + kk * blk_bytes + (i * D + j) * wb, out[i]);
       rem--;
     }
     __syncwarp();
-    // write the block rows of every chunk of the warp: 8-byte words
-    const uint32_t words_per = blk_bytes / 8;
-    const uint32_t total_words = K * words_per;
-    for (uint32_t q0 = 0; q0 < total_words; q0 += 32) {  // same trip count in every lane
-      const uint32_t qq = q0 + lane;
-      const uint32_t k2 = min(qq / words_per, K - 1);
-      const bool e2 = __shfl_sync(0xFFFFFFFFu, emit, k2 * D);
-      if (qq < total_words && e2) {
-        const uint64_t c2 = warp_id * K + k2;
-        const uint64_t r2 = c2 * g.chunk_rows + (uint64_t)b * kBlockRows;
-        uint64_t *d8 = reinterpret_cast<uint64_t *>(p.dst + r2 * D * wb) + (qq % words_per);
-        *d8 = *reinterpret_cast<const uint64_t *>(stage + (uint64_t)qq * 8);
-      }
+    // block rows of every chunk of the warp: 8-byte words
+    const uint32_t boff = b * (blk_bytes / 8);
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const bool e2 = __shfl_sync(0xFFFFFFFFu, emit, from_lane[t]);
+      if (has[t] && e2) dptr[t][boff] = reinterpret_cast<const uint64_t *>(stage)[src_word[t]];
     }
     __syncwarp();
   }
   // every record consumed, the body used up, unused slots of the last group zero
   if (live) {
     bool bad = rec != nrec || gpos != packed;
-    for (uint32_t s = gslot; s < g.G && !bad; ++s)
-      bad |= read_bits(body, hdr * 8 + (uint64_t)(s * D + j) * g.hb, g.hb) != 0;
+    for (uint32_t s = gslot; s < G && !bad; ++s) {
+      const uint32_t cbit = hdr * 8 + (s * D + j) * hb;
+      bad |= (fast ? wbits(wc, sh0 + cbit, (1u << hb) - 1u) : bbits(body, cbit, (1u << hb) - 1u)) != 0;
+    }
     if (bad) set_status(p.status, SPRINTZ_ERR_CORRUPT);
   }
 }
-
 
 // ---------------------------------------------------------------------------
 // Host side
@@ -652,7 +702,7 @@ int launch_decode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint6
   p.status = d_status;
   p.g = g;
   k_decode_header_tail<<<1, 128, 0, stream>>>(p);
-  if (g.n_chunks > 0 && g.D <= 32 && ((uintptr_t)dst & 7) == 0) {
+  if (g.n_chunks > 0 && g.D <= 32 && ((uintptr_t)dst & 7) == 0 && g.max_body < (1ull << 28)) {
     const uint64_t K = 32 / g.D;
     const uint64_t warps = (g.n_chunks + K - 1) / K;
     const uint64_t grid = (warps + kLaneWarps - 1) / kLaneWarps;

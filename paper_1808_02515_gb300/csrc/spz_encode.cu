@@ -20,6 +20,8 @@
 //      the raw tail, the stream header and the stream size.
 // Chunks too large for shared memory use a per-CTA global scratch slot and
 // read their rows straight from the source.
+#include <stdlib.h>
+
 #include <algorithm>
 
 #include "spz_common.cuh"
@@ -457,10 +459,380 @@ __global__ void k_encode_tail_only(EncParams p) {
 }
 
 // ---------------------------------------------------------------------------
+// Lane-per-column encoder (D <= 32)
+//
+// Persistent warps take groups of K = floor(32 / D) consecutive chunks from a
+// ticket; lane k*D + j owns column j of chunk k.  Per group:
+//   pass A  streams the rows block by block (a per-warp shared stage filled by
+//           8-byte loads, one block of lookahead), runs the forecaster in
+//           registers, takes every column's width and, with a segmented warp
+//           scan, each block's size; the record logic of Algorithm 1 (runs of
+//           all-zero blocks, groups of G headers) gives the body size;
+//   look-back over chunk groups (bounded waits) gives the group's offset;
+//   pass B  repeats the computation (its rows are still in L2: the grid is
+//           sized so the groups in flight fit) and ORs header codes and
+//           payload bits into a per-chunk shared ring addressed by absolute
+//           output byte; completed 16-byte units are stored with one vector
+//           store, only the bytes at the chunk's two ends with byte stores.
+// ---------------------------------------------------------------------------
+
+constexpr int kEncLaneThreads = 128;
+constexpr int kEncLaneWarps = kEncLaneThreads / 32;
+constexpr uint32_t kEncStage = 512;  // K * 8 rows * D * 2 bytes <= 512
+
+struct EncLaneCfg {
+  uint32_t window;  // ring bytes per chunk (power of two >= 64)
+  uint32_t n_groups;
+};
+
+__host__ __device__ inline uint32_t enc_window_bytes(const Geom &g) {
+  uint64_t maxpay = (uint64_t)g.D * g.w;  // bytes of a block at full width
+  uint64_t need = 2ull * g.hdr_bytes + (uint64_t)(g.G + 1) * maxpay + 48;
+  uint32_t wsz = 64;
+  while (wsz < need) wsz <<= 1;
+  return wsz;
+}
+
+// OR the low n (<= 16) bits of v into the ring at absolute bit position `abit`.
+__device__ __forceinline__ void ring_or(uint32_t *ring, uint32_t ring_words, uint64_t abit,
+                                        uint32_t v, uint32_t n) {
+  if (!n || !v) return;
+  const uint32_t wi = (uint32_t)(abit >> 5) & (ring_words - 1);
+  const uint32_t sh = (uint32_t)abit & 31;
+  atomicOr(&ring[wi], v << sh);
+  if (sh + n > 32) atomicOr(&ring[(wi + 1) & (ring_words - 1)], v >> (32 - sh));
+}
+
+// Per-chunk state of one pass.
+struct EncRun {
+  uint32_t xp;   // x_{i-1}
+  int32_t dp;    // delta_{i-1}
+  int32_t acc;   // FIRE accumulator
+  uint32_t run;  // blocks in the current zero run
+  uint32_t nrec;
+  uint64_t pos;  // body bytes laid out so far
+  uint64_t hpos; // header of the open group
+  bool open;     // a group is open (its header is incomplete)
+  uint64_t flushed;  // body bytes already stored
+};
+
+template <int W, bool EMIT>
+__device__ uint64_t encode_pass(const EncParams &p, const Geom &g, uint8_t *stage, uint32_t *ring,
+                                uint32_t ring_words, bool live, uint32_t grp, uint32_t K,
+                                uint32_t kk, uint32_t j, uint32_t lane, uint64_t row0, uint32_t nb,
+                                uint64_t base /* absolute address of the body (EMIT) */,
+                                uint32_t *nrec_out) {
+  const uint32_t D = g.D;
+  const uint32_t wb = W / 8;
+  const uint32_t seg0 = lane - j;
+  const uint32_t words_per = D * wb;  // 8-byte words of one chunk's block
+  const uint32_t total_words = K * words_per;
+  const uint32_t nb_max = (uint32_t)(min(g.chunk_rows, g.full_rows) / kBlockRows);
+  EncRun st{};
+
+  // which chunk, block word does each of this lane's (up to 2) stage words hold
+  auto load_words = [&](uint32_t b, uint64_t *w) {
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const uint32_t q = lane + 32 * t;
+      w[t] = 0;
+      const uint32_t k2 = min(q / words_per, K - 1);
+      const uint32_t lv = __shfl_sync(0xFFFFFFFFu, live ? nb : 0u, k2 * D);
+      if (q < total_words && b < lv) {
+        const uint64_t c2 = (uint64_t)grp * K + k2;
+        const uint64_t r = c2 * g.chunk_rows + (uint64_t)b * kBlockRows;
+        w[t] = __ldg(reinterpret_cast<const unsigned long long *>(p.src + r * D * wb) + (q % words_per));
+      }
+    }
+  };
+
+  uint64_t wcur[2], wnext[2];
+  load_words(0, wcur);
+  // L2 prefetch of the chunk's rows ahead (segment leader, pass A)
+  const uintptr_t rows_lo = (uintptr_t)(p.src + row0 * D * wb);
+  const uintptr_t rows_hi = rows_lo + (uint64_t)nb * kBlockRows * D * wb;
+  uintptr_t pf = rows_lo;
+  if (!EMIT && live && j == 0) {
+    uintptr_t e2 = min(rows_hi, pf + 8192);
+    prefetch_l2_range(pf, e2, rows_lo, rows_hi);
+    pf = e2;
+  }
+
+  auto record = [&](bool is_run, uint32_t run_len, uint32_t total, uint32_t prefix, uint32_t n,
+                    const uint32_t *z) {
+    if (st.nrec % g.G == 0) {
+      st.hpos = st.pos;
+      st.pos += g.hdr_bytes;
+      st.open = true;
+    }
+    const uint32_t s = st.nrec % g.G;
+    uint32_t size;
+    if (is_run) {
+      size = 2;
+      if (EMIT && j == 0) ring_or(ring, ring_words, ((uint64_t)base + st.pos) * 8, run_len, 16);
+    } else {
+      size = g.col_major ? total : 8 * ((total + 7) / 8);
+      if (EMIT) {
+        ring_or(ring, ring_words, ((uint64_t)base + st.hpos) * 8 + (uint64_t)(s * D + j) * g.hb,
+                width_to_code(n, W), g.hb);
+        if (n) {
+          const uint64_t b0 = ((uint64_t)base + st.pos) * 8;
+#pragma unroll
+          for (int i = 0; i < kBlockRows; ++i) {
+            const uint64_t bit = g.col_major ? b0 + (uint64_t)prefix * 8 + (uint64_t)i * n
+                                             : b0 + (uint64_t)i * size + prefix;
+            ring_or(ring, ring_words, bit, z[i], n);
+          }
+        }
+      }
+    }
+    st.pos += size;
+    st.nrec++;
+    if (st.nrec % g.G == 0) st.open = false;
+  };
+
+  // store the completed 16-byte units of [flushed, limit) (absolute alignment);
+  // units holding bytes outside [base, base + body) get byte stores
+  auto flush = [&](uint64_t limit, bool final_) {
+    const uint64_t a0 = base + st.flushed;
+    const uint64_t a1 = final_ ? base + limit : ((base + limit) & ~15ull);
+    if (a1 <= a0) return;
+    const uint64_t u0 = a0 & ~15ull;
+    const uint64_t nu = (a1 - u0 + 15) / 16;
+    for (uint64_t u = j; u < nu; u += D) {
+      const uint64_t ua = u0 + 16 * u;
+      const uint32_t ri = (uint32_t)(ua >> 2) & (ring_words - 1);
+      const uint4 v = *reinterpret_cast<const uint4 *>(&ring[ri]);
+      if (ua >= base && ua + 16 <= a1) {
+        *reinterpret_cast<uint4 *>(ua) = v;
+      } else {
+        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+        for (uint32_t k = 0; k < 16; ++k) {
+          const uint64_t ab = ua + k;
+          if (ab >= a0 && ab < a1) *reinterpret_cast<uint8_t *>(ab) = (uint8_t)(wv[k >> 2] >> (8 * (k & 3)));
+        }
+      }
+      // a fully written unit is cleared for reuse; the last partial one keeps its bytes
+      if (ua + 16 <= a1) *reinterpret_cast<uint4 *>(&ring[ri]) = make_uint4(0, 0, 0, 0);
+    }
+    st.flushed = (a1 & ~15ull) > base ? (a1 & ~15ull) - base : st.flushed;
+    if (final_) st.flushed = limit;
+  };
+
+  for (uint32_t b = 0; b < nb_max; ++b) {
+    // stage this block, start loading the next one
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+      if (lane + 32 * t < total_words) reinterpret_cast<uint64_t *>(stage)[lane + 32 * t] = wcur[t];
+    if (b + 1 < nb_max) load_words(b + 1, wnext);
+    __syncwarp();
+    const bool here = live && b < nb;
+    uint32_t z[kBlockRows];
+    uint32_t n = 0;
+    if (here) {
+      uint32_t x[kBlockRows];
+#pragma unroll
+      for (int i = 0; i < kBlockRows; ++i)
+        x[i] = load_sample<W>(stage + kk * (kBlockRows * D * wb) + (i * D + j) * wb);
+      uint32_t orz = 0;
+      if (g.forecaster == kFcDelta) {
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) {
+          z[i] = zigzag<W>(sext<W>(x[i] - st.xp));
+          st.xp = x[i];
+          orz |= z[i];
+        }
+      } else {
+        const int32_t a = st.acc >> g.learn_shift;
+        int32_t gsum = 0;
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) {
+          const int32_t e = sext<W>(x[i] - st.xp - fire_pred_delta<W>(a, st.dp));
+          if ((i & 1) == 0) gsum += sign_of(e) * st.dp;
+          z[i] = zigzag<W>(e);
+          orz |= z[i];
+          st.dp = sext<W>(x[i] - st.xp);
+          st.xp = x[i];
+        }
+        st.acc = wrap_acc<W>((int32_t)((uint32_t)st.acc + (uint32_t)(gsum >> 2)));
+      }
+      n = bit_len(orz);
+      if (n == W - 1) n = W;
+    }
+    // segmented scan of the widths: this lane's offset and the block's total
+    uint32_t v = n;
+    for (uint32_t o = 1; o < D; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+      if (j >= o) v += t;
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, v, seg0 + D - 1);
+    const uint32_t prefix = v - n;
+    if (here) {
+      if (total == 0) {
+        if (++st.run == kMaxRun) {
+          record(true, st.run, 0, 0, 0, z);
+          st.run = 0;
+        }
+      } else {
+        if (st.run) {
+          record(true, st.run, 0, 0, 0, z);
+          st.run = 0;
+        }
+        record(false, 0, total, prefix, n, z);
+      }
+      if (!EMIT && j == 0 && pf < rows_hi && rows_lo + (uint64_t)(b + 1) * kBlockRows * D * wb + 4096 > pf) {
+        uintptr_t e2 = min(rows_hi, pf + 4096);
+        prefetch_l2_range(pf, e2, rows_lo, rows_hi);
+        pf = e2;
+      }
+    }
+    if (EMIT) {
+      __syncwarp();
+      if (here) flush(st.open ? st.hpos : st.pos, false);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 2; ++t) wcur[t] = wnext[t];
+  }
+  if (live) {
+    if (st.run) record(true, st.run, 0, 0, 0, nullptr);
+    st.open = false;
+  }
+  if (EMIT) {
+    __syncwarp();
+    if (live) flush(st.pos, true);
+    __syncwarp();
+  }
+  *nrec_out = st.nrec;
+  return st.pos;
+}
+
+template <int W>
+__global__ void __launch_bounds__(kEncLaneThreads) k_encode_lanes(EncParams p, EncLaneCfg cfg) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const Geom &g = p.g;
+  const uint32_t D = g.D;
+  const uint32_t K = 32 / D;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t kk = lane / D, j = lane % D;
+  const uint32_t seg0 = lane - j;
+  uint8_t *stage = smem + warp * kEncStage;
+  const uint32_t ring_words = cfg.window / 4;
+  uint32_t *ring = reinterpret_cast<uint32_t *>(smem + kEncLaneWarps * kEncStage +
+                                                ((uint64_t)warp * K + min(kk, K - 1)) * cfg.window);
+  const uint32_t wb = W / 8;
+
+  for (;;) {
+    uint32_t grp = 0;
+    if (lane == 0) grp = atomicAdd(p.ticket, 1u);
+    grp = __shfl_sync(0xFFFFFFFFu, grp, 0);
+    if (grp >= cfg.n_groups) break;
+    const uint64_t c64 = (uint64_t)grp * K + kk;
+    const bool live = kk < K && c64 < g.n_chunks;
+    const uint32_t c = (uint32_t)c64;
+    const uint64_t row0 = c64 * g.chunk_rows;
+    const uint32_t nb = live ? (uint32_t)(min(g.chunk_rows, g.full_rows - row0) / kBlockRows) : 0u;
+
+    // pass A: body sizes
+    uint32_t nrec = 0;
+    const uint64_t S = encode_pass<W, false>(p, g, stage, ring, ring_words, live, grp, K, kk, j,
+                                             lane, row0, nb, 0, &nrec);
+    // this group's total and each chunk's offset inside it
+    uint64_t v = (live && j == 0) ? S : 0;
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+      const uint64_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+      if (lane >= o) v += t;
+    }
+    const uint64_t group_total = __shfl_sync(0xFFFFFFFFu, v, 31);
+    const uint64_t excl = __shfl_sync(0xFFFFFFFFu, v, seg0) - __shfl_sync(0xFFFFFFFFu, (live && j == 0) ? S : 0ull, seg0);
+    // look-back over groups
+    uint64_t prefix = 0;
+    if (lane == 0) {
+      uint64_t *lb = p.lookback;
+      if (grp == 0) {
+        st_release_u64(&lb[0], kFlagPrefix | group_total);
+      } else {
+        st_release_u64(&lb[grp], kFlagAggregate | group_total);
+        int64_t k = (int64_t)grp - 1;
+        uint32_t spins = 0;
+        while (k >= 0) {
+          const uint64_t w = ld_acquire_u64(&lb[k]);
+          const uint64_t flag = w & ~kValueMask;
+          if (flag == 0) {
+            if (++spins > kSpinLimit) {
+              set_status(p.status, SPRINTZ_ERR_TIMEOUT);
+              break;
+            }
+            __nanosleep(32);
+            continue;
+          }
+          prefix += w & kValueMask;
+          if (flag == kFlagPrefix) break;
+          --k;
+        }
+        st_release_u64(&lb[grp], kFlagPrefix | (prefix + group_total));
+      }
+    }
+    prefix = __shfl_sync(0xFFFFFFFFu, prefix, 0);
+    const uint64_t off = prefix + excl;
+
+    // pass B: the body at its place
+    const uint64_t base = (uint64_t)(uintptr_t)(p.dst + g.data_off + off);
+    if (live) {
+      // clear this chunk's ring
+      for (uint32_t t = j; t < ring_words / 4; t += D)
+        reinterpret_cast<uint4 *>(ring)[t] = make_uint4(0, 0, 0, 0);
+    }
+    __syncwarp();
+    const bool fits = g.data_off + prefix + group_total <= p.dst_cap;
+    if (!fits && lane == 0) set_status(p.status, SPRINTZ_ERR_DST_TOO_SMALL);
+    uint32_t nrec_b = 0;
+    encode_pass<W, true>(p, g, stage, ring, ring_words, live && fits, grp, K, kk, j, lane, row0, nb,
+                         base, &nrec_b);
+    if (live && j == 0 && fits) {
+      // chunk entry: body offset, record count, packed bytes (little-endian)
+      uint8_t *e = p.dst + kHdrBytes + (uint64_t)c * kEntryBytes;
+      const uint64_t w1 = (uint64_t)nrec | ((uint64_t)S << 32);
+      for (int k = 0; k < 8; ++k) {
+        e[k] = (uint8_t)(off >> (8 * k));
+        e[8 + k] = (uint8_t)(w1 >> (8 * k));
+      }
+    }
+    __syncwarp();
+    if (c == g.n_chunks - 1 && live) {
+      const uint64_t tail_off = g.data_off + off + S;
+      const uint64_t tail_bytes = g.tail_rows * D * wb;
+      const uint64_t total = tail_off + tail_bytes;
+      if (total <= p.dst_cap) {
+        for (uint64_t k = j; k < tail_bytes; k += D) p.dst[tail_off + k] = p.src[g.full_rows * D * wb + k];
+        if (j == 0) {
+          write_stream_header(p.dst, g, tail_off, total);
+          *p.out_size = total;
+        }
+      } else if (j == 0) {
+        set_status(p.status, SPRINTZ_ERR_DST_TOO_SMALL);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 
 static uint64_t align256(uint64_t v) { return (v + 255) & ~255ull; }
+
+// CTAs (of 4 warps) per SM for the lane encoder; SPRINTZ_ENC_CTAS_PER_SM
+// overrides it for tuning.
+static uint32_t enc_lane_ctas_per_sm() {
+  static uint32_t v = [] {
+    const char *e = getenv("SPRINTZ_ENC_CTAS_PER_SM");
+    int x = e ? atoi(e) : 0;
+    return (uint32_t)(x > 0 && x <= 32 ? x : 3);
+  }();
+  return v;
+}
 
 struct EncPlan {
   bool stage_rows;
@@ -514,6 +886,32 @@ int launch_encode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint8
   p.g = g;
   if (g.n_chunks == 0) {
     k_encode_tail_only<<<1, 128, 0, stream>>>(p);
+    return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
+  }
+  if (g.D <= 32 && ((uintptr_t)src & 7) == 0) {
+    // lane-per-column encoder: persistent warps, a few per SM so that the
+    // groups between their two passes stay in L2
+    const uint32_t K = 32 / g.D;
+    EncLaneCfg lc;
+    lc.window = enc_window_bytes(g);
+    lc.n_groups = (uint32_t)((g.n_chunks + K - 1) / K);
+    const uint64_t smem = (uint64_t)kEncLaneWarps * kEncStage + (uint64_t)kEncLaneWarps * K * lc.window;
+    if (smem > (uint64_t)cfg.max_smem_optin) return SPRINTZ_ERR_UNSUPPORTED;
+    if (ws_bytes < 16 + 8ull * g.n_chunks) return SPRINTZ_ERR_WS_TOO_SMALL;
+    p.ticket = reinterpret_cast<uint32_t *>(ws);
+    p.lookback = reinterpret_cast<uint64_t *>(ws + 16);
+    const void *fn = g.w == 8 ? (const void *)k_encode_lanes<8> : (const void *)k_encode_lanes<16>;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return SPRINTZ_ERR_CUDA;
+    const uint64_t want_ctas = (lc.n_groups + kEncLaneWarps - 1) / kEncLaneWarps;
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(want_ctas, (uint64_t)cfg.sm_count *
+                                                                                   enc_lane_ctas_per_sm()));
+    if (cudaMemsetAsync(ws, 0, 16 + 8ull * lc.n_groups, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+    if (g.w == 8)
+      k_encode_lanes<8><<<(uint32_t)grid, kEncLaneThreads, smem, stream>>>(p, lc);
+    else
+      k_encode_lanes<16><<<(uint32_t)grid, kEncLaneThreads, smem, stream>>>(p, lc);
     return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
   }
   EncPlan pl = enc_plan(g, cfg);
