@@ -115,6 +115,34 @@ int sprintz_decompress(sprintz_ctx *ctx, const void *src, uint64_t src_size,
                        const sprintz_info *info, void *dst, uint64_t dst_cap, void *workspace,
                        uint64_t ws_bytes, void *stream);
 
+/* Compression for callers that cannot allocate device memory.  (The paper has
+ * no counterpart: this is a deployment variant of sprintz_compress.)
+ *
+ * Some callers cannot call cudaMalloc: a process whose own pool allocator has
+ * taken all free device memory, or a serving request path that must not let
+ * cudaMalloc/cudaFree implicitly synchronize the device.  This entry point
+ * needs no context and no workspace: the encoder's scratch (chunk ticket,
+ * look-back words, status word) lives in a fixed 512 KiB array in device
+ * memory that the library defines; every GPU that loads the library holds it
+ * until the process exits.  It allocates nothing and frees nothing.
+ *   - Same arguments, stream bytes and *d_out_size as sprintz_compress() on
+ *     the same input; the current device is used.
+ *   - Limit: at most 65,536 chunks per call (2^26 rows at chunk_rows = 1024),
+ *     and chunks that fit the encoder's shared-memory paths; larger calls
+ *     return SPRINTZ_ERR_WS_TOO_SMALL before anything is enqueued.  Huffman
+ *     returns SPRINTZ_ERR_UNSUPPORTED.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array and each call clears what must start at
+ *     zero; two calls whose work overlaps on the GPU (different streams, or
+ *     different host threads) race and corrupt each other's output.
+ *   - A device-side failure (a bounded wait that gave up) sets *d_out_size to
+ *     0. */
+int sprintz_compress_noalloc(const void *src, uint64_t rows, uint32_t D, uint32_t w,
+                             const sprintz_opts *opts, void *dst, uint64_t dst_cap,
+                             uint64_t *d_out_size, void *stream);
+
 /* Parse a HOST copy of a stream's first n >= 64 bytes. */
 int sprintz_query(const void *host_header, uint64_t n, sprintz_info *out);
 

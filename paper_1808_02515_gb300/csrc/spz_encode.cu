@@ -23,6 +23,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "spz_common.cuh"
 
@@ -931,3 +932,82 @@ int launch_encode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint8
 }
 
 }  // namespace spz
+
+// ---------------------------------------------------------------------------
+// Compression for callers that cannot allocate device memory
+//
+// Some callers cannot call cudaMalloc at all: a process whose own pool
+// allocator has taken all free device memory and must see every allocation,
+// or a request path in a serving system that may not let cudaMalloc/cudaFree
+// implicitly synchronize the device while other streams are running.  For
+// them sprintz_compress_noalloc() runs the same encoder with its scratch (the
+// chunk ticket, the look-back words and a status word) in a fixed array that
+// this library defines in device memory.  Every GPU that loads the library
+// holds the array until the process exits.
+// ---------------------------------------------------------------------------
+
+namespace spz {
+
+constexpr uint64_t kNoAllocMaxChunks = 65536;                        // chunks per call
+constexpr uint64_t kNoAllocStatusOff = 16 + 8 * kNoAllocMaxChunks;   // ticket + look-back words
+constexpr uint64_t kNoAllocBytes = kNoAllocStatusOff + 256;          // + status word, padding
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocDevice {
+  std::once_flag once;
+  int rc = SPRINTZ_OK;
+  uint8_t *ptr = nullptr;  // device address of g_noalloc_scratch on this device
+  LaunchCfg cfg{};
+};
+constexpr int kNoAllocMaxDevices = 64;
+static NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+
+// A device-side failure (a bounded wait that gave up) is reported as size 0.
+__global__ void k_noalloc_finish(const int *status, uint64_t *out_size) {
+  if (*status != 0) *out_size = 0;
+}
+
+}  // namespace spz
+
+extern "C" int sprintz_compress_noalloc(const void *src, uint64_t rows, uint32_t D, uint32_t w,
+                                        const sprintz_opts *opts, void *dst, uint64_t dst_cap,
+                                        uint64_t *d_out_size, void *stream) {
+  using namespace spz;
+  if (!dst || !d_out_size || (rows && !src)) return SPRINTZ_ERR_INVALID_ARG;
+  Geom g;
+  int rc = make_geom(rows, D, w, opts, &g);
+  if (rc != SPRINTZ_OK) return rc;
+  if (opts->huffman) return SPRINTZ_ERR_UNSUPPORTED;
+  if (dst_cap < sprintz_max_compressed_size(rows, D, w, opts)) return SPRINTZ_ERR_DST_TOO_SMALL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return SPRINTZ_ERR_UNSUPPORTED;
+  NoAllocDevice &nd = g_noalloc_dev[dev];
+  // first call on this device (device current): find the array's address
+  std::call_once(nd.once, [&nd, dev] {
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nd.cfg.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nd.cfg.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess) {
+      nd.rc = SPRINTZ_ERR_CUDA;
+      return;
+    }
+    nd.ptr = static_cast<uint8_t *>(ptr);
+  });
+  if (nd.rc != SPRINTZ_OK) return nd.rc;
+  // the fixed array bounds the call: at most kNoAllocMaxChunks chunks, and no
+  // chunk so large that the encoder would need per-block global scratch
+  if (g.n_chunks > kNoAllocMaxChunks || encode_workspace_bytes(g, nd.cfg) > kNoAllocStatusOff)
+    return SPRINTZ_ERR_WS_TOO_SMALL;
+  int *status = reinterpret_cast<int *>(nd.ptr + kNoAllocStatusOff);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  rc = launch_encode(g, nd.cfg, (const uint8_t *)src, (uint8_t *)dst, dst_cap, d_out_size, nd.ptr,
+                     kNoAllocStatusOff, status, s);
+  if (rc != SPRINTZ_OK) return rc;
+  k_noalloc_finish<<<1, 1, 0, s>>>(status, d_out_size);
+  return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
+}
+

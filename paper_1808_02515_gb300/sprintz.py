@@ -90,6 +90,8 @@ def lib() -> ctypes.CDLL:
         L.sprintz_compress.argtypes = [vp, vp, u64, u32, u32, PO, vp, u64, vp, vp, u64, vp]
         L.sprintz_decompress.restype = i32
         L.sprintz_decompress.argtypes = [vp, vp, u64, PI, vp, u64, vp, u64, vp]
+        L.sprintz_compress_noalloc.restype = i32
+        L.sprintz_compress_noalloc.argtypes = [vp, u64, u32, u32, PO, vp, u64, vp, vp]
         L.sprintz_query.restype = i32
         L.sprintz_query.argtypes = [vp, u64, PI]
         L.sprintz_get_status.restype = i32
@@ -151,6 +153,25 @@ def query(header: bytes) -> Info:
 def decompress_workspace_size(info: Info) -> int:
     ci = info.c()
     return int(lib().sprintz_decompress_workspace_size(ctypes.byref(ci)))
+
+
+def compress_noalloc(x, opts: Opts, dst, out_size, stream=None) -> None:
+    """sprintz_compress_noalloc: compress a (rows, D) device tensor into the
+    caller's dst / out_size without any allocation by the library (its scratch
+    is a fixed device array); runs on the current device and torch stream."""
+    import torch
+    if x.dim() == 1:
+        x = x.view(-1, 1)
+    rows, D = x.shape
+    w = 8 if x.dtype == torch.uint8 else 16
+    s = stream if stream is not None else torch.cuda.current_stream()
+    o = opts.c()
+    rc = lib().sprintz_compress_noalloc(ctypes.c_void_p(x.data_ptr() if rows else 0), rows, D, w,
+                                        ctypes.byref(o), ctypes.c_void_p(dst.data_ptr()),
+                                        dst.numel() * dst.element_size(),
+                                        ctypes.c_void_p(out_size.data_ptr()),
+                                        ctypes.c_void_p(s.cuda_stream))
+    _check(rc, "sprintz_compress_noalloc")
 
 
 class Codec:
