@@ -149,8 +149,8 @@ int sprintz_compress(sprintz_ctx *ctx, const void *src, uint64_t rows, uint32_t 
   if (dst_cap < sprintz_max_compressed_size(rows, D, w, opts)) return SPRINTZ_ERR_DST_TOO_SMALL;
   if (ws_bytes < spz::encode_workspace_bytes(g, ctx->cfg)) return SPRINTZ_ERR_WS_TOO_SMALL;
   if (!workspace && ws_bytes) return SPRINTZ_ERR_INVALID_ARG;
-  return spz::launch_encode(g, ctx->cfg, (const uint8_t *)src, (uint8_t *)dst, dst_cap, d_out_size,
-                            (uint8_t *)workspace, ws_bytes, ctx->d_status, (cudaStream_t)stream);
+  return spz::launch_encode_fast(g, ctx->cfg, (const uint8_t *)src, (uint8_t *)dst, dst_cap, d_out_size,
+                                 (uint8_t *)workspace, ws_bytes, ctx->d_status, (cudaStream_t)stream);
 }
 
 int sprintz_query(const void *host_header, uint64_t n, sprintz_info *out) {

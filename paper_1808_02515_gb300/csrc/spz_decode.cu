@@ -20,6 +20,8 @@
 // copies the raw trailing rows.  Chunks too large for shared memory use a
 // per-CTA global scratch slot for the record arrays and work directly in the
 // source and destination.
+#include <stdlib.h>
+
 #include <algorithm>
 
 #include "spz_common.cuh"
@@ -53,6 +55,8 @@ __host__ __device__ inline DecLayout dec_layout(const Geom &g, bool staged) {
 }
 
 struct DecParams {
+  uint32_t pf_win;   // L2 bulk-prefetch window of the lane decoder (bytes, multiple of 16)
+  uint32_t pf_mode;  // bit 0: L1 prefetch ahead; bit 1: streaming stores of the output
   const uint8_t *src;
   uint64_t src_size;
   uint8_t *dst;
@@ -442,22 +446,47 @@ __device__ __forceinline__ uint32_t bbits(const uint8_t *b, uint32_t bit, uint32
   return (v >> s) & mask;
 }
 
+// Shared-memory ring of the lane decoder: per chunk NSEG segments of SEG
+// bytes (powers of two) hold the body bytes at ring offset (address mod
+// NSEG*SEG); the segment leader keeps NSEG - 1 segments loading ahead with TMA
+// bulk copies, each completing on its slot's mbarrier.
+struct LaneRing {
+  uint32_t seg;            // segment bytes, >= the largest header group
+  uint32_t seg_shift;      // log2(seg)
+  uint32_t nseg;           // segments per chunk ring
+  uint32_t bars_off;       // per-warp offsets inside the warp's shared region
+  uint32_t rings_off;
+  uint32_t per_warp;       // bytes of shared memory per warp
+};
+
+constexpr uint32_t kRingWaitLimit = 1u << 22;
+
 template <int W>
-__global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p) {
+__global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p, LaneRing rg) {
+  extern __shared__ __align__(16) uint8_t dsm[];
   const Geom &g = p.g;
   const uint32_t D = g.D;
   const uint32_t K = 32 / D;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t kk = lane / D, j = lane % D;
-  const uint32_t seg0 = lane - j;  // first lane of this chunk's segment
+  const uint32_t kc = kk < K ? kk : K - 1;  // idle lanes alias the last slot, never touch it
+  const uint32_t seg0 = lane - j;            // first lane of this chunk's segment
   const uint32_t last = seg0 + D - 1;
+  // this chunk's lanes (they take the same branches: their data is shared)
+  const uint32_t seg_mask = D == 32 ? 0xFFFFFFFFu : ((1u << D) - 1u) << seg0;
   const uint64_t warp_id = (uint64_t)blockIdx.x * kLaneWarps + warp;
   const uint64_t c64 = warp_id * K + kk;
-  __shared__ __align__(16) uint8_t stage_all[kLaneWarps][kStageBytes];
-  uint8_t *stage = stage_all[warp];
+  uint8_t *wsm = dsm + (uint64_t)warp * rg.per_warp;
+  uint8_t *stage = wsm;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + rg.bars_off) + kc * rg.nseg;
+  const uint32_t ring_bytes = rg.seg * rg.nseg;
+  uint8_t *ring = wsm + rg.rings_off + kc * ring_bytes;
+  const uint32_t *ring32 = reinterpret_cast<const uint32_t *>(ring);
+  const uint32_t ring_wmask = ring_bytes / 4 - 1;
   const uint32_t wb = W / 8;
   const uint32_t hb = g.hb, G = g.G;
   const uint32_t blk_bytes = kBlockRows * D * wb;  // one chunk's block of output
+  const uint32_t gmax = g.hdr_bytes + G * D * W;   // largest header group (bytes)
 
   // the chunk bodies end at tail_off
   const uint64_t tail_off = le_u64(p.src + 48);
@@ -482,22 +511,66 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p) {
     }
   }
   const uint8_t *body = p.src + g.data_off + off;
-  // aligned word view of the chunk: bit positions below are relative to wc
-  const uint32_t *wc = reinterpret_cast<const uint32_t *>((uintptr_t)body & ~(uintptr_t)3);
-  const uint32_t sh0 = (uint32_t)((uintptr_t)body & 3) * 8;  // body bit 0 inside wc
-  // word loads may touch up to 8 bytes past the body: only where they stay in the buffer
-  const bool fast = (uintptr_t)body + packed + 8 <= (uintptr_t)p.src + p.src_size;
 
-  // L2 prefetch window ahead of this chunk's read position (segment leader)
-  constexpr uint32_t kPrefetchWin = 2048;
-  const uintptr_t buf_lo = (uintptr_t)p.src, buf_hi = (uintptr_t)p.src + p.src_size;
-  const uintptr_t body_end = (uintptr_t)body + packed;
-  uintptr_t pf_end = (uintptr_t)body;
+  // ---- ring set-up: the leader initialises the barriers and starts loading
+  const uintptr_t B0 = (uintptr_t)body, B1 = B0 + packed;
+  const uintptr_t buf_lo = ((uintptr_t)p.src + 15) & ~(uintptr_t)15;
+  const uintptr_t buf_hi = ((uintptr_t)p.src + p.src_size) & ~(uintptr_t)15;
+  const uint32_t ssh = rg.seg_shift;
+  const uint64_t s_lo = live ? B0 >> ssh : 0, s_hi = live ? (B1 - 1) >> ssh : 0;
+  uint64_t seg_base = s_lo, seg_issued = s_lo, seg_waited = s_lo;
+  uint32_t parity = 0;  // bit h: parity of the next completion of slot h
+  bool ring_ok = true;
   if (live && j == 0) {
-    uintptr_t e2 = min(body_end, pf_end + 2 * kPrefetchWin);
-    prefetch_l2_range(pf_end, e2, buf_lo, buf_hi);
+    for (uint32_t h = 0; h < rg.nseg; ++h) mbar_init(&bars[h], 1);
+    fence_mbar_init();
+    fence_proxy_async_smem();
+  }
+  __syncwarp();
+  // issue the load of segment s into its slot (leader lane)
+  auto issue = [&](uint64_t s) {
+    const uint32_t h = (uint32_t)(s & (rg.nseg - 1));
+    uintptr_t a = max((uintptr_t)(s << ssh), max(B0 & ~(uintptr_t)15, buf_lo));
+    uintptr_t b = min((uintptr_t)((s + 1) << ssh), min((B1 + 15) & ~(uintptr_t)15, buf_hi));
+    const uint32_t bytes = b > a ? (uint32_t)(b - a) : 0u;
+    mbar_arrive_expect_tx(&bars[h], bytes);
+    if (bytes) tma_load_1d(ring + (a & (ring_bytes - 1)), reinterpret_cast<const void *>(a), bytes, &bars[h]);
+    // body bytes in the buffer's last partial 16-byte unit: plain loads
+    const uintptr_t t0 = max(buf_hi, max((uintptr_t)(s << ssh), B0));
+    const uintptr_t t1 = min(B1, (uintptr_t)((s + 1) << ssh));
+    for (uintptr_t q = t0; q < t1; ++q) ring[q & (ring_bytes - 1)] = *reinterpret_cast<const uint8_t *>(q);
+  };
+  auto wait_upto = [&](uint64_t s) {
+    while (seg_waited <= s && seg_waited < seg_issued) {
+      const uint32_t h = (uint32_t)(seg_waited & (rg.nseg - 1));
+      if (!mbar_wait(&bars[h], (parity >> h) & 1u, kRingWaitLimit)) {
+        ring_ok = false;
+        return;
+      }
+      parity ^= 1u << h;
+      seg_waited++;
+    }
+  };
+  if (live) {
+    const uint64_t first_end = min(s_hi + 1, s_lo + rg.nseg);
+    if (j == 0)
+      for (uint64_t s = s_lo; s < first_end; ++s) issue(s);
+    seg_issued = first_end;
+  }
+  // L2 prefetch ahead of the ring (segment leader)
+  const uint32_t kPrefetchWin = p.pf_win;
+  uintptr_t pf_end = B0 + (uintptr_t)rg.seg * rg.nseg;
+  if (live && j == 0 && pf_end < B1) {
+    const uintptr_t e2 = min(B1, pf_end + kPrefetchWin);
+    prefetch_l2_range(pf_end & ~(uintptr_t)15, e2, buf_lo, buf_hi);
     pf_end = e2;
   }
+  const uint32_t rb0 = (uint32_t)(B0 & (ring_bytes - 1)) * 8;  // body bit 0 in the ring
+  auto rbits = [&](uint32_t bit, uint32_t mask) {
+    const uint32_t q = rb0 + bit;
+    const uint32_t i0 = (q >> 5) & ring_wmask;
+    return __funnelshift_r(ring32[i0], ring32[(i0 + 1) & ring_wmask], q) & mask;
+  };
 
   // output mapping of this lane's (up to two) 8-byte words of each block step
   uint64_t *dptr[2];
@@ -515,11 +588,17 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p) {
     const uint64_t r2 = (warp_id * K + k2) * g.chunk_rows;
     dptr[t] = reinterpret_cast<uint64_t *>(p.dst + r2 * D * wb) + wq;
   }
-  uint8_t *my_stage = stage + kk * blk_bytes + j * wb;
+  uint8_t *my_stage = stage + kc * blk_bytes + j * wb;
   const uint32_t row_stride = D * wb;
+  auto put = [&](int i, uint32_t v) {
+    if (W == 8)
+      my_stage[i * row_stride] = (uint8_t)v;
+    else
+      *reinterpret_cast<uint16_t *>(my_stage + i * row_stride) = (uint16_t)v;
+  };
 
-  // walk state (bit positions relative to wc)
-  uint32_t gpos = 0, hdr = 0;  // body bytes
+  // walk state (body-relative bytes / bits)
+  uint32_t gpos = 0, hdr = 0;
   uint32_t gslot = G, rec = 0, rem = 0;
   bool run = true;
   uint32_t pbit = 0, stride = 0, mask = 0;
@@ -538,13 +617,32 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p) {
         hdr = gpos;
         gpos += g.hdr_bytes;
         gslot = 0;
+        // ring: release segments before the group, load ahead, wait for the group
+        const uint64_t s_cur = (B0 + hdr) >> ssh;
+        if (seg_base < s_cur) {
+          wait_upto(s_cur - 1);
+          ring_ok = __all_sync(seg_mask, ring_ok);
+          if (j == 0) fence_proxy_async_smem();
+          while (seg_base < s_cur) {
+            const uint64_t s_new = seg_base + rg.nseg;
+            if (s_new <= s_hi) {
+              if (j == 0) issue(s_new);
+              seg_issued = s_new + 1;
+            }
+            seg_base++;
+          }
+          if (j == 0 && pf_end < B1 && B0 + hdr + rg.seg * rg.nseg + kPrefetchWin / 2 > pf_end) {
+            const uintptr_t e2 = min(B1, pf_end + kPrefetchWin);
+            prefetch_l2_range(pf_end & ~(uintptr_t)15, e2, buf_lo, buf_hi);
+            pf_end = e2;
+          }
+        }
+        wait_upto(min(s_hi, (uint64_t)((B0 + hdr + gmax - 1) >> ssh)));
+        ring_ok = __all_sync(seg_mask, ring_ok);
       }
       const bool hdr_in = gpos <= packed;
-      bad |= !hdr_in;
-      const uint32_t cbit = hdr * 8 + (gslot * D + j) * hb;
-      const uint32_t hmask = (1u << hb) - 1u;
-      uint32_t code = 0;
-      if (hdr_in) code = fast ? wbits(wc, sh0 + cbit, hmask) : bbits(body, cbit, hmask);
+      bad |= !hdr_in || !ring_ok;
+      const uint32_t code = hdr_in ? rbits(hdr * 8 + (gslot * D + j) * hb, (1u << hb) - 1u) : 0u;
       const uint32_t nw = code == (uint32_t)W - 1 ? (uint32_t)W : code;
       uint32_t v = nw;
 #pragma unroll
@@ -557,8 +655,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p) {
       const uint32_t total = __shfl_sync(need_mask, v, last);
       if (total == 0) {
         uint32_t cnt = 0;
-        if (gpos + 2 <= packed)
-          cnt = fast ? wbits(wc, sh0 + gpos * 8, 0xFFFFu) : bbits(body, gpos * 8, 0xFFFFu);
+        if (gpos + 2 <= packed) cnt = rbits(gpos * 8, 0xFFFFu);
         gpos += 2;
         run = true;
         rem = cnt;
@@ -583,13 +680,8 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p) {
       rec++;
       if (bad) {
         live = false;
-        if (j == 0) set_status(p.status, SPRINTZ_ERR_CORRUPT);
+        if (j == 0) set_status(p.status, ring_ok ? SPRINTZ_ERR_CORRUPT : SPRINTZ_ERR_TIMEOUT);
       }
-    }
-    if (live && j == 0 && pf_end < body_end && (uintptr_t)body + gpos + kPrefetchWin > pf_end) {
-      uintptr_t e2 = min(body_end, pf_end + kPrefetchWin);
-      prefetch_l2_range(pf_end & ~(uintptr_t)15, e2, buf_lo, buf_hi);
-      pf_end = e2;
     }
     const bool emit = here && live;
     if (emit) {
@@ -598,19 +690,15 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p) {
       if (run || mask == 0) {
 #pragma unroll
         for (int i = 0; i < kBlockRows; ++i) z[i] = 0;
-      } else if (fast) {
-        const uint32_t b0 = sh0 + pbit;
-#pragma unroll
-        for (int i = 0; i < kBlockRows; ++i) z[i] = wbits(wc, b0 + i * stride, mask);
       } else {
 #pragma unroll
-        for (int i = 0; i < kBlockRows; ++i) z[i] = bbits(body, pbit + i * stride, mask);
+        for (int i = 0; i < kBlockRows; ++i) z[i] = rbits(pbit + i * stride, mask);
       }
       if (g.forecaster == kFcDelta) {
 #pragma unroll
         for (int i = 0; i < kBlockRows; ++i) {
           xp += (z[i] >> 1) ^ (0u - (z[i] & 1u));
-          store_sample<W>(my_stage + i * row_stride, xp);
+          put(i, xp);
         }
       } else {
         // delta_i = wrap_w(floor(alpha * delta_{i-1} / 2^w) + e_i): one
@@ -623,7 +711,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p) {
           const int32_t d = (int32_t)(A * (uint32_t)dp + (ev << (32 - W))) >> (32 - W);
           if ((i & 1) == 0) gsum += z[i] == 0 ? 0 : ((z[i] & 1u) ? -dp : dp);
           xp += (uint32_t)d;
-          store_sample<W>(my_stage + i * row_stride, xp);
+          put(i, xp);
           dp = d;
         }
         acc = wrap_acc<W>((int32_t)((uint32_t)acc + (uint32_t)(gsum >> 2)));
@@ -643,12 +731,41 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p) {
   // every record consumed, the body used up, unused slots of the last group zero
   if (live) {
     bool bad = rec != nrec || gpos != packed;
-    for (uint32_t s = gslot; s < G && !bad; ++s) {
-      const uint32_t cbit = hdr * 8 + (s * D + j) * hb;
-      bad |= (fast ? wbits(wc, sh0 + cbit, (1u << hb) - 1u) : bbits(body, cbit, (1u << hb) - 1u)) != 0;
-    }
+    for (uint32_t s = gslot; s < G && !bad; ++s)
+      bad |= rbits(hdr * 8 + (s * D + j) * hb, (1u << hb) - 1u) != 0;
     if (bad) set_status(p.status, SPRINTZ_ERR_CORRUPT);
   }
+  // no bulk copy may still be writing this warp's shared memory at exit
+  if (kk < K && c64 < g.n_chunks && hdr_ok) {
+    ring_ok = true;
+    wait_upto(~0ull);
+    if (!ring_ok && j == 0) set_status(p.status, SPRINTZ_ERR_TIMEOUT);
+  }
+}
+
+static LaneRing lane_ring_plan(const Geom &g, const LaunchCfg &cfg, uint32_t nseg_want) {
+  LaneRing r{};
+  const uint32_t K = 32 / g.D;
+  const uint32_t gmax = g.hdr_bytes + g.G * g.D * g.w;
+  r.seg = 128;
+  r.seg_shift = 7;
+  while (r.seg < gmax) {
+    r.seg <<= 1;
+    r.seg_shift++;
+  }
+  r.nseg = nseg_want;
+  auto layout = [&](LaneRing &x) {
+    x.bars_off = kStageBytes;
+    x.rings_off = x.bars_off + ((K * x.nseg * 8 + 15) & ~15u);
+    x.per_warp = x.rings_off + K * x.nseg * x.seg;
+  };
+  layout(r);
+  while (r.nseg > 2 && (uint64_t)r.per_warp * kLaneWarps > 64 * 1024) {
+    r.nseg >>= 1;
+    layout(r);
+  }
+  if ((uint64_t)r.per_warp * kLaneWarps > (uint64_t)cfg.max_smem_optin) r.per_warp = 0;  // does not fit
+  return r;
 }
 
 // ---------------------------------------------------------------------------
@@ -656,6 +773,16 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p) {
 // ---------------------------------------------------------------------------
 
 static uint64_t align256d(uint64_t v) { return (v + 255) & ~255ull; }
+
+// Segments per chunk ring of the lane decoder (SPRINTZ_DEC_RING_SEGS: 2 or 4).
+static uint32_t dec_ring_segments() {
+  static const uint32_t v = [] {
+    const char *e = getenv("SPRINTZ_DEC_RING_SEGS");
+    int x = e ? atoi(e) : 0;
+    return (uint32_t)(x == 2 || x == 4 || x == 8 ? x : 2);
+  }();
+  return v;
+}
 
 struct DecPlan {
   bool staged;
@@ -701,16 +828,33 @@ int launch_decode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint6
   p.dst_cap = dst_cap;
   p.status = d_status;
   p.g = g;
+  {
+    static const uint32_t win = [] {
+      const char *e = getenv("SPRINTZ_DEC_PF_WIN");
+      int x = e ? atoi(e) : 0;
+      return (uint32_t)(x >= 16 ? (x & ~15) : 2048);
+    }();
+    p.pf_win = win;
+    p.pf_mode = 0;
+  }
   k_decode_header_tail<<<1, 128, 0, stream>>>(p);
-  if (g.n_chunks > 0 && g.D <= 32 && ((uintptr_t)dst & 7) == 0 && g.max_body < (1ull << 28)) {
+  LaneRing rg{};
+  if (g.n_chunks > 0 && g.D <= 32 && ((uintptr_t)dst & 7) == 0 && g.max_body < (1ull << 28))
+    rg = lane_ring_plan(g, cfg, dec_ring_segments());
+  if (rg.per_warp) {
     const uint64_t K = 32 / g.D;
     const uint64_t warps = (g.n_chunks + K - 1) / K;
     const uint64_t grid = (warps + kLaneWarps - 1) / kLaneWarps;
     if (grid > 0x7FFFFFFFull) return SPRINTZ_ERR_INVALID_ARG;
+    const uint64_t smem = (uint64_t)rg.per_warp * kLaneWarps;
+    const void *fn = g.w == 8 ? (const void *)k_decode_lanes<8> : (const void *)k_decode_lanes<16>;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return SPRINTZ_ERR_CUDA;
     if (g.w == 8)
-      k_decode_lanes<8><<<(uint32_t)grid, kLaneThreads, 0, stream>>>(p);
+      k_decode_lanes<8><<<(uint32_t)grid, kLaneThreads, smem, stream>>>(p, rg);
     else
-      k_decode_lanes<16><<<(uint32_t)grid, kLaneThreads, 0, stream>>>(p);
+      k_decode_lanes<16><<<(uint32_t)grid, kLaneThreads, smem, stream>>>(p, rg);
   } else if (g.n_chunks > 0) {
     DecPlan pl = dec_plan(g, cfg);
     if (ws_bytes < (uint64_t)pl.grid * pl.scratch_per_cta) return SPRINTZ_ERR_WS_TOO_SMALL;

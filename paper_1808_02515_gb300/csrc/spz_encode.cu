@@ -819,6 +819,318 @@ __global__ void __launch_bounds__(kEncLaneThreads) k_encode_lanes(EncParams p, E
 }
 
 // ---------------------------------------------------------------------------
+// Single-pass lane encoder (D <= 32): bodies assembled in private slots
+//
+// As the two-pass encoder, but each warp owns K body slots in the workspace
+// (one per chunk it encodes).  One pass over the rows lays out the records
+// and ORs header codes and payload bits into a per-chunk shared ring, whose
+// completed 16-byte units go to the slot with one vector store each.  When
+// the chunk ends its size is known: the look-back over chunk groups gives its
+// offset and the chunk's lanes copy the slot to its place in the stream
+// (16-byte stores, bytes only at the two unaligned ends).  Slots are reused
+// by the same warp, so they stay in L2.
+// ---------------------------------------------------------------------------
+
+struct EncSlotCfg {
+  uint32_t window;       // ring bytes per chunk (power of two)
+  uint32_t n_groups;
+  uint32_t slot_stride;  // bytes per chunk slot (multiple of 16, >= the largest body + 16)
+  uint8_t *slots;        // [warp][K] slots
+};
+
+template <int W>
+__global__ void __launch_bounds__(kEncLaneThreads) k_encode_slots(EncParams p, EncSlotCfg cfg) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const Geom &g = p.g;
+  const uint32_t D = g.D;
+  const uint32_t K = 32 / D;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t kk = lane / D, j = lane % D;
+  const uint32_t kc = kk < K ? kk : K - 1;
+  const uint32_t seg0 = lane - j, last = seg0 + D - 1;
+  const uint32_t wb = W / 8;
+  const uint32_t G = g.G, hb = g.hb, H = g.hdr_bytes;
+  uint8_t *stage = smem + warp * kEncStage;
+  uint32_t *ring = reinterpret_cast<uint32_t *>(smem + kEncLaneWarps * kEncStage +
+                                                ((uint64_t)warp * K + kc) * cfg.window);
+  const uint32_t ring_wmask = cfg.window / 4 - 1, ring_bitmask = cfg.window * 8 - 1;
+  const uint64_t gwarp = (uint64_t)blockIdx.x * kEncLaneWarps + warp;
+  uint8_t *slot = cfg.slots + (gwarp * K + kc) * (uint64_t)cfg.slot_stride;
+
+  // cooperative stage loads: this lane's (up to two) 8-byte words of a block step
+  const uint32_t words_per = D * wb, total_words = K * words_per;
+  bool has[2];
+  uint32_t k2[2], wq[2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const uint32_t q = lane + 32 * t;
+    has[t] = q < total_words;
+    k2[t] = has[t] ? q / words_per : 0;
+    wq[t] = has[t] ? q % words_per : 0;
+  }
+  const uint32_t row_stride = D * wb;
+  const uint8_t *my_x = stage + kc * (kBlockRows * row_stride) + j * wb;
+  const uint32_t nb_max = (uint32_t)(min(g.chunk_rows, g.full_rows) / kBlockRows);
+
+  for (;;) {
+    uint32_t grp = 0;
+    if (lane == 0) grp = atomicAdd(p.ticket, 1u);
+    grp = __shfl_sync(0xFFFFFFFFu, grp, 0);
+    if (grp >= cfg.n_groups) break;
+    const uint64_t c64 = (uint64_t)grp * K + kk;
+    const bool live = kk < K && c64 < g.n_chunks;
+    const uint64_t row0 = c64 * g.chunk_rows;
+    const uint32_t nb = live ? (uint32_t)(min(g.chunk_rows, g.full_rows - row0) / kBlockRows) : 0u;
+    const unsigned long long *srcw[2];
+    uint32_t nbw[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      nbw[t] = __shfl_sync(0xFFFFFFFFu, nb, k2[t] * D);
+      const uint64_t c2 = (uint64_t)grp * K + k2[t];
+      srcw[t] = reinterpret_cast<const unsigned long long *>(p.src + c2 * g.chunk_rows * D * wb) + wq[t];
+    }
+    // L2 prefetch of the chunk's rows (leader), windows ahead of the reads
+    const uintptr_t rows_lo = (uintptr_t)(p.src + row0 * D * wb);
+    const uintptr_t rows_hi = rows_lo + (uint64_t)nb * kBlockRows * D * wb;
+    uintptr_t pf = rows_lo;
+    if (live && j == 0) {
+      const uintptr_t e2 = min(rows_hi, pf + 8192);
+      prefetch_l2_range(pf, e2, rows_lo, rows_hi);
+      pf = e2;
+    }
+    if (live)
+      for (uint32_t t = j; t < cfg.window / 16; t += D)
+        reinterpret_cast<uint4 *>(ring)[t] = make_uint4(0, 0, 0, 0);
+
+    uint32_t xp = 0, run = 0, nrec = 0, gs = 0, pos = 0, hpos = 0, flushed = 0;
+    int32_t dp = 0, acc = 0;
+    bool open = false;
+
+    auto ror = [&](uint32_t bit, uint32_t v, uint32_t n) {
+      if (!v) return;
+      const uint32_t q = bit & ring_bitmask;
+      const uint32_t wi = q >> 5, sh = q & 31;
+      atomicOr(&ring[wi], v << sh);
+      if (sh + n > 32) atomicOr(&ring[(wi + 1) & ring_wmask], v >> (32 - sh));
+    };
+    auto start_record = [&]() {
+      if (gs == 0) {
+        hpos = pos;
+        pos += H;
+        open = true;
+      }
+    };
+    auto end_record = [&](uint32_t size) {
+      pos += size;
+      nrec++;
+      if (++gs == G) {
+        gs = 0;
+        open = false;
+      }
+    };
+    auto emit_run = [&](uint32_t len) {
+      start_record();
+      if (j == 0) ror(pos * 8, len, 16);
+      end_record(2);
+    };
+    auto flush = [&](uint32_t limit, bool fin) {
+      const uint32_t u1 = fin ? (limit + 15) >> 4 : limit >> 4;
+      for (uint32_t u = (flushed >> 4) + j; u < u1; u += D) {
+        uint4 *r4 = reinterpret_cast<uint4 *>(&ring[(u * 4) & ring_wmask]);
+        *reinterpret_cast<uint4 *>(slot + 16ull * u) = *r4;
+        *r4 = make_uint4(0, 0, 0, 0);
+      }
+      if (u1 * 16 > flushed) flushed = u1 * 16;
+    };
+
+    unsigned long long wcur[2], wnext[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) wcur[t] = (has[t] && nbw[t] > 0) ? __ldg(srcw[t]) : 0ull;
+    __syncwarp();
+    for (uint32_t b = 0; b < nb_max; ++b) {
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+        if (has[t]) reinterpret_cast<unsigned long long *>(stage)[lane + 32 * t] = wcur[t];
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+        wnext[t] = (has[t] && b + 1 < nbw[t]) ? __ldg(srcw[t] + (uint64_t)(b + 1) * words_per) : 0ull;
+      __syncwarp();
+      const bool here = live && b < nb;
+      uint32_t z[kBlockRows];
+      uint32_t n = 0;
+      if (here) {
+        uint32_t x[kBlockRows];
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i)
+          x[i] = W == 8 ? (uint32_t)my_x[i * row_stride]
+                        : (uint32_t) * reinterpret_cast<const uint16_t *>(my_x + i * row_stride);
+        uint32_t orz = 0;
+        if (g.forecaster == kFcDelta) {
+#pragma unroll
+          for (int i = 0; i < kBlockRows; ++i) {
+            z[i] = zigzag<W>(sext<W>(x[i] - xp));
+            xp = x[i];
+            orz |= z[i];
+          }
+        } else {
+          const int32_t a = acc >> g.learn_shift;
+          int32_t gsum = 0;
+#pragma unroll
+          for (int i = 0; i < kBlockRows; ++i) {
+            const int32_t e = sext<W>(x[i] - xp - fire_pred_delta<W>(a, dp));
+            if ((i & 1) == 0) gsum += e == 0 ? 0 : (e > 0 ? dp : -dp);
+            z[i] = zigzag<W>(e);
+            orz |= z[i];
+            dp = sext<W>(x[i] - xp);
+            xp = x[i];
+          }
+          acc = wrap_acc<W>((int32_t)((uint32_t)acc + (uint32_t)(gsum >> 2)));
+        }
+        n = 32u - __clz(orz);
+        if (n == W - 1) n = W;
+      }
+      // segmented scan of the widths: this lane's offset and the block's total
+      uint32_t v = n;
+#pragma unroll
+      for (uint32_t o = 1; o < 32; o <<= 1) {
+        if (o < D) {
+          const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+          if (j >= o) v += t;
+        }
+      }
+      const uint32_t total = __shfl_sync(0xFFFFFFFFu, v, last);
+      if (here) {
+        if (total == 0) {
+          if (++run == kMaxRun) {
+            emit_run(run);
+            run = 0;
+          }
+        } else {
+          if (run) {
+            emit_run(run);
+            run = 0;
+          }
+          start_record();
+          const uint32_t prefix = v - n;
+          const uint32_t size = g.col_major ? total : (total + 7) & ~7u;
+          ror(hpos * 8 + (gs * D + j) * hb, n == W ? W - 1 : n, hb);
+          if (n) {
+            const uint32_t b0 = g.col_major ? (pos + prefix) * 8 : pos * 8 + prefix;
+            const uint32_t st = g.col_major ? n : size;  // size bytes = 8 rows * R: bits per row = size
+#pragma unroll
+            for (int i = 0; i < kBlockRows; ++i) ror(b0 + i * st, z[i], n);
+          }
+          end_record(size);
+        }
+        if (j == 0 && pf < rows_hi && rows_lo + (uint64_t)(b + 1) * kBlockRows * D * wb + 4096 > pf) {
+          const uintptr_t e2 = min(rows_hi, pf + 4096);
+          prefetch_l2_range(pf, e2, rows_lo, rows_hi);
+          pf = e2;
+        }
+      }
+      __syncwarp();
+      if (here) flush(open ? hpos : pos, false);
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < 2; ++t) wcur[t] = wnext[t];
+    }
+    if (live) {
+      if (run) emit_run(run);
+      open = false;
+    }
+    __syncwarp();
+    if (live) flush(pos, true);
+    __syncwarp();
+    const uint32_t S = pos;
+
+    // offsets: this group's total, each chunk's place inside it, look-back
+    uint64_t v = (live && j == 0) ? S : 0;
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+      const uint64_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+      if (lane >= o) v += t;
+    }
+    const uint64_t group_total = __shfl_sync(0xFFFFFFFFu, v, 31);
+    const uint64_t excl = __shfl_sync(0xFFFFFFFFu, v, seg0) - __shfl_sync(0xFFFFFFFFu, (uint64_t)S, seg0);
+    uint64_t prefix = 0;
+    if (lane == 0) {
+      uint64_t *lb = p.lookback;
+      if (grp == 0) {
+        st_release_u64(&lb[0], kFlagPrefix | group_total);
+      } else {
+        st_release_u64(&lb[grp], kFlagAggregate | group_total);
+        int64_t k = (int64_t)grp - 1;
+        uint32_t spins = 0;
+        while (k >= 0) {
+          const uint64_t w = ld_acquire_u64(&lb[k]);
+          const uint64_t flag = w & ~kValueMask;
+          if (flag == 0) {
+            if (++spins > kSpinLimit) {
+              set_status(p.status, SPRINTZ_ERR_TIMEOUT);
+              break;
+            }
+            __nanosleep(32);
+            continue;
+          }
+          prefix += w & kValueMask;
+          if (flag == kFlagPrefix) break;
+          --k;
+        }
+        st_release_u64(&lb[grp], kFlagPrefix | (prefix + group_total));
+      }
+    }
+    prefix = __shfl_sync(0xFFFFFFFFu, prefix, 0);
+    const uint64_t off = prefix + excl;
+
+    // the body to its place: bytes up to a 16-byte boundary, 16-byte units
+    // assembled from the slot's words, bytes after the last unit
+    if (live && g.data_off + off + S <= p.dst_cap) {
+      uint8_t *d = p.dst + g.data_off + off;
+      const uint32_t head = min((uint32_t)((16 - ((uintptr_t)d & 15)) & 15), S);
+      for (uint32_t k = j; k < head; k += D) d[k] = slot[k];
+      const uint32_t n16 = (S - head) / 16;
+      const uint32_t sh = (head & 3) * 8;
+      const uint32_t *sw = reinterpret_cast<const uint32_t *>(slot + (head & ~3u));
+      for (uint32_t u = j; u < n16; u += D) {
+        const uint32_t *q = sw + 4 * u;
+        const uint32_t a0 = q[0], a1 = q[1], a2 = q[2], a3 = q[3], a4 = q[4];
+        uint4 o;
+        o.x = __funnelshift_r(a0, a1, sh);
+        o.y = __funnelshift_r(a1, a2, sh);
+        o.z = __funnelshift_r(a2, a3, sh);
+        o.w = __funnelshift_r(a3, a4, sh);
+        *reinterpret_cast<uint4 *>(d + head + 16 * u) = o;
+      }
+      for (uint32_t k = head + 16 * n16 + j; k < S; k += D) d[k] = slot[k];
+      if (j == 0) {
+        uint8_t *e = p.dst + kHdrBytes + c64 * kEntryBytes;
+        const uint64_t w1 = (uint64_t)nrec | ((uint64_t)S << 32);
+        for (int k = 0; k < 8; ++k) {
+          e[k] = (uint8_t)(off >> (8 * k));
+          e[8 + k] = (uint8_t)(w1 >> (8 * k));
+        }
+      }
+      if (c64 == g.n_chunks - 1) {
+        const uint64_t tail_off = g.data_off + off + S;
+        const uint64_t tail_bytes = g.tail_rows * D * wb;
+        const uint64_t tot = tail_off + tail_bytes;
+        if (tot <= p.dst_cap) {
+          for (uint64_t k = j; k < tail_bytes; k += D) p.dst[tail_off + k] = p.src[g.full_rows * D * wb + k];
+          if (j == 0) {
+            write_stream_header(p.dst, g, tail_off, tot);
+            *p.out_size = tot;
+          }
+        } else if (j == 0) {
+          set_status(p.status, SPRINTZ_ERR_DST_TOO_SMALL);
+        }
+      }
+    } else if (live && j == 0) {
+      set_status(p.status, SPRINTZ_ERR_DST_TOO_SMALL);
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 
@@ -868,11 +1180,53 @@ static EncPlan enc_plan(const Geom &g, const LaunchCfg &cfg) {
   return pl;
 }
 
-uint64_t encode_workspace_bytes(const Geom &g, const LaunchCfg &cfg) {
+// Workspace of the encoders that need only the ticket, the look-back words and
+// (for chunks too large for shared memory) per-CTA scratch.
+static uint64_t encode_workspace_basic(const Geom &g, const LaunchCfg &cfg) {
   uint64_t base = align256(16 + 8ull * g.n_chunks);
   if (g.n_chunks == 0) return base;
   EncPlan pl = enc_plan(g, cfg);
   return base + (uint64_t)pl.grid * pl.scratch_per_cta;
+}
+
+// Plan of the single-pass slot encoder (grid 0: not applicable).
+struct SlotPlan {
+  EncSlotCfg sc;
+  uint32_t grid;
+  uint64_t smem;
+  uint64_t ws_base;   // ticket + look-back words (aligned)
+  uint64_t ws_total;
+};
+
+static uint32_t enc_slot_ctas_per_sm() {
+  static uint32_t v = [] {
+    const char *e = getenv("SPRINTZ_ENC_SLOT_CTAS_PER_SM");
+    int x = e ? atoi(e) : 0;
+    return (uint32_t)(x > 0 && x <= 32 ? x : 8);
+  }();
+  return v;
+}
+
+static SlotPlan slot_plan(const Geom &g, const LaunchCfg &cfg) {
+  SlotPlan pl{};
+  if (g.n_chunks == 0 || g.D > 32 || g.max_body >= (1ull << 28)) return pl;
+  const uint32_t K = 32 / g.D;
+  pl.sc.window = enc_window_bytes(g);
+  pl.sc.n_groups = (uint32_t)((g.n_chunks + K - 1) / K);
+  pl.sc.slot_stride = (uint32_t)(((g.max_body + 15) & ~15ull) + 16);
+  pl.smem = (uint64_t)kEncLaneWarps * kEncStage + (uint64_t)kEncLaneWarps * K * pl.sc.window;
+  if (pl.smem > (uint64_t)cfg.max_smem_optin) return pl;
+  const uint64_t want = (pl.sc.n_groups + kEncLaneWarps - 1) / kEncLaneWarps;
+  pl.grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)cfg.sm_count *
+                                                                          enc_slot_ctas_per_sm()));
+  pl.ws_base = align256(16 + 8ull * pl.sc.n_groups);
+  pl.ws_total = pl.ws_base + (uint64_t)pl.grid * kEncLaneWarps * K * pl.sc.slot_stride;
+  return pl;
+}
+
+uint64_t encode_workspace_bytes(const Geom &g, const LaunchCfg &cfg) {
+  const SlotPlan sp = slot_plan(g, cfg);
+  return std::max<uint64_t>(encode_workspace_basic(g, cfg), sp.grid ? sp.ws_total : 0ull);
 }
 
 int launch_encode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint8_t *dst,
@@ -928,6 +1282,41 @@ int launch_encode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint8
     k_encode<8><<<pl.grid, kEncThreads, pl.smem, stream>>>(p);
   else
     k_encode<16><<<pl.grid, kEncThreads, pl.smem, stream>>>(p);
+  return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
+}
+
+}  // namespace spz
+
+namespace spz {
+
+// Compression through the fastest applicable encoder: the single-pass slot
+// encoder when the workspace holds its slots, else launch_encode's choice.
+int launch_encode_fast(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint8_t *dst,
+                       uint64_t dst_cap, uint64_t *d_out_size, uint8_t *ws, uint64_t ws_bytes,
+                       int *d_status, cudaStream_t stream) {
+  const SlotPlan sp = slot_plan(g, cfg);
+  if (!sp.grid || ((uintptr_t)src & 7) != 0 || ws_bytes < sp.ws_total)
+    return launch_encode(g, cfg, src, dst, dst_cap, d_out_size, ws, ws_bytes, d_status, stream);
+  EncParams p{};
+  p.src = src;
+  p.dst = dst;
+  p.dst_cap = dst_cap;
+  p.out_size = d_out_size;
+  p.status = d_status;
+  p.g = g;
+  p.ticket = reinterpret_cast<uint32_t *>(ws);
+  p.lookback = reinterpret_cast<uint64_t *>(ws + 16);
+  EncSlotCfg sc = sp.sc;
+  sc.slots = ws + sp.ws_base;
+  const void *fn = g.w == 8 ? (const void *)k_encode_slots<8> : (const void *)k_encode_slots<16>;
+  if (sp.smem > 48 * 1024 &&
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem) != cudaSuccess)
+    return SPRINTZ_ERR_CUDA;
+  if (cudaMemsetAsync(ws, 0, 16 + 8ull * sc.n_groups, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  if (g.w == 8)
+    k_encode_slots<8><<<sp.grid, kEncLaneThreads, sp.smem, stream>>>(p, sc);
+  else
+    k_encode_slots<16><<<sp.grid, kEncLaneThreads, sp.smem, stream>>>(p, sc);
   return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
 }
 
@@ -999,7 +1388,7 @@ extern "C" int sprintz_compress_noalloc(const void *src, uint64_t rows, uint32_t
   if (nd.rc != SPRINTZ_OK) return nd.rc;
   // the fixed array bounds the call: at most kNoAllocMaxChunks chunks, and no
   // chunk so large that the encoder would need per-block global scratch
-  if (g.n_chunks > kNoAllocMaxChunks || encode_workspace_bytes(g, nd.cfg) > kNoAllocStatusOff)
+  if (g.n_chunks > kNoAllocMaxChunks || encode_workspace_basic(g, nd.cfg) > kNoAllocStatusOff)
     return SPRINTZ_ERR_WS_TOO_SMALL;
   int *status = reinterpret_cast<int *>(nd.ptr + kNoAllocStatusOff);
   cudaStream_t s = (cudaStream_t)stream;
