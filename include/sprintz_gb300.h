@@ -115,6 +115,38 @@ int sprintz_decompress(sprintz_ctx *ctx, const void *src, uint64_t src_size,
                        const sprintz_info *info, void *dst, uint64_t dst_cap, void *workspace,
                        uint64_t ws_bytes, void *stream);
 
+/* ---- Batches of independent streams --------------------------------------
+ * Many streams of uneven length, width and D encoded or decoded by one
+ * persistent kernel launch over the chunk groups of all of them.  The paper
+ * compresses one stream at a time; a batch is a set of independent streams,
+ * and every stream's bytes are exactly those sprintz_compress() would write.
+ *
+ * sprintz_batch_plan() checks the items, uploads their descriptors into the
+ * workspace (one host-to-device copy, stream-ordered) and records the launch
+ * shape in the context; sprintz_batch_run() then only enqueues memsets and
+ * kernels, so it may be repeated (or captured in a CUDA graph) for the same
+ * buffers.  A context holds one plan at a time.  Batches need D <= 32 for
+ * every stream, 8-byte-aligned sample buffers, and no Huffman coding
+ * (SPRINTZ_ERR_UNSUPPORTED otherwise). */
+typedef struct {
+  const void *src;     /* compress: rows x D samples; decompress: the stream */
+  uint64_t src_bytes;  /* decompress: stream size in bytes; compress: unused */
+  void *dst;           /* compress: stream buffer; decompress: rows x D samples */
+  uint64_t dst_cap;    /* bytes available at dst */
+  uint64_t *out_size;  /* compress: device uint64 receiving the stream size */
+  uint64_t rows;       /* shape and options (decompress: from sprintz_query) */
+  uint32_t D;
+  uint32_t w;
+  sprintz_opts opts;
+} sprintz_batch_item;
+
+/* Workspace bytes for a batch (compress = 1 or 0); 0 if an item is invalid. */
+uint64_t sprintz_batch_workspace_size(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n,
+                                      int compress);
+int sprintz_batch_plan(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n, int compress,
+                       void *workspace, uint64_t ws_bytes, void *stream);
+int sprintz_batch_run(sprintz_ctx *ctx, void *workspace, uint64_t ws_bytes, void *stream);
+
 /* Compression for callers that cannot allocate device memory.  (The paper has
  * no counterpart: this is a deployment variant of sprintz_compress.)
  *

@@ -11,6 +11,11 @@ struct sprintz_ctx {
   int *d_status;
   int *h_status;  // pinned
   spz::LaunchCfg cfg;
+  // the current batch plan and the host images of its descriptors
+  spz::BatchPlan plan{};
+  bool has_plan = false;
+  std::vector<uint8_t> items_img;
+  std::vector<uint64_t> prefix_img;
 };
 
 namespace spz {
@@ -197,6 +202,53 @@ int sprintz_decompress(sprintz_ctx *ctx, const void *src, uint64_t src_size, con
   if (ws_bytes < spz::decode_workspace_bytes(g, ctx->cfg)) return SPRINTZ_ERR_WS_TOO_SMALL;
   return spz::launch_decode(g, ctx->cfg, (const uint8_t *)src, src_size, (uint8_t *)dst, dst_cap,
                             (uint8_t *)workspace, ws_bytes, ctx->d_status, (cudaStream_t)stream);
+}
+
+static int plan_any(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n, int compress, uint8_t *ws,
+                    spz::BatchPlan *pl) {
+  if (!ctx || (!items && n)) return SPRINTZ_ERR_INVALID_ARG;
+  if (n == 0) return SPRINTZ_ERR_INVALID_ARG;
+  return compress ? spz::plan_batch_encode(items, n, ctx->cfg, ctx->d_status, ws, pl, &ctx->items_img,
+                                           &ctx->prefix_img)
+                  : spz::plan_batch_decode(items, n, ctx->cfg, ctx->d_status, ws, pl, &ctx->items_img,
+                                           &ctx->prefix_img);
+}
+
+uint64_t sprintz_batch_workspace_size(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n,
+                                      int compress) {
+  spz::BatchPlan pl;
+  if (plan_any(ctx, items, n, compress, nullptr, &pl) != SPRINTZ_OK) return 0;
+  return pl.ws_total;
+}
+
+int sprintz_batch_plan(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n, int compress,
+                       void *workspace, uint64_t ws_bytes, void *stream) {
+  if (!workspace) return SPRINTZ_ERR_INVALID_ARG;
+  spz::BatchPlan pl;
+  if (ctx) ctx->has_plan = false;
+  int rc = plan_any(ctx, items, n, compress, (uint8_t *)workspace, &pl);
+  if (rc != SPRINTZ_OK) return rc;
+  if (ws_bytes < pl.ws_total) return SPRINTZ_ERR_WS_TOO_SMALL;
+  pl.ws = workspace;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint8_t *ws = (uint8_t *)workspace;
+  if (cudaMemcpyAsync(ws + pl.items_off, ctx->items_img.data(), ctx->items_img.size(), cudaMemcpyHostToDevice,
+                      s) != cudaSuccess ||
+      cudaMemcpyAsync(ws + pl.prefix_off, ctx->prefix_img.data(), ctx->prefix_img.size() * 8,
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return SPRINTZ_ERR_CUDA;
+  // the host images must outlive the copies: wait for them here
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  ctx->plan = pl;
+  ctx->has_plan = true;
+  return SPRINTZ_OK;
+}
+
+int sprintz_batch_run(sprintz_ctx *ctx, void *workspace, uint64_t ws_bytes, void *stream) {
+  if (!ctx || !ctx->has_plan || ctx->plan.ws != workspace || ws_bytes < ctx->plan.ws_total)
+    return SPRINTZ_ERR_INVALID_ARG;
+  return ctx->plan.compress ? spz::run_batch_encode(ctx->plan, (cudaStream_t)stream)
+                            : spz::run_batch_decode(ctx->plan, (cudaStream_t)stream);
 }
 
 int sprintz_get_status(sprintz_ctx *ctx, void *stream) {

@@ -18,6 +18,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string.h>
+
+#include <vector>
+
 #include "../../include/sprintz_gb300.h"
 
 namespace spz {
@@ -169,6 +173,9 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -220,6 +227,32 @@ int launch_encode_fast(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, 
                        uint64_t dst_cap, uint64_t *d_out_size, uint8_t *ws, uint64_t ws_bytes,
                        int *d_status, cudaStream_t stream);
 uint64_t decode_workspace_bytes(const Geom &g, const LaunchCfg &cfg);
+
+// Batched launches: the host part of a plan (device descriptors live in the
+// workspace at the recorded offsets).
+struct BatchPlan {
+  int compress;
+  uint32_t n;
+  uint32_t grid;
+  uint32_t region;        // shared bytes per warp
+  uint64_t slot_region;   // encode: slot bytes per warp
+  uint64_t items_off;     // descriptor table
+  uint64_t prefix_off;    // chunk-group prefix (n + 1 words)
+  uint64_t slots_off;     // encode: slots
+  uint64_t zero_bytes;    // encode: ticket + look-back words to clear at [0, zero_bytes)
+  uint64_t ws_total;
+  void *ws;
+};
+// Build the plan and the descriptor image (host bytes to copy to ws + items_off
+// and ws + prefix_off).  Returns SPRINTZ_OK or an error.
+int plan_batch_encode(const sprintz_batch_item *items, uint32_t n, const LaunchCfg &cfg, int *d_status,
+                      uint8_t *ws, BatchPlan *plan, std::vector<uint8_t> *items_img,
+                      std::vector<uint64_t> *prefix_img);
+int run_batch_encode(const BatchPlan &plan, cudaStream_t stream);
+int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchCfg &cfg, int *d_status,
+                      uint8_t *ws, BatchPlan *plan, std::vector<uint8_t> *items_img,
+                      std::vector<uint64_t> *prefix_img);
+int run_batch_decode(const BatchPlan &plan, cudaStream_t stream);
 int launch_decode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint64_t src_size,
                   uint8_t *dst, uint64_t dst_cap, uint8_t *ws, uint64_t ws_bytes, int *d_status,
                   cudaStream_t stream);

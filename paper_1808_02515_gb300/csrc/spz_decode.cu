@@ -461,9 +461,11 @@ struct LaneRing {
 
 constexpr uint32_t kRingWaitLimit = 1u << 22;
 
+// Decode chunk group `warp_id` (K consecutive chunks) of one stream with one
+// warp whose shared region (stage, barriers, rings) starts at wsm.
 template <int W>
-__global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p, LaneRing rg) {
-  extern __shared__ __align__(16) uint8_t dsm[];
+__device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing &rg, uint64_t warp_id,
+                                             uint8_t *wsm) {
   const Geom &g = p.g;
   const uint32_t D = g.D;
   const uint32_t K = 32 / D;
@@ -474,9 +476,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p, Lane
   const uint32_t last = seg0 + D - 1;
   // this chunk's lanes (they take the same branches: their data is shared)
   const uint32_t seg_mask = D == 32 ? 0xFFFFFFFFu : ((1u << D) - 1u) << seg0;
-  const uint64_t warp_id = (uint64_t)blockIdx.x * kLaneWarps + warp;
   const uint64_t c64 = warp_id * K + kk;
-  uint8_t *wsm = dsm + (uint64_t)warp * rg.per_warp;
   uint8_t *stage = wsm;
   uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + rg.bars_off) + kc * rg.nseg;
   const uint32_t ring_bytes = rg.seg * rg.nseg;
@@ -735,12 +735,84 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p, Lane
       bad |= rbits(hdr * 8 + (s * D + j) * hb, (1u << hb) - 1u) != 0;
     if (bad) set_status(p.status, SPRINTZ_ERR_CORRUPT);
   }
-  // no bulk copy may still be writing this warp's shared memory at exit
+  // no bulk copy may still be writing this warp's shared memory when it is
+  // reused or the CTA exits; then the barriers are retired
   if (kk < K && c64 < g.n_chunks && hdr_ok) {
     ring_ok = true;
     wait_upto(~0ull);
     if (!ring_ok && j == 0) set_status(p.status, SPRINTZ_ERR_TIMEOUT);
+    if (j == 0 && s_hi >= s_lo && seg_issued > s_lo)
+      for (uint32_t h = 0; h < rg.nseg; ++h) mbar_inval(&bars[h]);
   }
+  __syncwarp();
+}
+
+template <int W>
+__global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p, LaneRing rg) {
+  extern __shared__ __align__(16) uint8_t dsm[];
+  const uint32_t warp = threadIdx.x >> 5;
+  const DecParams pp = p;
+  const LaneRing rr = rg;
+  decode_group<W>(pp, rr, (uint64_t)blockIdx.x * kLaneWarps + warp, dsm + (uint64_t)warp * rr.per_warp);
+}
+
+// One stream of a batched decode.
+struct DecBatchItem {
+  DecParams p;
+  LaneRing rg;
+};
+
+// Batched decode: the chunk groups of all streams form one work list
+// (gprefix[s] = first group of stream s); each warp takes items in turn.
+__global__ void __launch_bounds__(kLaneThreads) k_decode_batch(const DecBatchItem *items,
+                                                              const uint64_t *gprefix, uint32_t n,
+                                                              uint32_t per_warp) {
+  extern __shared__ __align__(16) uint8_t dsm[];
+  const uint32_t warp = threadIdx.x >> 5;
+  uint8_t *wsm = dsm + (uint64_t)warp * per_warp;
+  const uint64_t total = gprefix[n];
+  for (uint64_t item = (uint64_t)blockIdx.x * kLaneWarps + warp; item < total;
+       item += (uint64_t)gridDim.x * kLaneWarps) {
+    // stream of this item: last s with gprefix[s] <= item
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) / 2;
+      if (gprefix[mid] <= item) lo = mid; else hi = mid;
+    }
+    const DecBatchItem it = items[lo];
+    if (it.p.g.w == 8)
+      decode_group<8>(it.p, it.rg, item - gprefix[lo], wsm);
+    else
+      decode_group<16>(it.p, it.rg, item - gprefix[lo], wsm);
+  }
+}
+
+// Header check and raw tail of every stream of a batch (one CTA per stream).
+__global__ void k_decode_batch_tails(const DecBatchItem *items) {
+  const DecParams &p = items[blockIdx.x].p;
+  const Geom &g = p.g;
+  __shared__ uint32_t s_ok;
+  __shared__ uint64_t s_tail_off;
+  if (threadIdx.x == 0) {
+    const uint8_t *h = p.src;
+    bool ok = h[0] == 'S' && h[1] == 'P' && h[2] == 'Z' && h[3] == '1' && h[4] == 1 &&
+              h[5] == g.w && h[6] == g.forecaster && h[7] == (g.huffman ? 1 : 0) &&
+              (h[8] | (h[9] << 8)) == g.D && h[10] == g.G && h[11] == g.learn_shift &&
+              le_u32(h + 12) == g.chunk_rows_opt && le_u32(h + 16) == (g.huffman ? g.huff_chunks : 0) &&
+              le_u32(h + 20) == g.n_chunks && le_u64(h + 24) == g.rows &&
+              le_u32(h + 32) == g.tail_rows && le_u32(h + 36) == 0 && le_u64(h + 40) == g.data_off;
+    const uint64_t tail_off = le_u64(h + 48), total = le_u64(h + 56);
+    ok = ok && tail_off >= g.data_off && total <= p.src_size && total == tail_off + g.tail_rows * g.D * g.wb;
+    s_ok = ok;
+    s_tail_off = tail_off;
+    if (!ok) set_status(p.status, SPRINTZ_ERR_CORRUPT);
+  }
+  __syncthreads();
+  if (!s_ok) return;
+  const uint64_t tail_bytes = g.tail_rows * g.D * g.wb;
+  uint8_t *d = p.dst + g.full_rows * g.D * g.wb;
+  const uint8_t *src = p.src + s_tail_off;
+  for (uint64_t k = threadIdx.x; k < tail_bytes; k += blockDim.x) d[k] = src[k];
 }
 
 static LaneRing lane_ring_plan(const Geom &g, const LaunchCfg &cfg, uint32_t nseg_want) {
@@ -810,6 +882,79 @@ static DecPlan dec_plan(const Geom &g, const LaunchCfg &cfg) {
   }
   if (pl.grid == 0) pl.grid = 1;
   return pl;
+}
+
+// ---- batches ----------------------------------------------------------------
+
+int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchCfg &cfg, int *d_status,
+                      uint8_t *ws, BatchPlan *pl, std::vector<uint8_t> *img, std::vector<uint64_t> *pre) {
+  (void)ws;
+  std::vector<DecBatchItem> v(n);
+  pre->assign((size_t)n + 1, 0);
+  uint32_t region = 0;
+  static const uint32_t win = [] {
+    const char *e = getenv("SPRINTZ_DEC_PF_WIN");
+    int x = e ? atoi(e) : 0;
+    return (uint32_t)(x >= 16 ? (x & ~15) : 2048);
+  }();
+  for (uint32_t i = 0; i < n; ++i) {
+    const sprintz_batch_item &it = items[i];
+    Geom g;
+    int rc = make_geom(it.rows, it.D, it.w, &it.opts, &g);
+    if (rc != SPRINTZ_OK) return rc;
+    if (it.opts.huffman || g.D > 32 || g.max_body >= (1ull << 28)) return SPRINTZ_ERR_UNSUPPORTED;
+    if (!it.src || (it.rows && !it.dst)) return SPRINTZ_ERR_INVALID_ARG;
+    if (((uintptr_t)it.dst & 7) != 0) return SPRINTZ_ERR_UNSUPPORTED;
+    if (it.dst_cap < it.rows * it.D * g.wb) return SPRINTZ_ERR_DST_TOO_SMALL;
+    if (it.src_bytes < g.data_off) return SPRINTZ_ERR_CORRUPT;
+    DecBatchItem &d = v[i];
+    memset(&d, 0, sizeof(d));
+    d.p.src = (const uint8_t *)it.src;
+    d.p.src_size = it.src_bytes;
+    d.p.dst = (uint8_t *)it.dst;
+    d.p.dst_cap = it.dst_cap;
+    d.p.status = d_status;
+    d.p.g = g;
+    d.p.pf_win = win;
+    if (g.n_chunks) {
+      d.rg = lane_ring_plan(g, cfg, 2);
+      if (!d.rg.per_warp) return SPRINTZ_ERR_UNSUPPORTED;
+      region = std::max(region, d.rg.per_warp);
+    }
+    const uint64_t K = 32 / g.D;
+    (*pre)[i + 1] = (*pre)[i] + (g.n_chunks + K - 1) / K;
+  }
+  memset(pl, 0, sizeof(*pl));
+  pl->compress = 0;
+  pl->n = n;
+  pl->region = std::max<uint32_t>(region, 16);
+  pl->items_off = 0;
+  pl->prefix_off = align256d((uint64_t)n * sizeof(DecBatchItem));
+  pl->ws_total = pl->prefix_off + 8ull * (n + 1);
+  const uint64_t smem = (uint64_t)kLaneWarps * pl->region;
+  if (smem > (uint64_t)cfg.max_smem_optin) return SPRINTZ_ERR_UNSUPPORTED;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_decode_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_decode_batch, kLaneThreads, smem) != cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  const uint64_t total = (*pre)[n];
+  pl->grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((total + kLaneWarps - 1) / kLaneWarps,
+                                                                (uint64_t)cfg.sm_count * occ));
+  img->assign(reinterpret_cast<const uint8_t *>(v.data()),
+              reinterpret_cast<const uint8_t *>(v.data()) + (size_t)n * sizeof(DecBatchItem));
+  return SPRINTZ_OK;
+}
+
+int run_batch_decode(const BatchPlan &pl, cudaStream_t stream) {
+  uint8_t *ws = (uint8_t *)pl.ws;
+  const DecBatchItem *items = reinterpret_cast<const DecBatchItem *>(ws + pl.items_off);
+  const uint64_t *pre = reinterpret_cast<const uint64_t *>(ws + pl.prefix_off);
+  k_decode_batch_tails<<<pl.n, 128, 0, stream>>>(items);
+  k_decode_batch<<<pl.grid, kLaneThreads, (uint64_t)kLaneWarps * pl.region, stream>>>(items, pre, pl.n,
+                                                                                     pl.region);
+  return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
 }
 
 uint64_t decode_workspace_bytes(const Geom &g, const LaunchCfg &cfg) {

@@ -838,9 +838,11 @@ struct EncSlotCfg {
   uint8_t *slots;        // [warp][K] slots
 };
 
+// Encode chunk group `grp` of one stream with one warp: wsm is the warp's
+// shared region (stage, then K rings), wslots its K body slots.
 template <int W>
-__global__ void __launch_bounds__(kEncLaneThreads) k_encode_slots(EncParams p, EncSlotCfg cfg) {
-  extern __shared__ __align__(16) uint8_t smem[];
+__device__ __forceinline__ void encode_group_slots(const EncParams &p, const EncSlotCfg &cfg, uint32_t grp,
+                                                   uint8_t *wsm, uint8_t *wslots) {
   const Geom &g = p.g;
   const uint32_t D = g.D;
   const uint32_t K = 32 / D;
@@ -850,12 +852,11 @@ __global__ void __launch_bounds__(kEncLaneThreads) k_encode_slots(EncParams p, E
   const uint32_t seg0 = lane - j, last = seg0 + D - 1;
   const uint32_t wb = W / 8;
   const uint32_t G = g.G, hb = g.hb, H = g.hdr_bytes;
-  uint8_t *stage = smem + warp * kEncStage;
-  uint32_t *ring = reinterpret_cast<uint32_t *>(smem + kEncLaneWarps * kEncStage +
-                                                ((uint64_t)warp * K + kc) * cfg.window);
+  (void)warp;
+  uint8_t *stage = wsm;
+  uint32_t *ring = reinterpret_cast<uint32_t *>(wsm + kEncStage + (uint64_t)kc * cfg.window);
   const uint32_t ring_wmask = cfg.window / 4 - 1, ring_bitmask = cfg.window * 8 - 1;
-  const uint64_t gwarp = (uint64_t)blockIdx.x * kEncLaneWarps + warp;
-  uint8_t *slot = cfg.slots + (gwarp * K + kc) * (uint64_t)cfg.slot_stride;
+  uint8_t *slot = wslots + (uint64_t)kc * cfg.slot_stride;
 
   // cooperative stage loads: this lane's (up to two) 8-byte words of a block step
   const uint32_t words_per = D * wb, total_words = K * words_per;
@@ -872,11 +873,7 @@ __global__ void __launch_bounds__(kEncLaneThreads) k_encode_slots(EncParams p, E
   const uint8_t *my_x = stage + kc * (kBlockRows * row_stride) + j * wb;
   const uint32_t nb_max = (uint32_t)(min(g.chunk_rows, g.full_rows) / kBlockRows);
 
-  for (;;) {
-    uint32_t grp = 0;
-    if (lane == 0) grp = atomicAdd(p.ticket, 1u);
-    grp = __shfl_sync(0xFFFFFFFFu, grp, 0);
-    if (grp >= cfg.n_groups) break;
+  {
     const uint64_t c64 = (uint64_t)grp * K + kk;
     const bool live = kk < K && c64 < g.n_chunks;
     const uint64_t row0 = c64 * g.chunk_rows;
@@ -1130,6 +1127,80 @@ __global__ void __launch_bounds__(kEncLaneThreads) k_encode_slots(EncParams p, E
   }
 }
 
+template <int W>
+__global__ void __launch_bounds__(kEncLaneThreads) k_encode_slots(EncParams p, EncSlotCfg cfg) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t K = 32 / p.g.D;
+  const uint32_t region = kEncStage + K * cfg.window;
+  uint8_t *wsm = smem + (uint64_t)warp * region;
+  const uint64_t gwarp = (uint64_t)blockIdx.x * kEncLaneWarps + warp;
+  uint8_t *wslots = cfg.slots + gwarp * K * (uint64_t)cfg.slot_stride;
+  for (;;) {
+    uint32_t grp = 0;
+    if (lane == 0) grp = atomicAdd(p.ticket, 1u);
+    grp = __shfl_sync(0xFFFFFFFFu, grp, 0);
+    if (grp >= cfg.n_groups) break;
+    encode_group_slots<W>(p, cfg, grp, wsm, wslots);
+  }
+}
+
+// One stream of a batched encode.
+struct EncBatchItem {
+  EncParams p;    // its own look-back words, destination and size word
+  EncSlotCfg cfg;
+};
+
+// Batched encode: the chunk groups of all streams, in stream order, form one
+// work list taken from a single ticket, so a group's look-back only waits on
+// earlier groups of its own stream, all of which are already running.
+__global__ void __launch_bounds__(kEncLaneThreads) k_encode_batch(const EncBatchItem *items,
+                                                                 const uint64_t *gprefix, uint32_t n,
+                                                                 uint32_t *ticket, uint32_t region,
+                                                                 uint8_t *slots, uint64_t slot_region) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint8_t *wsm = smem + (uint64_t)warp * region;
+  const uint64_t gwarp = (uint64_t)blockIdx.x * kEncLaneWarps + warp;
+  uint8_t *wslots = slots + gwarp * slot_region;
+  const uint64_t total = gprefix[n];
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(reinterpret_cast<unsigned long long *>(ticket), 1ull);
+    item = __shfl_sync(0xFFFFFFFFu, item, 0);
+    if (item >= total) break;
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) / 2;
+      if (gprefix[mid] <= item) lo = mid; else hi = mid;
+    }
+    const EncBatchItem it = items[lo];
+    const uint32_t grp = (uint32_t)(item - gprefix[lo]);
+    if (it.p.g.w == 8)
+      encode_group_slots<8>(it.p, it.cfg, grp, wsm, wslots);
+    else
+      encode_group_slots<16>(it.p, it.cfg, grp, wsm, wslots);
+  }
+}
+
+// Streams of a batch without a full block: header and raw tail only.
+__global__ void k_encode_batch_tails(const EncBatchItem *items) {
+  const EncParams &p = items[blockIdx.x].p;
+  const Geom &g = p.g;
+  if (g.n_chunks != 0) return;
+  const uint64_t tail_bytes = g.tail_rows * g.D * g.wb;
+  const uint64_t total = g.data_off + tail_bytes;
+  if (total > p.dst_cap) {
+    if (threadIdx.x == 0) set_status(p.status, SPRINTZ_ERR_DST_TOO_SMALL);
+    return;
+  }
+  for (uint64_t k = threadIdx.x; k < tail_bytes; k += blockDim.x) p.dst[g.data_off + k] = p.src[k];
+  if (threadIdx.x == 0) {
+    write_stream_header(p.dst, g, g.data_off, total);
+    *p.out_size = total;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -1214,7 +1285,7 @@ static SlotPlan slot_plan(const Geom &g, const LaunchCfg &cfg) {
   pl.sc.window = enc_window_bytes(g);
   pl.sc.n_groups = (uint32_t)((g.n_chunks + K - 1) / K);
   pl.sc.slot_stride = (uint32_t)(((g.max_body + 15) & ~15ull) + 16);
-  pl.smem = (uint64_t)kEncLaneWarps * kEncStage + (uint64_t)kEncLaneWarps * K * pl.sc.window;
+  pl.smem = (uint64_t)kEncLaneWarps * (kEncStage + (uint64_t)K * pl.sc.window);
   if (pl.smem > (uint64_t)cfg.max_smem_optin) return pl;
   const uint64_t want = (pl.sc.n_groups + kEncLaneWarps - 1) / kEncLaneWarps;
   pl.grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)cfg.sm_count *
@@ -1317,6 +1388,91 @@ int launch_encode_fast(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, 
     k_encode_slots<8><<<sp.grid, kEncLaneThreads, sp.smem, stream>>>(p, sc);
   else
     k_encode_slots<16><<<sp.grid, kEncLaneThreads, sp.smem, stream>>>(p, sc);
+  return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
+}
+
+// ---- batches ----------------------------------------------------------------
+
+static uint32_t enc_batch_ctas_per_sm() {
+  static uint32_t v = [] {
+    const char *e = getenv("SPRINTZ_ENC_BATCH_CTAS_PER_SM");
+    int x = e ? atoi(e) : 0;
+    return (uint32_t)(x > 0 && x <= 32 ? x : 4);
+  }();
+  return v;
+}
+
+int plan_batch_encode(const sprintz_batch_item *items, uint32_t n, const LaunchCfg &cfg, int *d_status,
+                      uint8_t *ws, BatchPlan *pl, std::vector<uint8_t> *img, std::vector<uint64_t> *pre) {
+  std::vector<EncBatchItem> v(n);
+  pre->assign((size_t)n + 1, 0);
+  uint64_t lb_words = 0;
+  uint32_t region = kEncStage;
+  uint64_t slot_region = 16;
+  for (uint32_t i = 0; i < n; ++i) {
+    const sprintz_batch_item &it = items[i];
+    Geom g;
+    int rc = make_geom(it.rows, it.D, it.w, &it.opts, &g);
+    if (rc != SPRINTZ_OK) return rc;
+    if (it.opts.huffman || g.D > 32 || g.max_body >= (1ull << 28)) return SPRINTZ_ERR_UNSUPPORTED;
+    if (!it.dst || !it.out_size || (it.rows && !it.src)) return SPRINTZ_ERR_INVALID_ARG;
+    if (((uintptr_t)it.src & 7) != 0) return SPRINTZ_ERR_UNSUPPORTED;
+    if (it.dst_cap < sprintz_max_compressed_size(it.rows, it.D, it.w, &it.opts)) return SPRINTZ_ERR_DST_TOO_SMALL;
+    const uint32_t K = 32 / g.D;
+    EncBatchItem &e = v[i];
+    memset(&e, 0, sizeof(e));
+    e.p.src = (const uint8_t *)it.src;
+    e.p.dst = (uint8_t *)it.dst;
+    e.p.dst_cap = it.dst_cap;
+    e.p.out_size = it.out_size;
+    e.p.status = d_status;
+    e.p.g = g;
+    e.p.lookback = reinterpret_cast<uint64_t *>(ws + 16 + 8 * lb_words);
+    e.cfg.window = enc_window_bytes(g);
+    e.cfg.n_groups = (uint32_t)((g.n_chunks + K - 1) / K);
+    e.cfg.slot_stride = (uint32_t)(((g.max_body + 15) & ~15ull) + 16);
+    lb_words += e.cfg.n_groups;
+    (*pre)[i + 1] = (*pre)[i] + e.cfg.n_groups;
+    region = std::max<uint32_t>(region, kEncStage + K * e.cfg.window);
+    slot_region = std::max<uint64_t>(slot_region, (uint64_t)K * e.cfg.slot_stride);
+  }
+  memset(pl, 0, sizeof(*pl));
+  pl->compress = 1;
+  pl->n = n;
+  pl->region = region;
+  pl->slot_region = slot_region;
+  pl->zero_bytes = 16 + 8 * lb_words;
+  pl->items_off = align256(pl->zero_bytes);
+  pl->prefix_off = align256(pl->items_off + (uint64_t)n * sizeof(EncBatchItem));
+  pl->slots_off = align256(pl->prefix_off + 8ull * (n + 1));
+  const uint64_t smem = (uint64_t)kEncLaneWarps * region;
+  if (smem > (uint64_t)cfg.max_smem_optin) return SPRINTZ_ERR_UNSUPPORTED;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_encode_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_encode_batch, kEncLaneThreads, smem) != cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  const uint64_t total = (*pre)[n];
+  const uint64_t per_sm = std::min<uint64_t>((uint64_t)occ, enc_batch_ctas_per_sm());
+  pl->grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((total + kEncLaneWarps - 1) / kEncLaneWarps,
+                                                                (uint64_t)cfg.sm_count * per_sm));
+  pl->ws_total = pl->slots_off + (uint64_t)pl->grid * kEncLaneWarps * slot_region;
+  if (ws)
+    for (auto &e : v) e.p.ticket = reinterpret_cast<uint32_t *>(ws);
+  img->assign(reinterpret_cast<const uint8_t *>(v.data()),
+              reinterpret_cast<const uint8_t *>(v.data()) + (size_t)n * sizeof(EncBatchItem));
+  return SPRINTZ_OK;
+}
+
+int run_batch_encode(const BatchPlan &pl, cudaStream_t stream) {
+  uint8_t *ws = (uint8_t *)pl.ws;
+  const EncBatchItem *items = reinterpret_cast<const EncBatchItem *>(ws + pl.items_off);
+  const uint64_t *pre = reinterpret_cast<const uint64_t *>(ws + pl.prefix_off);
+  if (cudaMemsetAsync(ws, 0, pl.zero_bytes, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  k_encode_batch_tails<<<pl.n, 128, 0, stream>>>(items);
+  k_encode_batch<<<pl.grid, kEncLaneThreads, (uint64_t)kEncLaneWarps * pl.region, stream>>>(
+      items, pre, pl.n, reinterpret_cast<uint32_t *>(ws), pl.region, ws + pl.slots_off, pl.slot_region);
   return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
 }
 

@@ -44,6 +44,12 @@ class _Info(ctypes.Structure):
                 ("total_bytes", ctypes.c_uint64)]
 
 
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_void_p), ("src_bytes", ctypes.c_uint64), ("dst", ctypes.c_void_p),
+                ("dst_cap", ctypes.c_uint64), ("out_size", ctypes.c_void_p), ("rows", ctypes.c_uint64),
+                ("D", ctypes.c_uint32), ("w", ctypes.c_uint32), ("opts", _Opts)]
+
+
 @dataclass(frozen=True)
 class Opts:
     forecaster: int = FIRE
@@ -92,6 +98,13 @@ def lib() -> ctypes.CDLL:
         L.sprintz_decompress.argtypes = [vp, vp, u64, PI, vp, u64, vp, u64, vp]
         L.sprintz_compress_noalloc.restype = i32
         L.sprintz_compress_noalloc.argtypes = [vp, u64, u32, u32, PO, vp, u64, vp, vp]
+        PB = ctypes.POINTER(_BatchItem)
+        L.sprintz_batch_workspace_size.restype = u64
+        L.sprintz_batch_workspace_size.argtypes = [vp, PB, u32, i32]
+        L.sprintz_batch_plan.restype = i32
+        L.sprintz_batch_plan.argtypes = [vp, PB, u32, i32, vp, u64, vp]
+        L.sprintz_batch_run.restype = i32
+        L.sprintz_batch_run.argtypes = [vp, vp, u64, vp]
         L.sprintz_query.restype = i32
         L.sprintz_query.argtypes = [vp, u64, PI]
         L.sprintz_get_status.restype = i32
@@ -264,3 +277,73 @@ class Codec:
 
     def check(self, stream=None) -> None:
         _check(self.status(stream), "device status")
+
+    # ---- batches of independent streams -----------------------------------
+
+    def _items(self, rows_d_w_opts, srcs, src_bytes, dsts, out_sizes):
+        arr = (_BatchItem * len(rows_d_w_opts))()
+        for k, (rows, D, w, o) in enumerate(rows_d_w_opts):
+            arr[k] = _BatchItem(ctypes.c_void_p(srcs[k]), src_bytes[k], ctypes.c_void_p(dsts[k][0]),
+                                dsts[k][1], ctypes.c_void_p(out_sizes[k]), rows, D, w, o.c())
+        return arr
+
+    def batch_plan_run(self, arr, compress: int, stream=None):
+        """Size a workspace, plan the batch into it and run it once; returns
+        the workspace (keep it to call batch_run again)."""
+        n = len(arr)
+        wsn = int(lib().sprintz_batch_workspace_size(self.ctx, arr, n, compress))
+        if wsn == 0:
+            raise SprintzError(ERR_INVALID_ARG, "sprintz_batch_workspace_size")
+        ws = self.torch.empty(wsn, dtype=self.torch.uint8, device=f"cuda:{self.device}")
+        _check(lib().sprintz_batch_plan(self.ctx, arr, n, compress, ctypes.c_void_p(ws.data_ptr()), wsn,
+                                        self._stream(stream)), "sprintz_batch_plan")
+        self.batch_run(ws, stream)
+        return ws
+
+    def batch_run(self, ws, stream=None) -> None:
+        _check(lib().sprintz_batch_run(self.ctx, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                       self._stream(stream)), "sprintz_batch_run")
+
+    def compress_batch(self, xs, opts, stream=None):
+        """Compress a list of (rows, D) uint8/16-bit device tensors in one
+        batched launch; `opts` is one Opts or one per stream. Returns
+        (streams, sizes, ws): stream buffers, a device int64 tensor of sizes,
+        and the planned workspace."""
+        torch = self.torch
+        n = len(xs)
+        ol = list(opts) if isinstance(opts, (list, tuple)) else [opts] * n
+        shapes, srcs, dsts = [], [], []
+        sizes = torch.zeros(n, dtype=torch.int64, device=xs[0].device)
+        bufs = []
+        for x, o in zip(xs, ol):
+            x2 = x.view(-1, 1) if x.dim() == 1 else x
+            rows, D = x2.shape
+            w = 8 if x2.dtype == torch.uint8 else 16
+            cap = max_compressed_size(rows, D, w, o)
+            buf = torch.empty(cap, dtype=torch.uint8, device=x.device)
+            bufs.append(buf)
+            shapes.append((rows, D, w, o))
+            srcs.append(x2.data_ptr() if rows else 0)
+            dsts.append((buf.data_ptr(), cap))
+        arr = self._items(shapes, srcs, [0] * n, dsts,
+                          [sizes.data_ptr() + 8 * k for k in range(n)])
+        ws = self.batch_plan_run(arr, 1, stream)
+        return bufs, sizes, ws
+
+    def decompress_batch(self, streams, infos, sizes, stream=None):
+        """Decompress device streams (with their host-parsed infos and byte
+        sizes) in one batched launch; returns the decoded tensors and the
+        planned workspace."""
+        torch = self.torch
+        outs, shapes, srcs, dsts = [], [], [], []
+        for s, info, n in zip(streams, infos, sizes):
+            dt = torch.uint8 if info.w == 8 else torch.int16
+            y = torch.empty((info.rows, info.D), dtype=dt, device=s.device)
+            outs.append(y)
+            shapes.append((info.rows, info.D, info.w, info.opts))
+            srcs.append(s.data_ptr())
+            dsts.append((y.data_ptr() if y.numel() else 0, y.numel() * y.element_size()))
+        arr = self._items(shapes, srcs, list(sizes), dsts, [0] * len(streams))
+        ws = self.batch_plan_run(arr, 0, stream)
+        return outs, ws
+
