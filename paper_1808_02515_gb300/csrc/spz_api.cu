@@ -133,6 +133,7 @@ static spz::LaunchCfg default_cfg() {
 uint64_t sprintz_compress_workspace_size(uint64_t rows, uint32_t D, uint32_t w, const sprintz_opts *o) {
   Geom g;
   if (spz::make_geom(rows, D, w, o, &g) != SPRINTZ_OK) return 0;
+  if (g.huffman) return spz::huff_encode_workspace_bytes(g, default_cfg());
   return spz::encode_workspace_bytes(g, default_cfg());
 }
 
@@ -140,6 +141,7 @@ uint64_t sprintz_decompress_workspace_size(const sprintz_info *info) {
   if (!info) return 0;
   Geom g;
   if (spz::make_geom(info->rows, info->D, info->w, &info->opts, &g) != SPRINTZ_OK) return 0;
+  if (g.huffman) return spz::huff_decode_workspace_bytes(g, default_cfg());
   return spz::decode_workspace_bytes(g, default_cfg());
 }
 
@@ -150,10 +152,14 @@ int sprintz_compress(sprintz_ctx *ctx, const void *src, uint64_t rows, uint32_t 
   Geom g;
   int rc = spz::make_geom(rows, D, w, opts, &g);
   if (rc != SPRINTZ_OK) return rc;
-  if (opts->huffman) return SPRINTZ_ERR_UNSUPPORTED;
   if (dst_cap < sprintz_max_compressed_size(rows, D, w, opts)) return SPRINTZ_ERR_DST_TOO_SMALL;
-  if (ws_bytes < spz::encode_workspace_bytes(g, ctx->cfg)) return SPRINTZ_ERR_WS_TOO_SMALL;
   if (!workspace && ws_bytes) return SPRINTZ_ERR_INVALID_ARG;
+  if (g.huffman) {
+    if (ws_bytes < spz::huff_encode_workspace_bytes(g, ctx->cfg)) return SPRINTZ_ERR_WS_TOO_SMALL;
+    return spz::launch_encode_huffman(g, ctx->cfg, (const uint8_t *)src, (uint8_t *)dst, dst_cap, d_out_size,
+                                      (uint8_t *)workspace, ws_bytes, ctx->d_status, (cudaStream_t)stream);
+  }
+  if (ws_bytes < spz::encode_workspace_bytes(g, ctx->cfg)) return SPRINTZ_ERR_WS_TOO_SMALL;
   return spz::launch_encode_fast(g, ctx->cfg, (const uint8_t *)src, (uint8_t *)dst, dst_cap, d_out_size,
                                  (uint8_t *)workspace, ws_bytes, ctx->d_status, (cudaStream_t)stream);
 }
@@ -194,11 +200,15 @@ int sprintz_decompress(sprintz_ctx *ctx, const void *src, uint64_t src_size, con
   if (spz::make_geom(info->rows, info->D, info->w, &info->opts, &g) != SPRINTZ_OK)
     return SPRINTZ_ERR_INVALID_ARG;
   if (g.n_chunks != info->n_chunks || g.data_off != info->data_off) return SPRINTZ_ERR_INVALID_ARG;
-  if (info->opts.huffman) return SPRINTZ_ERR_UNSUPPORTED;
   if (src_size < g.data_off) return SPRINTZ_ERR_CORRUPT;
   uint64_t need = info->rows * info->D * g.wb;
   if (need && !dst) return SPRINTZ_ERR_INVALID_ARG;
   if (dst_cap < need) return SPRINTZ_ERR_DST_TOO_SMALL;
+  if (g.huffman) {
+    if (ws_bytes < spz::huff_decode_workspace_bytes(g, ctx->cfg)) return SPRINTZ_ERR_WS_TOO_SMALL;
+    return spz::launch_decode_huffman(g, ctx->cfg, (const uint8_t *)src, src_size, (uint8_t *)dst, dst_cap,
+                                      (uint8_t *)workspace, ws_bytes, ctx->d_status, (cudaStream_t)stream);
+  }
   if (ws_bytes < spz::decode_workspace_bytes(g, ctx->cfg)) return SPRINTZ_ERR_WS_TOO_SMALL;
   return spz::launch_decode(g, ctx->cfg, (const uint8_t *)src, src_size, (uint8_t *)dst, dst_cap,
                             (uint8_t *)workspace, ws_bytes, ctx->d_status, (cudaStream_t)stream);

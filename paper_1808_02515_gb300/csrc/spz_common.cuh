@@ -227,6 +227,15 @@ int launch_encode_fast(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, 
                        uint64_t dst_cap, uint64_t *d_out_size, uint8_t *ws, uint64_t ws_bytes,
                        int *d_status, cudaStream_t stream);
 uint64_t decode_workspace_bytes(const Geom &g, const LaunchCfg &cfg);
+// Huffman stage (spz_huff.cu)
+uint64_t huff_encode_workspace_bytes(const Geom &g, const LaunchCfg &cfg);
+int launch_encode_huffman(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint8_t *dst,
+                          uint64_t dst_cap, uint64_t *d_out_size, uint8_t *ws, uint64_t ws_bytes,
+                          int *d_status, cudaStream_t stream);
+uint64_t huff_decode_workspace_bytes(const Geom &g, const LaunchCfg &cfg);
+int launch_decode_huffman(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint64_t src_size,
+                          uint8_t *dst, uint64_t dst_cap, uint8_t *ws, uint64_t ws_bytes, int *d_status,
+                          cudaStream_t stream);
 
 // Batched launches: the host part of a plan (device descriptors live in the
 // workspace at the recorded offsets).

@@ -1128,7 +1128,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
 }
 
 template <int W>
-__global__ void __launch_bounds__(kEncLaneThreads) k_encode_slots(EncParams p, EncSlotCfg cfg) {
+__global__ void __launch_bounds__(kEncLaneThreads, 7) k_encode_slots(EncParams p, EncSlotCfg cfg) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t K = 32 / p.g.D;
