@@ -126,8 +126,10 @@ int sprintz_decompress(sprintz_ctx *ctx, const void *src, uint64_t src_size,
  * shape in the context; sprintz_batch_run() then only enqueues memsets and
  * kernels, so it may be repeated (or captured in a CUDA graph) for the same
  * buffers.  A context holds one plan at a time.  Batches need D <= 32 for
- * every stream, 8-byte-aligned sample buffers, and no Huffman coding
- * (SPRINTZ_ERR_UNSUPPORTED otherwise). */
+ * every stream, 8-byte-aligned sample buffers (except range outputs), and no
+ * Huffman coding (SPRINTZ_ERR_UNSUPPORTED otherwise).  A decompress item with
+ * row_end > row_begin is a range request: only the chunks covering those rows
+ * are decoded (chunks restart the forecaster, so any chunk decodes alone). */
 typedef struct {
   const void *src;     /* compress: rows x D samples; decompress: the stream */
   uint64_t src_bytes;  /* decompress: stream size in bytes; compress: unused */
@@ -138,6 +140,8 @@ typedef struct {
   uint32_t D;
   uint32_t w;
   sprintz_opts opts;
+  uint64_t row_begin;  /* decompress: rows [row_begin, row_end) only, when row_end > row_begin; */
+  uint64_t row_end;    /*   dst then receives exactly those rows; 0, 0 = the whole stream */
 } sprintz_batch_item;
 
 /* Workspace bytes for a batch (compress = 1 or 0); 0 if an item is invalid. */

@@ -56,7 +56,10 @@ __host__ __device__ inline DecLayout dec_layout(const Geom &g, bool staged) {
 
 struct DecParams {
   uint32_t pf_win;   // L2 bulk-prefetch window of the lane decoder (bytes, multiple of 16)
-  uint32_t pf_mode;  // bit 0: L1 prefetch ahead; bit 1: streaming stores of the output
+  uint32_t pf_mode;  // unused (0)
+  // lane decoder: decode chunks [c_begin, c_end); dst holds row c_begin * chunk_rows
+  uint32_t c_begin;
+  uint32_t c_end;
   const uint8_t *src;
   uint64_t src_size;
   uint8_t *dst;
@@ -476,7 +479,7 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
   const uint32_t last = seg0 + D - 1;
   // this chunk's lanes (they take the same branches: their data is shared)
   const uint32_t seg_mask = D == 32 ? 0xFFFFFFFFu : ((1u << D) - 1u) << seg0;
-  const uint64_t c64 = warp_id * K + kk;
+  const uint64_t c64 = p.c_begin + warp_id * K + kk;
   uint8_t *stage = wsm;
   uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + rg.bars_off) + kc * rg.nseg;
   const uint32_t ring_bytes = rg.seg * rg.nseg;
@@ -493,7 +496,7 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
   const bool hdr_ok = tail_off >= g.data_off && tail_off <= p.src_size;
   const uint64_t data_bytes = hdr_ok ? tail_off - g.data_off : 0;
 
-  bool live = kk < K && c64 < g.n_chunks && hdr_ok;
+  bool live = kk < K && c64 < p.c_end && hdr_ok;
   const uint32_t c = (uint32_t)c64;
   uint64_t off = 0, end = 0;
   uint32_t nrec = 0, packed = 0, nb = 0;
@@ -585,7 +588,7 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
     const uint32_t wq = has[t] ? q % words_per : 0;
     from_lane[t] = k2 * D;
     src_word[t] = q;
-    const uint64_t r2 = (warp_id * K + k2) * g.chunk_rows;
+    const uint64_t r2 = (warp_id * K + k2) * g.chunk_rows;  // rows from chunk c_begin
     dptr[t] = reinterpret_cast<uint64_t *>(p.dst + r2 * D * wb) + wq;
   }
   uint8_t *my_stage = stage + kc * blk_bytes + j * wb;
@@ -737,7 +740,7 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
   }
   // no bulk copy may still be writing this warp's shared memory when it is
   // reused or the CTA exits; then the barriers are retired
-  if (kk < K && c64 < g.n_chunks && hdr_ok) {
+  if (kk < K && c64 < p.c_end && hdr_ok) {
     ring_ok = true;
     wait_upto(~0ull);
     if (!ring_ok && j == 0) set_status(p.status, SPRINTZ_ERR_TIMEOUT);
@@ -760,6 +763,10 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p, Lane
 struct DecBatchItem {
   DecParams p;
   LaneRing rg;
+  // range request (row_end > row_begin): p.dst is a temporary holding the
+  // covering chunks; rows [row_begin, row_end) then go to out
+  uint64_t row_begin, row_end;
+  uint8_t *out;
 };
 
 // Batched decode: the chunk groups of all streams form one work list
@@ -787,8 +794,33 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_batch(const DecBatchIte
   }
 }
 
+// Range requests: copy rows [row_begin, row_end) from the decoded covering
+// chunks (and the raw trailing rows) to the request's output.
+__global__ void k_decode_batch_rows(const DecBatchItem *items) {
+  const DecBatchItem &it = items[blockIdx.y];
+  if (it.row_end <= it.row_begin) return;
+  const Geom &g = it.p.g;
+  const uint64_t rb = (uint64_t)g.D * g.wb;
+  const uint64_t r_full = min(it.row_end, g.full_rows);
+  const uint64_t base_row = (uint64_t)it.p.c_begin * g.chunk_rows;
+  const uint64_t n_mid = r_full > it.row_begin ? (r_full - it.row_begin) * rb : 0;
+  const uint8_t *from = it.p.dst + (it.row_begin - base_row) * rb;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_mid;
+       k += (uint64_t)gridDim.x * blockDim.x)
+    it.out[k] = from[k];
+  if (it.row_end > g.full_rows && blockIdx.x == 0) {
+    const uint64_t t0 = max(it.row_begin, g.full_rows);
+    const uint64_t tail_off = le_u64(it.p.src + 48);
+    const uint64_t nb = (it.row_end - t0) * rb;
+    const uint8_t *tail = it.p.src + tail_off + (t0 - g.full_rows) * rb;
+    if (tail_off + (g.tail_rows * rb) <= it.p.src_size)
+      for (uint64_t k = threadIdx.x; k < nb; k += blockDim.x) it.out[n_mid + k] = tail[k];
+  }
+}
+
 // Header check and raw tail of every stream of a batch (one CTA per stream).
 __global__ void k_decode_batch_tails(const DecBatchItem *items) {
+  const bool ranged = items[blockIdx.x].row_end > items[blockIdx.x].row_begin;
   const DecParams &p = items[blockIdx.x].p;
   const Geom &g = p.g;
   __shared__ uint32_t s_ok;
@@ -808,7 +840,7 @@ __global__ void k_decode_batch_tails(const DecBatchItem *items) {
     if (!ok) set_status(p.status, SPRINTZ_ERR_CORRUPT);
   }
   __syncthreads();
-  if (!s_ok) return;
+  if (!s_ok || ranged) return;
   const uint64_t tail_bytes = g.tail_rows * g.D * g.wb;
   uint8_t *d = p.dst + g.full_rows * g.D * g.wb;
   const uint8_t *src = p.src + s_tail_off;
@@ -890,6 +922,9 @@ int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchC
                       uint8_t *ws, BatchPlan *pl, std::vector<uint8_t> *img, std::vector<uint64_t> *pre) {
   (void)ws;
   std::vector<DecBatchItem> v(n);
+  std::vector<uint64_t> temp_off(n, 0);
+  uint64_t temp_total = 0;
+  bool any_ranged = false;
   pre->assign((size_t)n + 1, 0);
   uint32_t region = 0;
   static const uint32_t win = [] {
@@ -903,9 +938,12 @@ int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchC
     int rc = make_geom(it.rows, it.D, it.w, &it.opts, &g);
     if (rc != SPRINTZ_OK) return rc;
     if (it.opts.huffman || g.D > 32 || g.max_body >= (1ull << 28)) return SPRINTZ_ERR_UNSUPPORTED;
-    if (!it.src || (it.rows && !it.dst)) return SPRINTZ_ERR_INVALID_ARG;
-    if (((uintptr_t)it.dst & 7) != 0) return SPRINTZ_ERR_UNSUPPORTED;
-    if (it.dst_cap < it.rows * it.D * g.wb) return SPRINTZ_ERR_DST_TOO_SMALL;
+    const bool ranged = it.row_end > it.row_begin;
+    if (ranged && it.row_end > it.rows) return SPRINTZ_ERR_INVALID_ARG;
+    const uint64_t want_rows = ranged ? it.row_end - it.row_begin : it.rows;
+    if (!it.src || (want_rows && !it.dst)) return SPRINTZ_ERR_INVALID_ARG;
+    if (!ranged && ((uintptr_t)it.dst & 7) != 0) return SPRINTZ_ERR_UNSUPPORTED;
+    if (it.dst_cap < want_rows * it.D * g.wb) return SPRINTZ_ERR_DST_TOO_SMALL;
     if (it.src_bytes < g.data_off) return SPRINTZ_ERR_CORRUPT;
     DecBatchItem &d = v[i];
     memset(&d, 0, sizeof(d));
@@ -916,13 +954,35 @@ int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchC
     d.p.status = d_status;
     d.p.g = g;
     d.p.pf_win = win;
+    d.p.c_begin = 0;
+    d.p.c_end = g.n_chunks;
+    if (ranged) {
+      // decode the chunks covering the rows into a temporary of the workspace
+      const uint64_t r_full = std::min<uint64_t>(it.row_end, g.full_rows);
+      d.row_begin = it.row_begin;
+      d.row_end = it.row_end;
+      d.out = (uint8_t *)it.dst;
+      if (r_full > it.row_begin) {
+        d.p.c_begin = (uint32_t)(it.row_begin / g.chunk_rows);
+        d.p.c_end = (uint32_t)((r_full + g.chunk_rows - 1) / g.chunk_rows);
+      } else {
+        d.p.c_begin = d.p.c_end = 0;
+      }
+      const uint64_t tmp_rows =
+          std::min<uint64_t>((uint64_t)d.p.c_end * g.chunk_rows, g.full_rows) - (uint64_t)d.p.c_begin * g.chunk_rows;
+      d.p.dst = ws ? ws + temp_total : nullptr;  // completed below with the table offset
+      d.p.dst_cap = tmp_rows * g.D * g.wb;
+      temp_off[i] = temp_total;
+      temp_total = (temp_total + d.p.dst_cap + 255) & ~255ull;
+      any_ranged = true;
+    }
     if (g.n_chunks) {
       d.rg = lane_ring_plan(g, cfg, 2);
       if (!d.rg.per_warp) return SPRINTZ_ERR_UNSUPPORTED;
       region = std::max(region, d.rg.per_warp);
     }
     const uint64_t K = 32 / g.D;
-    (*pre)[i + 1] = (*pre)[i] + (g.n_chunks + K - 1) / K;
+    (*pre)[i + 1] = (*pre)[i] + (d.p.c_end - d.p.c_begin + K - 1) / K;
   }
   memset(pl, 0, sizeof(*pl));
   pl->compress = 0;
@@ -930,7 +990,11 @@ int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchC
   pl->region = std::max<uint32_t>(region, 16);
   pl->items_off = 0;
   pl->prefix_off = align256d((uint64_t)n * sizeof(DecBatchItem));
-  pl->ws_total = pl->prefix_off + 8ull * (n + 1);
+  pl->slots_off = align256d(pl->prefix_off + 8ull * (n + 1));  // range temporaries
+  pl->ws_total = pl->slots_off + temp_total;
+  pl->slot_region = any_ranged ? 1 : 0;
+  for (uint32_t i = 0; i < n; ++i)
+    if (v[i].row_end > v[i].row_begin) v[i].p.dst = ws ? ws + pl->slots_off + temp_off[i] : nullptr;
   const uint64_t smem = (uint64_t)kLaneWarps * pl->region;
   if (smem > (uint64_t)cfg.max_smem_optin) return SPRINTZ_ERR_UNSUPPORTED;
   if (smem > 48 * 1024)
@@ -954,6 +1018,7 @@ int run_batch_decode(const BatchPlan &pl, cudaStream_t stream) {
   k_decode_batch_tails<<<pl.n, 128, 0, stream>>>(items);
   k_decode_batch<<<pl.grid, kLaneThreads, (uint64_t)kLaneWarps * pl.region, stream>>>(items, pre, pl.n,
                                                                                      pl.region);
+  if (pl.slot_region) k_decode_batch_rows<<<dim3(8, pl.n), 256, 0, stream>>>(items);
   return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
 }
 
@@ -973,6 +1038,8 @@ int launch_decode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint6
   p.dst_cap = dst_cap;
   p.status = d_status;
   p.g = g;
+  p.c_begin = 0;
+  p.c_end = g.n_chunks;
   {
     static const uint32_t win = [] {
       const char *e = getenv("SPRINTZ_DEC_PF_WIN");

@@ -47,7 +47,8 @@ class _Info(ctypes.Structure):
 class _BatchItem(ctypes.Structure):
     _fields_ = [("src", ctypes.c_void_p), ("src_bytes", ctypes.c_uint64), ("dst", ctypes.c_void_p),
                 ("dst_cap", ctypes.c_uint64), ("out_size", ctypes.c_void_p), ("rows", ctypes.c_uint64),
-                ("D", ctypes.c_uint32), ("w", ctypes.c_uint32), ("opts", _Opts)]
+                ("D", ctypes.c_uint32), ("w", ctypes.c_uint32), ("opts", _Opts),
+                ("row_begin", ctypes.c_uint64), ("row_end", ctypes.c_uint64)]
 
 
 @dataclass(frozen=True)
@@ -280,11 +281,12 @@ class Codec:
 
     # ---- batches of independent streams -----------------------------------
 
-    def _items(self, rows_d_w_opts, srcs, src_bytes, dsts, out_sizes):
+    def _items(self, rows_d_w_opts, srcs, src_bytes, dsts, out_sizes, ranges=None):
         arr = (_BatchItem * len(rows_d_w_opts))()
         for k, (rows, D, w, o) in enumerate(rows_d_w_opts):
+            rb, re_ = ranges[k] if ranges else (0, 0)
             arr[k] = _BatchItem(ctypes.c_void_p(srcs[k]), src_bytes[k], ctypes.c_void_p(dsts[k][0]),
-                                dsts[k][1], ctypes.c_void_p(out_sizes[k]), rows, D, w, o.c())
+                                dsts[k][1], ctypes.c_void_p(out_sizes[k]), rows, D, w, o.c(), rb, re_)
         return arr
 
     def batch_plan_run(self, arr, compress: int, stream=None):
@@ -329,6 +331,23 @@ class Codec:
                           [sizes.data_ptr() + 8 * k for k in range(n)])
         ws = self.batch_plan_run(arr, 1, stream)
         return bufs, sizes, ws
+
+    def decompress_ranges(self, streams, infos, sizes, ranges, outs=None, stream=None):
+        """Range requests: rows [a, b) of each device stream, decoded in one
+        batched launch (only the covering chunks are decoded). Returns the
+        output tensors and the planned workspace."""
+        torch = self.torch
+        res, shapes, srcs, dsts = [], [], [], []
+        for k, (s, info, (a, b)) in enumerate(zip(streams, infos, ranges)):
+            dt = torch.uint8 if info.w == 8 else torch.int16
+            y = outs[k] if outs is not None else torch.empty((b - a, info.D), dtype=dt, device=s.device)
+            res.append(y)
+            shapes.append((info.rows, info.D, info.w, info.opts))
+            srcs.append(s.data_ptr())
+            dsts.append((y.data_ptr(), y.numel() * y.element_size()))
+        arr = self._items(shapes, srcs, list(sizes), dsts, [0] * len(streams), list(ranges))
+        ws = self.batch_plan_run(arr, 0, stream)
+        return res, ws
 
     def decompress_batch(self, streams, infos, sizes, stream=None):
         """Decompress device streams (with their host-parsed infos and byte
