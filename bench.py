@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--rows", type=int, default=ROWS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="sensor",
+                    choices=["sensor", "walk", "batch", "huffman", "serve"])
+    ap.add_argument("--streams", type=int, default=10_000, help="batch: number of streams")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     return ap.parse_args()
 
 
@@ -145,6 +149,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload != "sensor":
+        from paper_1808_02515_gb300 import bench_workloads
+        bench_workloads.run(args, METRIC, ClockSampler, peaks)
         return
 
     import torch

@@ -1,0 +1,203 @@
+"""Benchmark runners of the workloads other than the headline one (selected
+with bench.py --workload): the small single stream, the batch of 10,000
+streams (batched launch vs per-stream launches), the Huffman workload and
+the serving loop. Each prints one JSON line like bench.py's."""
+from __future__ import annotations
+
+import json
+import statistics
+import time
+
+import numpy as np
+
+
+def _events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def _time(fn, steps, stream):
+    import torch
+    a, b = _events(2)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def run(args, metric, ClockSampler, peaks):
+    import torch
+    import paper_1808_02515_gb300.sprintz as spz
+    from paper_1808_02515_gb300 import _build, synth
+    _build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    codec = spz.Codec(0)
+    stream = torch.cuda.current_stream(dev)
+    peak, peak_kind = peaks()
+    line = {"metric": metric, "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+            "impl": "ours", "workload_kind": args.workload}
+
+    def single(x, opts, label, w):
+        rows, D = x.shape
+        cap = spz.max_compressed_size(rows, D, w, opts)
+        dst = torch.empty(cap, dtype=torch.uint8, device=dev)
+        size = torch.zeros(1, dtype=torch.int64, device=dev)
+        wsn = spz.compress_workspace_size(rows, D, w, opts)
+        ws = torch.empty(max(wsn, 1), dtype=torch.uint8, device=dev)
+        codec.compress_into(x, rows, D, w, opts, dst, size, ws)
+        torch.cuda.synchronize()
+        codec.check()
+        C = int(size.item())
+        info = spz.query(dst[:64].cpu().numpy().tobytes())
+        wsd = spz.decompress_workspace_size(info)
+        ws_d = torch.empty(max(wsd, 1), dtype=torch.uint8, device=dev)
+        out = torch.empty_like(x)
+        for _ in range(args.warmup):
+            codec.compress_into(x, rows, D, w, opts, dst, size, ws)
+            codec.decompress_into(dst, C, info, out, ws_d)
+        torch.cuda.synchronize()
+        codec.check()
+        assert torch.equal(out, x), "round trip mismatch"
+        with ClockSampler(0) as clk:
+            enc = _time(lambda: codec.compress_into(x, rows, D, w, opts, dst, size, ws), args.steps, stream)
+            dec = _time(lambda: codec.decompress_into(dst, C, info, out, ws_d), args.steps, stream)
+        U = x.numel() * x.element_size()
+        extra = 16 * info.n_chunks
+        line.update({
+            "value": U / ((enc + dec) * 1e-3) / 1e9, "ms_per_step": enc + dec,
+            "compress_ms": enc, "decompress_ms": dec,
+            "compress_gbs": U / (enc * 1e-3) / 1e9, "decompress_gbs": U / (dec * 1e-3) / 1e9,
+            "dtype": "u8" if w == 8 else "u16",
+            "config": {"workload": label, "rows": rows, "D": D, "w": w, "forecaster": opts.forecaster,
+                       "huffman": opts.huffman, "chunk_rows": opts.chunk_rows, "group_blocks": opts.group_blocks,
+                       "huff_chunks": opts.huff_chunks, "uncompressed_bytes": U, "compressed_bytes": C,
+                       "ratio": U / C, "step": "compress + decompress round trip"},
+            "roofline": {"bound": "hbm", "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "decode_frac": (U + C) / (dec * 1e-3) / 1e9 / peak,
+                         "encode_frac": (U + C + extra) / (enc * 1e-3) / 1e9 / peak,
+                         "traffic": None},
+            "clocks": clk.summary()})
+
+    if args.workload == "walk":
+        x = torch.from_numpy(synth.random_walk_u8(100_000, 1, seed=0)).to(dev)
+        single(x, spz.Opts(forecaster=0), "random_walk_u8_D1_100000rows_delta", 8)
+        line["config"]["note"] = "100 KB: launch-latency bound; roofline not meaningful"
+    elif args.workload == "huffman":
+        x = synth.accel_u8_torch(1 << 28, 3, seed=3, device=dev)
+        single(x, spz.Opts(forecaster=1, huffman=1, huff_chunks=64), "accel_u8_D3_2^28rows_FIRE_huffman", 8)
+        line["config"]["generator"] = "accel_u8 recipe drawn on the GPU (torch)"
+    elif args.workload == "batch":
+        run_batch(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, synth, spz)
+    elif args.workload == "serve":
+        run_serve(args, codec, dev, line, synth, spz)
+    codec.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, synth, spz):
+    import torch
+    t0 = time.perf_counter()
+    xs = [synth.batch_stream_torch(i, device=dev) for i in range(args.streams)]
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    U = sum(x.numel() * x.element_size() for x in xs)
+    res = {}
+    for fc_name, fc in (("delta", 0), ("fire", 1)):
+        opts = spz.Opts(forecaster=fc)
+        bufs, sizes, ws_c = codec.compress_batch(xs, opts)
+        torch.cuda.synchronize()
+        codec.check()
+        sz = [int(v) for v in sizes.cpu().numpy()]
+        C = sum(sz)
+        infos = [spz.query(b[:64].cpu().numpy().tobytes()) for b in bufs]
+        outs, ws_d = codec.decompress_batch(bufs, infos, sz)
+        torch.cuda.synchronize()
+        codec.check()
+        for x, y in zip(xs, outs):
+            assert torch.equal(x, y), "batched round trip mismatch"
+        # the batched form: one plan, then batch_run per step
+        dec_b = _time(lambda: codec.batch_run(ws_d), args.steps, stream)
+        _, _, ws_c = codec.compress_batch(xs, opts)
+        enc_b = _time(lambda: codec.batch_run(ws_c), args.steps, stream)
+        # per-stream launches of the same work (one shared workspace: the
+        # launches run one after another on the same CUDA stream)
+        shapes = [((x.view(-1, 1) if x.dim() == 1 else x).shape, 8 if x.dtype == torch.uint8 else 16)
+                  for x in xs]
+        ws_e = torch.empty(max(spz.compress_workspace_size(r, d, w, opts) for (r, d), w in shapes),
+                           dtype=torch.uint8, device=dev)
+        ws_dd = torch.empty(max(max(spz.decompress_workspace_size(i) for i in infos), 1),
+                            dtype=torch.uint8, device=dev)
+
+        def per_stream_enc():
+            for k, (x, b) in enumerate(zip(xs, bufs)):
+                (rows, D), w = shapes[k]
+                codec.compress_into(x, rows, D, w, opts, b, sizes[k:k + 1], ws_e)
+
+        def per_stream_dec():
+            for b, info, n, y in zip(bufs, infos, sz, outs):
+                codec.decompress_into(b, n, info, y, ws_dd)
+        per_stream_enc()
+        per_stream_dec()
+        torch.cuda.synchronize()
+        enc_s = _time(per_stream_enc, max(1, args.steps // 5), stream)
+        dec_s = _time(per_stream_dec, max(1, args.steps // 5), stream)
+        res[fc_name] = dict(C=C, enc_b=enc_b, dec_b=dec_b, enc_s=enc_s, dec_s=dec_s)
+    f = res["fire"]
+    line.update({
+        "value": U / ((f["enc_b"] + f["dec_b"]) * 1e-3) / 1e9, "ms_per_step": f["enc_b"] + f["dec_b"],
+        "dtype": "u8/u16",
+        "config": {"workload": f"batch_{args.streams}_streams_log_uniform_1e3_1e6_rows_D1-16_u8u16",
+                   "streams": args.streams, "uncompressed_bytes": U, "generator_s": gen_s,
+                   "generator": "batch_stream recipe drawn on the GPU (torch)",
+                   "step": "batched compress + batched decompress (FIRE)"},
+        "batched": {k: {"compress_gbs": U / (v["enc_b"] * 1e-3) / 1e9,
+                        "decompress_gbs": U / (v["dec_b"] * 1e-3) / 1e9,
+                        "compressed_bytes": v["C"], "ratio": U / v["C"],
+                        "decode_frac": (U + v["C"]) / (v["dec_b"] * 1e-3) / 1e9 / peak,
+                        "encode_frac": (U + v["C"]) / (v["enc_b"] * 1e-3) / 1e9 / peak}
+                    for k, v in res.items()},
+        "per_stream_launches": {k: {"compress_gbs": U / (v["enc_s"] * 1e-3) / 1e9,
+                                    "decompress_gbs": U / (v["dec_s"] * 1e-3) / 1e9}
+                                for k, v in res.items()},
+        "roofline": {"bound": "hbm", "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "traffic": None}})
+
+
+def run_serve(args, codec, dev, line, synth, spz):
+    import torch
+    from paper_1808_02515_gb300 import serve
+    n_streams, rows, D = 1000, 1 << 20, 4
+    t0 = time.perf_counter()
+    xs = [synth.sensor_u16_torch(rows, D, seed=4000 + i, device=dev) for i in range(n_streams)]
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    opts = spz.Opts(forecaster=1)
+    store = serve.ShardStore(codec, D, 16, opts)
+    store.add_streams(xs)
+    del xs
+    torch.cuda.synchronize()
+    pool = [synth.sensor_u16_torch(8192, D, seed=500000 + k, device=dev) for k in range(64)]
+    rate = 20000.0
+    n_req = int(rate * (args.serve_seconds + 1.0))
+    reqs = serve.poisson_requests(store, n_req, rate=rate, seed=4, append_frac=0.1, append_rows=8192,
+                                  append_source=lambda sid, k: pool[(sid * 7 + k) % len(pool)])
+    server = serve.Server(store, mem_budget=4 << 30, max_batch=512, n_slots=3)
+    stats = server.run(reqs, realtime=True)
+    warm = [r for r in reqs if r.t_arrival >= 1.0]
+    lat = np.array([r.t_done - r.t_arrival for r in warm])
+    rb = D * 2
+    served = sum((r.b - r.a) * rb if r.kind == "range" else r.rows.shape[0] * rb for r in warm)
+    span = max(r.t_done for r in warm) - min(r.t_arrival for r in warm)
+    line.update({
+        "value": served / span / 1e9, "ms_per_step": None, "dtype": "u16",
+        "config": {"workload": "serve_1000_streams_u16_D4_2^20rows_poisson_20k_req_s",
+                   "rate_req_s": rate, "requests": len(reqs), "measured_requests": len(warm),
+                   "mix": "90% range 1K-64K rows (log-uniform, uniform start), 10% append 8192 rows",
+                   "generator_s": gen_s, "mem_budget": 4 << 30, "slots": 3, "max_batch": 512},
+        "serving": {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                    "gbs": served / span / 1e9, "batches": stats["batches"], "peak_mem": stats["peak_mem"],
+                    "wall_s": stats["wall_s"]}})

@@ -151,3 +151,99 @@ def batch_stream(idx: int, max_rows: int = 1_000_000, min_rows: int = 1_000) -> 
 DELTA, FIRE = 0, 1
 DEFAULT_OPTS = dict(forecaster=FIRE, huffman=0, group_blocks=2, learn_shift=1,
                     chunk_rows=1024, huff_chunks=64)
+
+
+# ---------------------------------------------------------------------------
+# The same recipes drawn on the GPU with torch (for the large benchmark
+# workloads: tens of GB would take minutes in numpy). Scalar parameters come
+# from numpy PCG64 with the same seeds; the bulk draws from a torch CUDA
+# generator seeded alike, so these series follow the same distributions as
+# the numpy ones above but are different samples.
+# ---------------------------------------------------------------------------
+
+def _tgen(seed: int, device):
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    return g
+
+
+def random_walk_u8_torch(rows: int, cols: int, scale: float, const_frac: float, seed: int,
+                         device="cuda"):
+    import torch
+    g = _tgen(seed, device)
+    p = 1.0 - math.exp(-1.0 / scale)
+    s = (torch.empty((rows, cols), device=device).geometric_(p, generator=g)
+         - torch.empty((rows, cols), device=device).geometric_(p, generator=g)).to(torch.int64)
+    n_blocks = (rows + BLOCK_ROWS - 1) // BLOCK_ROWS
+    flat = torch.rand(n_blocks, generator=g, device=device) < const_frac
+    s[flat.repeat_interleave(BLOCK_ROWS)[:rows]] = 0
+    return (torch.cumsum(s, 0) % 256).to(torch.uint8)
+
+
+def sensor_u16_torch(rows: int, cols: int, seed: int, flat_frac: float = 0.05, device="cuda"):
+    """uint16 samples as an int16 tensor (the same bits)."""
+    import torch
+    rng = _rng(seed)
+    g = _tgen(seed, device)
+    t = torch.arange(rows, dtype=torch.float64, device=device)
+    x = torch.empty((rows, cols), dtype=torch.int32, device=device)
+    for j in range(cols):
+        v = torch.randn(rows, generator=g, dtype=torch.float64, device=device) * 20.0
+        for _ in range(2):
+            period, amp, phase = rng.uniform(50.0, 5000.0), rng.uniform(0.0, 8000.0), rng.uniform(0.0, 2 * math.pi)
+            v += amp * torch.sin(2.0 * math.pi * t / period + phase)
+        x[:, j] = torch.clamp(torch.round(v) + 32768.0, 0, 65535).to(torch.int32)
+    # flat stretches over flat_frac of the rows, every column held
+    target = int(flat_frac * rows)
+    done, attempts = 0, 0
+    covered = np.zeros(rows, dtype=bool)
+    while done < target and attempts < 100_000 and rows >= 32:
+        attempts += 1
+        length = min(int(math.exp(rng.uniform(math.log(16), math.log(8192)))), rows - 1)
+        start = int(rng.integers(0, rows - length + 1))
+        if covered[start:start + length].any():
+            continue
+        covered[start:start + length] = True
+        x[start:start + length] = x[start]
+        done += length
+    return (x - 65536 * (x >= 32768)).to(torch.int16)
+
+
+def accel_u8_torch(rows: int, cols: int = 3, seed: int = 3, fs_hz: float = 100.0, device="cuda"):
+    import torch
+    rng = _rng(seed)
+    g = _tgen(seed, device)
+    p = 1.0 - math.exp(-1.0 / 0.25)
+    x = torch.empty((rows, cols), dtype=torch.uint8, device=device)
+    step = 1 << 24
+    for j in range(cols):
+        amp, freq, phase = rng.uniform(10.0, 30.0), rng.uniform(1.0, 3.0), rng.uniform(0.0, 2 * math.pi)
+        level = 0
+        for r0 in range(0, rows, step):
+            n = min(step, rows - r0)
+            s = (torch.empty(n, device=device).geometric_(p, generator=g)
+                 - torch.empty(n, device=device).geometric_(p, generator=g)).to(torch.int64)
+            walk = level + torch.cumsum(s, 0)
+            level = int(walk[-1].item())
+            u = torch.remainder(walk + 60, 240)
+            folded = torch.where(u <= 120, u, 240 - u) - 60
+            t = torch.arange(r0, r0 + n, dtype=torch.float64, device=device)
+            v = 128.0 + folded + amp * torch.sin(2.0 * math.pi * freq * t / fs_hz + phase)
+            # Laplace(0, 3): the difference of two exponentials of mean 3
+            lap = (torch.empty(n, dtype=torch.float64, device=device).exponential_(1.0 / 3.0, generator=g)
+                   - torch.empty(n, dtype=torch.float64, device=device).exponential_(1.0 / 3.0, generator=g))
+            v += torch.round(lap)
+            x[r0:r0 + n, j] = torch.clamp(torch.round(v), 0, 255).to(torch.uint8)
+    return x
+
+
+def batch_stream_torch(idx: int, max_rows: int = 1_000_000, min_rows: int = 1_000, device="cuda"):
+    """Stream `idx` of the batched workload (same recipe as batch_stream)."""
+    rng = _rng(2 + idx)
+    rows = int(math.exp(rng.uniform(math.log(min_rows), math.log(max_rows))))
+    cols = int(rng.integers(1, 17))
+    if idx % 2 == 0:
+        return random_walk_u8_torch(rows, cols, scale=rng.uniform(0.5, 4.0),
+                                    const_frac=rng.uniform(0.0, 0.4), seed=2 + idx, device=device)
+    return sensor_u16_torch(rows, cols, seed=2 + idx, device=device)
