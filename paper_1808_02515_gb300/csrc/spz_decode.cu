@@ -466,13 +466,13 @@ constexpr uint32_t kRingWaitLimit = 1u << 22;
 
 // Decode chunk group `warp_id` (K consecutive chunks) of one stream with one
 // warp whose shared region (stage, barriers, rings) starts at wsm.
-template <int W>
+template <int W, int DT>
 __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing &rg, uint64_t warp_id,
                                              uint8_t *wsm) {
   const Geom &g = p.g;
-  const uint32_t D = g.D;
+  const uint32_t D = DT ? (uint32_t)DT : g.D;  // columns: a compile-time constant for common D
   const uint32_t K = 32 / D;
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lane = threadIdx.x & 31;
   const uint32_t kk = lane / D, j = lane % D;
   const uint32_t kc = kk < K ? kk : K - 1;  // idle lanes alias the last slot, never touch it
   const uint32_t seg0 = lane - j;            // first lane of this chunk's segment
@@ -750,13 +750,27 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
   __syncwarp();
 }
 
-template <int W>
+template <int W, int DT>
 __global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p, LaneRing rg) {
   extern __shared__ __align__(16) uint8_t dsm[];
   const uint32_t warp = threadIdx.x >> 5;
   const DecParams pp = p;
   const LaneRing rr = rg;
-  decode_group<W>(pp, rr, (uint64_t)blockIdx.x * kLaneWarps + warp, dsm + (uint64_t)warp * rr.per_warp);
+  decode_group<W, DT>(pp, rr, (uint64_t)blockIdx.x * kLaneWarps + warp, dsm + (uint64_t)warp * rr.per_warp);
+}
+
+// The lane decoder specialised for the column count (0: any D <= 32).
+template <int W>
+static const void *lane_decoder(uint32_t D) {
+  switch (D) {
+    case 1: return (const void *)k_decode_lanes<W, 1>;
+    case 2: return (const void *)k_decode_lanes<W, 2>;
+    case 3: return (const void *)k_decode_lanes<W, 3>;
+    case 4: return (const void *)k_decode_lanes<W, 4>;
+    case 8: return (const void *)k_decode_lanes<W, 8>;
+    case 16: return (const void *)k_decode_lanes<W, 16>;
+    default: return (const void *)k_decode_lanes<W, 0>;
+  }
 }
 
 // One stream of a batched decode.
@@ -788,9 +802,9 @@ __global__ void __launch_bounds__(kLaneThreads) k_decode_batch(const DecBatchIte
     }
     const DecBatchItem it = items[lo];
     if (it.p.g.w == 8)
-      decode_group<8>(it.p, it.rg, item - gprefix[lo], wsm);
+      decode_group<8, 0>(it.p, it.rg, item - gprefix[lo], wsm);
     else
-      decode_group<16>(it.p, it.rg, item - gprefix[lo], wsm);
+      decode_group<16, 0>(it.p, it.rg, item - gprefix[lo], wsm);
   }
 }
 
@@ -1059,14 +1073,13 @@ int launch_decode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint6
     const uint64_t grid = (warps + kLaneWarps - 1) / kLaneWarps;
     if (grid > 0x7FFFFFFFull) return SPRINTZ_ERR_INVALID_ARG;
     const uint64_t smem = (uint64_t)rg.per_warp * kLaneWarps;
-    const void *fn = g.w == 8 ? (const void *)k_decode_lanes<8> : (const void *)k_decode_lanes<16>;
+    const void *fn = g.w == 8 ? lane_decoder<8>(g.D) : lane_decoder<16>(g.D);
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return SPRINTZ_ERR_CUDA;
-    if (g.w == 8)
-      k_decode_lanes<8><<<(uint32_t)grid, kLaneThreads, smem, stream>>>(p, rg);
-    else
-      k_decode_lanes<16><<<(uint32_t)grid, kLaneThreads, smem, stream>>>(p, rg);
+    void *args[] = {&p, &rg};
+    if (cudaLaunchKernel(fn, dim3((uint32_t)grid), dim3(kLaneThreads), args, smem, stream) != cudaSuccess)
+      return SPRINTZ_ERR_CUDA;
   } else if (g.n_chunks > 0) {
     DecPlan pl = dec_plan(g, cfg);
     if (ws_bytes < (uint64_t)pl.grid * pl.scratch_per_cta) return SPRINTZ_ERR_WS_TOO_SMALL;

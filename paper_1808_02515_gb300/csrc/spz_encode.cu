@@ -840,11 +840,11 @@ struct EncSlotCfg {
 
 // Encode chunk group `grp` of one stream with one warp: wsm is the warp's
 // shared region (stage, then K rings), wslots its K body slots.
-template <int W>
+template <int W, int DT>
 __device__ __forceinline__ void encode_group_slots(const EncParams &p, const EncSlotCfg &cfg, uint32_t grp,
                                                    uint8_t *wsm, uint8_t *wslots) {
   const Geom &g = p.g;
-  const uint32_t D = g.D;
+  const uint32_t D = DT ? (uint32_t)DT : g.D;  // a compile-time constant for common D
   const uint32_t K = 32 / D;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t kk = lane / D, j = lane % D;
@@ -1127,7 +1127,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
   }
 }
 
-template <int W>
+template <int W, int DT>
 __global__ void __launch_bounds__(kEncLaneThreads, 7) k_encode_slots(EncParams p, EncSlotCfg cfg) {
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1141,7 +1141,21 @@ __global__ void __launch_bounds__(kEncLaneThreads, 7) k_encode_slots(EncParams p
     if (lane == 0) grp = atomicAdd(p.ticket, 1u);
     grp = __shfl_sync(0xFFFFFFFFu, grp, 0);
     if (grp >= cfg.n_groups) break;
-    encode_group_slots<W>(p, cfg, grp, wsm, wslots);
+    encode_group_slots<W, DT>(p, cfg, grp, wsm, wslots);
+  }
+}
+
+// The slot encoder specialised for the column count (0: any D <= 32).
+template <int W>
+static const void *slot_encoder(uint32_t D) {
+  switch (D) {
+    case 1: return (const void *)k_encode_slots<W, 1>;
+    case 2: return (const void *)k_encode_slots<W, 2>;
+    case 3: return (const void *)k_encode_slots<W, 3>;
+    case 4: return (const void *)k_encode_slots<W, 4>;
+    case 8: return (const void *)k_encode_slots<W, 8>;
+    case 16: return (const void *)k_encode_slots<W, 16>;
+    default: return (const void *)k_encode_slots<W, 0>;
   }
 }
 
@@ -1177,9 +1191,9 @@ __global__ void __launch_bounds__(kEncLaneThreads) k_encode_batch(const EncBatch
     const EncBatchItem it = items[lo];
     const uint32_t grp = (uint32_t)(item - gprefix[lo]);
     if (it.p.g.w == 8)
-      encode_group_slots<8>(it.p, it.cfg, grp, wsm, wslots);
+      encode_group_slots<8, 0>(it.p, it.cfg, grp, wsm, wslots);
     else
-      encode_group_slots<16>(it.p, it.cfg, grp, wsm, wslots);
+      encode_group_slots<16, 0>(it.p, it.cfg, grp, wsm, wslots);
   }
 }
 
@@ -1379,16 +1393,15 @@ int launch_encode_fast(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, 
   p.lookback = reinterpret_cast<uint64_t *>(ws + 16);
   EncSlotCfg sc = sp.sc;
   sc.slots = ws + sp.ws_base;
-  const void *fn = g.w == 8 ? (const void *)k_encode_slots<8> : (const void *)k_encode_slots<16>;
+  const void *fn = g.w == 8 ? slot_encoder<8>(g.D) : slot_encoder<16>(g.D);
   if (sp.smem > 48 * 1024 &&
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem) != cudaSuccess)
     return SPRINTZ_ERR_CUDA;
   if (cudaMemsetAsync(ws, 0, 16 + 8ull * sc.n_groups, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
-  if (g.w == 8)
-    k_encode_slots<8><<<sp.grid, kEncLaneThreads, sp.smem, stream>>>(p, sc);
-  else
-    k_encode_slots<16><<<sp.grid, kEncLaneThreads, sp.smem, stream>>>(p, sc);
-  return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
+  void *args[] = {&p, &sc};
+  if (cudaLaunchKernel(fn, dim3(sp.grid), dim3(kEncLaneThreads), args, sp.smem, stream) != cudaSuccess)
+    return SPRINTZ_ERR_CUDA;
+  return SPRINTZ_OK;
 }
 
 // ---- batches ----------------------------------------------------------------
