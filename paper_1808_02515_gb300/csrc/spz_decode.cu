@@ -423,7 +423,16 @@ __global__ void k_decode_header_tail(DecParams p) {
 
 constexpr int kLaneThreads = 128;
 constexpr int kLaneWarps = kLaneThreads / 32;
-constexpr uint32_t kStageBytes = 512;  // K * 8 rows * D columns * 2 bytes <= 512
+
+// Bytes between the staged blocks of consecutive chunks of a warp.  When a row
+// is a whole number of 8-byte words, the stride is padded so that chunk k's
+// stage starts k * D * wb bytes (mod 128) into the shared-memory banks: the
+// row stores of the warp's chunks then fall into disjoint banks.
+__host__ __device__ inline uint32_t dec_stage_stride(uint32_t D, uint32_t wb) {
+  const uint32_t row = D * wb, blk = kBlockRows * row;
+  if (row % 8) return blk;
+  return blk + ((row - blk) & 127u);
+}
 
 // n (<= 16) bits at bit position `bit` of 4-byte-aligned memory `w`.
 __device__ __forceinline__ uint32_t bits_at(const uint32_t *w, uint64_t bit, uint32_t n) {
@@ -489,6 +498,7 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
   const uint32_t wb = W / 8;
   const uint32_t hb = g.hb, G = g.G;
   const uint32_t blk_bytes = kBlockRows * D * wb;  // one chunk's block of output
+  const uint32_t stage_stride = dec_stage_stride(D, wb);
   const uint32_t gmax = g.hdr_bytes + G * D * W;   // largest header group (bytes)
 
   // the chunk bodies end at tail_off
@@ -587,11 +597,11 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
     const uint32_t k2 = has[t] ? q / words_per : 0;
     const uint32_t wq = has[t] ? q % words_per : 0;
     from_lane[t] = k2 * D;
-    src_word[t] = q;
+    src_word[t] = k2 * (stage_stride / 8) + wq;
     const uint64_t r2 = (warp_id * K + k2) * g.chunk_rows;  // rows from chunk c_begin
     dptr[t] = reinterpret_cast<uint64_t *>(p.dst + r2 * D * wb) + wq;
   }
-  uint8_t *my_stage = stage + kc * blk_bytes + j * wb;
+  uint8_t *my_stage = stage + kc * stage_stride + j * wb;
   const uint32_t row_stride = D * wb;
   auto put = [&](int i, uint32_t v) {
     if (W == 8)
@@ -873,7 +883,7 @@ static LaneRing lane_ring_plan(const Geom &g, const LaunchCfg &cfg, uint32_t nse
   }
   r.nseg = nseg_want;
   auto layout = [&](LaneRing &x) {
-    x.bars_off = kStageBytes;
+    x.bars_off = (K * dec_stage_stride(g.D, g.wb) + 15) & ~15u;
     x.rings_off = x.bars_off + ((K * x.nseg * 8 + 15) & ~15u);
     x.per_warp = x.rings_off + K * x.nseg * x.seg;
   };

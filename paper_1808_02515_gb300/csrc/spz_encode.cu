@@ -504,6 +504,49 @@ __device__ __forceinline__ void ring_or(uint32_t *ring, uint32_t ring_words, uin
   if (sh + n > 32) atomicOr(&ring[(wi + 1) & (ring_words - 1)], v >> (32 - sh));
 }
 
+// Decoupled look-back over chunk groups with the whole warp: each lane reads
+// one of the 32 nearest unread predecessors' words; the run of published
+// aggregates up to the nearest inclusive prefix is summed at once.  The group
+// publishes its aggregate first and its inclusive prefix last.  Waits are
+// bounded (SPRINTZ_ERR_TIMEOUT).  Returns the exclusive prefix in every lane.
+__device__ uint64_t lookback_warp(uint64_t *lb, uint32_t grp, uint64_t total, int *status) {
+  const uint32_t lane = threadIdx.x & 31;
+  if (grp == 0) {
+    if (lane == 0) st_release_u64(&lb[0], kFlagPrefix | total);
+    return 0;
+  }
+  if (lane == 0) st_release_u64(&lb[grp], kFlagAggregate | total);
+  uint64_t prefix = 0;
+  int64_t k = (int64_t)grp - 1;  // nearest predecessor not yet summed
+  uint32_t spins = 0;
+  while (true) {
+    const int64_t idx = k - (int64_t)lane;
+    const uint64_t w = idx >= 0 ? ld_acquire_u64(&lb[idx]) : kFlagPrefix;  // before group 0: prefix 0
+    const uint64_t flag = w & ~kValueMask;
+    const uint32_t pend = __ballot_sync(0xFFFFFFFFu, flag == 0);
+    const uint32_t pref = __ballot_sync(0xFFFFFFFFu, flag == kFlagPrefix);
+    const uint32_t np = pref ? __ffs(pref) - 1 : 32u;  // lane of the nearest prefix
+    const uint32_t nq = pend ? __ffs(pend) - 1 : 32u;  // lane of the nearest unpublished group
+    const bool done = np < nq;
+    const uint32_t take = done ? np + 1 : nq;
+    uint64_t v = lane < take ? (w & kValueMask) : 0;
+#pragma unroll
+    for (uint32_t o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    prefix += v;
+    if (done) break;
+    k -= take;
+    if (take == 0) {
+      if (++spins > kSpinLimit) {
+        if (lane == 0) set_status(status, SPRINTZ_ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(32);
+    }
+  }
+  if (lane == 0) st_release_u64(&lb[grp], kFlagPrefix | (prefix + total));
+  return prefix;
+}
+
 // Per-chunk state of one pass.
 struct EncRun {
   uint32_t xp;   // x_{i-1}
@@ -747,34 +790,7 @@ __global__ void __launch_bounds__(kEncLaneThreads) k_encode_lanes(EncParams p, E
     const uint64_t group_total = __shfl_sync(0xFFFFFFFFu, v, 31);
     const uint64_t excl = __shfl_sync(0xFFFFFFFFu, v, seg0) - __shfl_sync(0xFFFFFFFFu, (live && j == 0) ? S : 0ull, seg0);
     // look-back over groups
-    uint64_t prefix = 0;
-    if (lane == 0) {
-      uint64_t *lb = p.lookback;
-      if (grp == 0) {
-        st_release_u64(&lb[0], kFlagPrefix | group_total);
-      } else {
-        st_release_u64(&lb[grp], kFlagAggregate | group_total);
-        int64_t k = (int64_t)grp - 1;
-        uint32_t spins = 0;
-        while (k >= 0) {
-          const uint64_t w = ld_acquire_u64(&lb[k]);
-          const uint64_t flag = w & ~kValueMask;
-          if (flag == 0) {
-            if (++spins > kSpinLimit) {
-              set_status(p.status, SPRINTZ_ERR_TIMEOUT);
-              break;
-            }
-            __nanosleep(32);
-            continue;
-          }
-          prefix += w & kValueMask;
-          if (flag == kFlagPrefix) break;
-          --k;
-        }
-        st_release_u64(&lb[grp], kFlagPrefix | (prefix + group_total));
-      }
-    }
-    prefix = __shfl_sync(0xFFFFFFFFu, prefix, 0);
+    const uint64_t prefix = lookback_warp(p.lookback, grp, group_total, p.status);
     const uint64_t off = prefix + excl;
 
     // pass B: the body at its place
@@ -831,6 +847,44 @@ __global__ void __launch_bounds__(kEncLaneThreads) k_encode_lanes(EncParams p, E
 // by the same warp, so they stay in L2.
 // ---------------------------------------------------------------------------
 
+// Appends bit fields to the chunk's shared ring from bit position `bit` on:
+// whole 32-bit words are OR-ed in as they fill, so one lane touches each
+// word once (the first and last words may be shared with other writers).
+struct BitSink {
+  uint32_t *ring;
+  uint32_t wmask, w, lo, fill;
+  __device__ __forceinline__ BitSink(uint32_t *r, uint32_t wm, uint32_t bit)
+      : ring(r), wmask(wm), w((bit >> 5) & wm), lo(0), fill(bit & 31) {}
+  // v < 2^n, n <= 32
+  __device__ __forceinline__ void put(uint32_t v, uint32_t n) {
+    const uint32_t f = fill;
+    lo |= v << f;
+    fill = f + n;
+    if (fill >= 32) {
+      if (lo) atomicOr(&ring[w], lo);
+      w = (w + 1) & wmask;
+      lo = __funnelshift_l(v, 0u, f);  // the bits of v past the word
+      fill -= 32;
+    }
+  }
+  __device__ __forceinline__ void finish() {
+    if (lo) atomicOr(&ring[w], lo);
+  }
+};
+
+// Transposition tile of the row-major packer: per chunk, D columns of 8
+// entries (zigzagged error | width << 16), 48 bytes per column so that the
+// lanes' 16-byte stores of a quarter warp fall into distinct banks, and
+// chunks 32 bytes apart modulo 128 so that the row owners' loads do too.
+__host__ __device__ inline uint32_t enc_tile_stride(uint32_t D) {
+  const uint32_t t = D * 48;
+  return t + ((((32u - t) & 127u) + 15u) & ~15u);
+}
+__host__ __device__ inline uint32_t enc_slot_region(const Geom &g, uint32_t window) {
+  const uint32_t K = 32 / g.D;
+  return kEncStage + K * enc_tile_stride(g.D) + K * window;
+}
+
 struct EncSlotCfg {
   uint32_t window;       // ring bytes per chunk (power of two)
   uint32_t n_groups;
@@ -854,8 +908,14 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
   const uint32_t G = g.G, hb = g.hb, H = g.hdr_bytes;
   (void)warp;
   uint8_t *stage = wsm;
-  uint32_t *ring = reinterpret_cast<uint32_t *>(wsm + kEncStage + (uint64_t)kc * cfg.window);
+  const uint32_t tile_stride = enc_tile_stride(D);
+  uint32_t *tile = reinterpret_cast<uint32_t *>(wsm + kEncStage + kc * tile_stride);
+  uint32_t *ring = reinterpret_cast<uint32_t *>(wsm + kEncStage + K * tile_stride + (uint64_t)kc * cfg.window);
   const uint32_t ring_wmask = cfg.window / 4 - 1, ring_bitmask = cfg.window * 8 - 1;
+  const uint32_t seg_mask = D == 32 ? 0xFFFFFFFFu : ((1u << D) - 1u) << seg0;
+  // the chunk's header codes fit one word and combine by butterfly shuffles
+  constexpr uint32_t HB = W == 8 ? 3u : 4u;
+  constexpr bool kHdrShfl = DT != 0 && (DT & (DT - 1)) == 0 && DT * HB <= 32;
   uint8_t *slot = wslots + (uint64_t)kc * cfg.slot_stride;
 
   // cooperative stage loads: this lane's (up to two) 8-byte words of a block step
@@ -996,6 +1056,13 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
         }
       }
       const uint32_t total = __shfl_sync(0xFFFFFFFFu, v, last);
+      if (here && !g.col_major) {
+        uint4 *t4 = reinterpret_cast<uint4 *>(tile + j * 12);
+        const uint32_t nh = n << 16;
+        t4[0] = make_uint4(z[0] | nh, z[1] | nh, z[2] | nh, z[3] | nh);
+        t4[1] = make_uint4(z[4] | nh, z[5] | nh, z[6] | nh, z[7] | nh);
+      }
+      __syncwarp();
       if (here) {
         if (total == 0) {
           if (++run == kMaxRun) {
@@ -1010,12 +1077,41 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
           start_record();
           const uint32_t prefix = v - n;
           const uint32_t size = g.col_major ? total : (total + 7) & ~7u;
-          ror(hpos * 8 + (gs * D + j) * hb, n == W ? W - 1 : n, hb);
-          if (n) {
-            const uint32_t b0 = g.col_major ? (pos + prefix) * 8 : pos * 8 + prefix;
-            const uint32_t st = g.col_major ? n : size;  // size bytes = 8 rows * R: bits per row = size
+          const uint32_t code = n == W ? W - 1 : n;
+          if (kHdrShfl) {
+            uint32_t hv = code << (j * HB);
 #pragma unroll
-            for (int i = 0; i < kBlockRows; ++i) ror(b0 + i * st, z[i], n);
+            for (uint32_t o = 1; o < (DT ? (uint32_t)DT : 1u); o <<= 1) hv |= __shfl_xor_sync(seg_mask, hv, o);
+            if (j == 0) {
+              BitSink hs(ring, ring_wmask, hpos * 8 + gs * D * HB);
+              hs.put(hv, D * HB);
+              hs.finish();
+            }
+          } else {
+            ror(hpos * 8 + (gs * D + j) * hb, code, hb);
+          }
+          if (g.col_major) {
+            // column j: its 8 values of n bits, contiguous from byte pos + prefix
+            if (n) {
+              BitSink bs(ring, ring_wmask, (pos + prefix) * 8);
+#pragma unroll
+              for (int i = 0; i < kBlockRows; ++i) bs.put(z[i], n);
+              bs.finish();
+            }
+          } else {
+            // rows j, j + D, ...: each the concatenation of its D fields
+            // (size bits per row), gathered from the tile
+            (void)prefix;
+            const uint32_t *tc = tile;  // this chunk's tile
+            for (uint32_t i = j; i < kBlockRows; i += D) {
+              BitSink bs(ring, ring_wmask, pos * 8 + i * size);
+#pragma unroll 8
+              for (uint32_t c = 0; c < D; ++c) {
+                const uint32_t e = tc[c * 12 + i];
+                bs.put(e & 0xFFFFu, e >> 16);
+              }
+              bs.finish();
+            }
           }
           end_record(size);
         }
@@ -1048,34 +1144,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
     }
     const uint64_t group_total = __shfl_sync(0xFFFFFFFFu, v, 31);
     const uint64_t excl = __shfl_sync(0xFFFFFFFFu, v, seg0) - __shfl_sync(0xFFFFFFFFu, (uint64_t)S, seg0);
-    uint64_t prefix = 0;
-    if (lane == 0) {
-      uint64_t *lb = p.lookback;
-      if (grp == 0) {
-        st_release_u64(&lb[0], kFlagPrefix | group_total);
-      } else {
-        st_release_u64(&lb[grp], kFlagAggregate | group_total);
-        int64_t k = (int64_t)grp - 1;
-        uint32_t spins = 0;
-        while (k >= 0) {
-          const uint64_t w = ld_acquire_u64(&lb[k]);
-          const uint64_t flag = w & ~kValueMask;
-          if (flag == 0) {
-            if (++spins > kSpinLimit) {
-              set_status(p.status, SPRINTZ_ERR_TIMEOUT);
-              break;
-            }
-            __nanosleep(32);
-            continue;
-          }
-          prefix += w & kValueMask;
-          if (flag == kFlagPrefix) break;
-          --k;
-        }
-        st_release_u64(&lb[grp], kFlagPrefix | (prefix + group_total));
-      }
-    }
-    prefix = __shfl_sync(0xFFFFFFFFu, prefix, 0);
+    const uint64_t prefix = lookback_warp(p.lookback, grp, group_total, p.status);
     const uint64_t off = prefix + excl;
 
     // the body to its place: bytes up to a 16-byte boundary, 16-byte units
@@ -1087,15 +1156,30 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
       const uint32_t n16 = (S - head) / 16;
       const uint32_t sh = (head & 3) * 8;
       const uint32_t *sw = reinterpret_cast<const uint32_t *>(slot + (head & ~3u));
-      for (uint32_t u = j; u < n16; u += D) {
-        const uint32_t *q = sw + 4 * u;
-        const uint32_t a0 = q[0], a1 = q[1], a2 = q[2], a3 = q[3], a4 = q[4];
-        uint4 o;
-        o.x = __funnelshift_r(a0, a1, sh);
-        o.y = __funnelshift_r(a1, a2, sh);
-        o.z = __funnelshift_r(a2, a3, sh);
-        o.w = __funnelshift_r(a3, a4, sh);
-        *reinterpret_cast<uint4 *>(d + head + 16 * u) = o;
+      // four units per lane in flight: all loads before the stores
+      for (uint32_t u0 = j; u0 < n16; u0 += 4 * D) {
+        uint32_t a[4][5];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const uint32_t u = u0 + t * D;
+          if (u < n16) {
+            const uint32_t *q = sw + 4 * u;
+#pragma unroll
+            for (int e = 0; e < 5; ++e) a[t][e] = q[e];
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const uint32_t u = u0 + t * D;
+          if (u < n16) {
+            uint4 o;
+            o.x = __funnelshift_r(a[t][0], a[t][1], sh);
+            o.y = __funnelshift_r(a[t][1], a[t][2], sh);
+            o.z = __funnelshift_r(a[t][2], a[t][3], sh);
+            o.w = __funnelshift_r(a[t][3], a[t][4], sh);
+            *reinterpret_cast<uint4 *>(d + head + 16 * u) = o;
+          }
+        }
       }
       for (uint32_t k = head + 16 * n16 + j; k < S; k += D) d[k] = slot[k];
       if (j == 0) {
@@ -1132,7 +1216,7 @@ __global__ void __launch_bounds__(kEncLaneThreads, 7) k_encode_slots(EncParams p
   extern __shared__ __align__(16) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t K = 32 / p.g.D;
-  const uint32_t region = kEncStage + K * cfg.window;
+  const uint32_t region = enc_slot_region(p.g, cfg.window);
   uint8_t *wsm = smem + (uint64_t)warp * region;
   const uint64_t gwarp = (uint64_t)blockIdx.x * kEncLaneWarps + warp;
   uint8_t *wslots = cfg.slots + gwarp * K * (uint64_t)cfg.slot_stride;
@@ -1299,7 +1383,7 @@ static SlotPlan slot_plan(const Geom &g, const LaunchCfg &cfg) {
   pl.sc.window = enc_window_bytes(g);
   pl.sc.n_groups = (uint32_t)((g.n_chunks + K - 1) / K);
   pl.sc.slot_stride = (uint32_t)(((g.max_body + 15) & ~15ull) + 16);
-  pl.smem = (uint64_t)kEncLaneWarps * (kEncStage + (uint64_t)K * pl.sc.window);
+  pl.smem = (uint64_t)kEncLaneWarps * enc_slot_region(g, pl.sc.window);
   if (pl.smem > (uint64_t)cfg.max_smem_optin) return pl;
   const uint64_t want = (pl.sc.n_groups + kEncLaneWarps - 1) / kEncLaneWarps;
   pl.grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)cfg.sm_count *
@@ -1446,7 +1530,7 @@ int plan_batch_encode(const sprintz_batch_item *items, uint32_t n, const LaunchC
     e.cfg.slot_stride = (uint32_t)(((g.max_body + 15) & ~15ull) + 16);
     lb_words += e.cfg.n_groups;
     (*pre)[i + 1] = (*pre)[i] + e.cfg.n_groups;
-    region = std::max<uint32_t>(region, kEncStage + K * e.cfg.window);
+    region = std::max<uint32_t>(region, enc_slot_region(g, e.cfg.window));
     slot_region = std::max<uint64_t>(slot_region, (uint64_t)K * e.cfg.slot_stride);
   }
   memset(pl, 0, sizeof(*pl));
