@@ -424,15 +424,6 @@ __global__ void k_decode_header_tail(DecParams p) {
 constexpr int kLaneThreads = 128;
 constexpr int kLaneWarps = kLaneThreads / 32;
 
-// Bytes between the staged blocks of consecutive chunks of a warp.  When a row
-// is a whole number of 8-byte words, the stride is padded so that chunk k's
-// stage starts k * D * wb bytes (mod 128) into the shared-memory banks: the
-// row stores of the warp's chunks then fall into disjoint banks.
-__host__ __device__ inline uint32_t dec_stage_stride(uint32_t D, uint32_t wb) {
-  const uint32_t row = D * wb, blk = kBlockRows * row;
-  if (row % 8) return blk;
-  return blk + ((row - blk) & 127u);
-}
 
 // n (<= 16) bits at bit position `bit` of 4-byte-aligned memory `w`.
 __device__ __forceinline__ uint32_t bits_at(const uint32_t *w, uint64_t bit, uint32_t n) {
@@ -472,6 +463,7 @@ struct LaneRing {
 };
 
 constexpr uint32_t kRingWaitLimit = 1u << 22;
+constexpr bool kDecDirect = true;
 
 // Decode chunk group `warp_id` (K consecutive chunks) of one stream with one
 // warp whose shared region (stage, barriers, rings) starts at wsm.
@@ -498,7 +490,7 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
   const uint32_t wb = W / 8;
   const uint32_t hb = g.hb, G = g.G;
   const uint32_t blk_bytes = kBlockRows * D * wb;  // one chunk's block of output
-  const uint32_t stage_stride = dec_stage_stride(D, wb);
+  const uint32_t stage_stride = blk_stage_stride(D, wb);
   const uint32_t gmax = g.hdr_bytes + G * D * W;   // largest header group (bytes)
 
   // the chunk bodies end at tail_off
@@ -601,8 +593,11 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
     const uint64_t r2 = (warp_id * K + k2) * g.chunk_rows;  // rows from chunk c_begin
     dptr[t] = reinterpret_cast<uint64_t *>(p.dst + r2 * D * wb) + wq;
   }
-  uint8_t *my_stage = stage + kc * stage_stride + j * wb;
   const uint32_t row_stride = D * wb;
+  // kDecDirect: each lane stores its samples straight to global memory;
+  // otherwise a block's rows are staged and written as 8-byte words
+  uint8_t *my_stage = kDecDirect ? p.dst + (warp_id * K + kc) * (uint64_t)g.chunk_rows * row_stride + j * wb
+                                 : stage + kc * stage_stride + j * wb;
   auto put = [&](int i, uint32_t v) {
     if (W == 8)
       my_stage[i * row_stride] = (uint8_t)v;
@@ -731,15 +726,19 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
       }
       rem--;
     }
-    __syncwarp();
-    // block rows of every chunk of the warp: 8-byte words
-    const uint32_t boff = b * (blk_bytes / 8);
+    if (kDecDirect) {
+      my_stage += kBlockRows * row_stride;
+    } else {
+      __syncwarp();
+      // block rows of every chunk of the warp: 8-byte words
+      const uint32_t boff = b * (blk_bytes / 8);
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const bool e2 = __shfl_sync(0xFFFFFFFFu, emit, from_lane[t]);
-      if (has[t] && e2) dptr[t][boff] = reinterpret_cast<const uint64_t *>(stage)[src_word[t]];
+      for (int t = 0; t < 2; ++t) {
+        const bool e2 = __shfl_sync(0xFFFFFFFFu, emit, from_lane[t]);
+        if (has[t] && e2) dptr[t][boff] = reinterpret_cast<const uint64_t *>(stage)[src_word[t]];
+      }
+      __syncwarp();
     }
-    __syncwarp();
   }
   // every record consumed, the body used up, unused slots of the last group zero
   if (live) {
@@ -883,7 +882,7 @@ static LaneRing lane_ring_plan(const Geom &g, const LaunchCfg &cfg, uint32_t nse
   }
   r.nseg = nseg_want;
   auto layout = [&](LaneRing &x) {
-    x.bars_off = (K * dec_stage_stride(g.D, g.wb) + 15) & ~15u;
+    x.bars_off = (K * blk_stage_stride(g.D, g.wb) + 15) & ~15u;
     x.rings_off = x.bars_off + ((K * x.nseg * 8 + 15) & ~15u);
     x.per_warp = x.rings_off + K * x.nseg * x.seg;
   };

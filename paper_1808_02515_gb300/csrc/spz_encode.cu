@@ -872,17 +872,22 @@ struct BitSink {
   }
 };
 
-// Transposition tile of the row-major packer: per chunk, D columns of 8
-// entries (zigzagged error | width << 16), 48 bytes per column so that the
-// lanes' 16-byte stores of a quarter warp fall into distinct banks, and
-// chunks 32 bytes apart modulo 128 so that the row owners' loads do too.
+// Transposition tile of the row-major packer: per chunk, 8 rows of D entries
+// (zigzagged error | width << 16).  A row takes an odd number of 16-byte
+// units, so that the row owners' 16-byte loads of a quarter warp fall into
+// distinct banks; chunks start D * 4 bytes apart modulo 128, so that the
+// column owners' stores of one row do too.
+__host__ __device__ inline uint32_t enc_tile_row(uint32_t D) { return (((D * 4 + 15) / 16) | 1u) * 16; }
 __host__ __device__ inline uint32_t enc_tile_stride(uint32_t D) {
-  const uint32_t t = D * 48;
-  return t + ((((32u - t) & 127u) + 15u) & ~15u);
+  const uint32_t t = kBlockRows * enc_tile_row(D);
+  return t + ((((D * 4) - t) & 127u) + 15u & ~15u);
+}
+__host__ __device__ inline uint32_t enc_stage_bytes(uint32_t D, uint32_t wb) {
+  return ((32 / D) * blk_stage_stride(D, wb) + 15) & ~15u;
 }
 __host__ __device__ inline uint32_t enc_slot_region(const Geom &g, uint32_t window) {
   const uint32_t K = 32 / g.D;
-  return kEncStage + K * enc_tile_stride(g.D) + K * window;
+  return enc_stage_bytes(g.D, g.wb) + K * enc_tile_stride(g.D) + K * window;
 }
 
 struct EncSlotCfg {
@@ -908,14 +913,18 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
   const uint32_t G = g.G, hb = g.hb, H = g.hdr_bytes;
   (void)warp;
   uint8_t *stage = wsm;
-  const uint32_t tile_stride = enc_tile_stride(D);
-  uint32_t *tile = reinterpret_cast<uint32_t *>(wsm + kEncStage + kc * tile_stride);
-  uint32_t *ring = reinterpret_cast<uint32_t *>(wsm + kEncStage + K * tile_stride + (uint64_t)kc * cfg.window);
+  // rows are read once and bodies wait in their slots until the look-back:
+  // the slots are kept in L2 ahead of the streamed rows
+  const uint64_t pol_first = l2_evict_first_policy(), pol_last = l2_evict_last_policy();
+  const uint32_t tile_stride = enc_tile_stride(D), tile_rw = enc_tile_row(D) / 4;
+  const uint32_t st_stride = blk_stage_stride(D, wb), st_bytes = enc_stage_bytes(D, wb);
+  uint32_t *tile = reinterpret_cast<uint32_t *>(wsm + st_bytes + kc * tile_stride);
+  uint32_t *ring = reinterpret_cast<uint32_t *>(wsm + st_bytes + K * tile_stride + (uint64_t)kc * cfg.window);
   const uint32_t ring_wmask = cfg.window / 4 - 1, ring_bitmask = cfg.window * 8 - 1;
   const uint32_t seg_mask = D == 32 ? 0xFFFFFFFFu : ((1u << D) - 1u) << seg0;
   // the chunk's header codes fit one word and combine by butterfly shuffles
   constexpr uint32_t HB = W == 8 ? 3u : 4u;
-  constexpr bool kHdrShfl = DT != 0 && (DT & (DT - 1)) == 0 && DT * HB <= 32;
+  constexpr bool kHdrShfl = DT >= 2 && (DT & (DT - 1)) == 0 && DT * HB <= 32;
   uint8_t *slot = wslots + (uint64_t)kc * cfg.slot_stride;
 
   // cooperative stage loads: this lane's (up to two) 8-byte words of a block step
@@ -930,7 +939,10 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
     wq[t] = has[t] ? q % words_per : 0;
   }
   const uint32_t row_stride = D * wb;
-  const uint8_t *my_x = stage + kc * (kBlockRows * row_stride) + j * wb;
+  const uint8_t *my_x = stage + kc * st_stride + j * wb;
+  uint32_t st_word[2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) st_word[t] = k2[t] * (st_stride / 8) + wq[t];
   const uint32_t nb_max = (uint32_t)(min(g.chunk_rows, g.full_rows) / kBlockRows);
 
   {
@@ -952,7 +964,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
     uintptr_t pf = rows_lo;
     if (live && j == 0) {
       const uintptr_t e2 = min(rows_hi, pf + 8192);
-      prefetch_l2_range(pf, e2, rows_lo, rows_hi);
+      prefetch_l2_range_hint(pf, e2, rows_lo, rows_hi, pol_first);
       pf = e2;
     }
     if (live)
@@ -990,11 +1002,13 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
       if (j == 0) ror(pos * 8, len, 16);
       end_record(2);
     };
+    // completed bytes to the slot in whole 32-byte sectors (the last partial
+    // 16-byte unit at the end of the chunk)
     auto flush = [&](uint32_t limit, bool fin) {
-      const uint32_t u1 = fin ? (limit + 15) >> 4 : limit >> 4;
+      const uint32_t u1 = fin ? (limit + 15) >> 4 : (limit >> 5) << 1;
       for (uint32_t u = (flushed >> 4) + j; u < u1; u += D) {
         uint4 *r4 = reinterpret_cast<uint4 *>(&ring[(u * 4) & ring_wmask]);
-        *reinterpret_cast<uint4 *>(slot + 16ull * u) = *r4;
+        st_global_v4_hint(slot + 16ull * u, *r4, pol_last);
         *r4 = make_uint4(0, 0, 0, 0);
       }
       if (u1 * 16 > flushed) flushed = u1 * 16;
@@ -1002,15 +1016,15 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
 
     unsigned long long wcur[2], wnext[2];
 #pragma unroll
-    for (int t = 0; t < 2; ++t) wcur[t] = (has[t] && nbw[t] > 0) ? __ldg(srcw[t]) : 0ull;
+    for (int t = 0; t < 2; ++t) wcur[t] = (has[t] && nbw[t] > 0) ? ldg_u64_hint(srcw[t], pol_first) : 0ull;
     __syncwarp();
     for (uint32_t b = 0; b < nb_max; ++b) {
 #pragma unroll
       for (int t = 0; t < 2; ++t)
-        if (has[t]) reinterpret_cast<unsigned long long *>(stage)[lane + 32 * t] = wcur[t];
+        if (has[t]) reinterpret_cast<unsigned long long *>(stage)[st_word[t]] = wcur[t];
 #pragma unroll
       for (int t = 0; t < 2; ++t)
-        wnext[t] = (has[t] && b + 1 < nbw[t]) ? __ldg(srcw[t] + (uint64_t)(b + 1) * words_per) : 0ull;
+        wnext[t] = (has[t] && b + 1 < nbw[t]) ? ldg_u64_hint(srcw[t] + (uint64_t)(b + 1) * words_per, pol_first) : 0ull;
       __syncwarp();
       const bool here = live && b < nb;
       uint32_t z[kBlockRows];
@@ -1057,10 +1071,9 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
       }
       const uint32_t total = __shfl_sync(0xFFFFFFFFu, v, last);
       if (here && !g.col_major) {
-        uint4 *t4 = reinterpret_cast<uint4 *>(tile + j * 12);
         const uint32_t nh = n << 16;
-        t4[0] = make_uint4(z[0] | nh, z[1] | nh, z[2] | nh, z[3] | nh);
-        t4[1] = make_uint4(z[4] | nh, z[5] | nh, z[6] | nh, z[7] | nh);
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) tile[i * tile_rw + j] = z[i] | nh;
       }
       __syncwarp();
       if (here) {
@@ -1082,10 +1095,11 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
             uint32_t hv = code << (j * HB);
 #pragma unroll
             for (uint32_t o = 1; o < (DT ? (uint32_t)DT : 1u); o <<= 1) hv |= __shfl_xor_sync(seg_mask, hv, o);
-            if (j == 0) {
-              BitSink hs(ring, ring_wmask, hpos * 8 + gs * D * HB);
-              hs.put(hv, D * HB);
-              hs.finish();
+            // lane 0 ORs the low part into the first word, lane 1 the rest into the next
+            if (j < 2) {
+              const uint32_t hbit = hpos * 8 + gs * D * HB, sh = hbit & 31;
+              const uint32_t hw = j == 0 ? hv << sh : __funnelshift_l(hv, 0u, sh);
+              if (hw) atomicOr(&ring[((hbit >> 5) + j) & ring_wmask], hw);
             }
           } else {
             ror(hpos * 8 + (gs * D + j) * hb, code, hb);
@@ -1100,15 +1114,29 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
             }
           } else {
             // rows j, j + D, ...: each the concatenation of its D fields
-            // (size bits per row), gathered from the tile
+            // (size bits per row), read from the tile 4 entries at a time and
+            // appended two columns at a time
             (void)prefix;
-            const uint32_t *tc = tile;  // this chunk's tile
             for (uint32_t i = j; i < kBlockRows; i += D) {
+              const uint4 *row = reinterpret_cast<const uint4 *>(tile + i * tile_rw);
               BitSink bs(ring, ring_wmask, pos * 8 + i * size);
-#pragma unroll 8
-              for (uint32_t c = 0; c < D; ++c) {
-                const uint32_t e = tc[c * 12 + i];
-                bs.put(e & 0xFFFFu, e >> 16);
+#pragma unroll
+              for (uint32_t c4 = 0; c4 < (D + 3) / 4; ++c4) {
+                const uint4 q = row[c4];
+                const uint32_t e[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (uint32_t h = 0; h < 4; h += 2) {
+                  const uint32_t c = c4 * 4 + h;
+                  if (c < D) {
+                    const uint32_t n0 = e[h] >> 16, v0 = e[h] & 0xFFFFu;
+                    if (c + 1 < D) {
+                      const uint32_t n1 = e[h + 1] >> 16, v1 = e[h + 1] & 0xFFFFu;
+                      bs.put(v0 | (v1 << n0), n0 + n1);
+                    } else {
+                      bs.put(v0, n0);
+                    }
+                  }
+                }
               }
               bs.finish();
             }
@@ -1117,7 +1145,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
         }
         if (j == 0 && pf < rows_hi && rows_lo + (uint64_t)(b + 1) * kBlockRows * D * wb + 4096 > pf) {
           const uintptr_t e2 = min(rows_hi, pf + 4096);
-          prefetch_l2_range(pf, e2, rows_lo, rows_hi);
+          prefetch_l2_range_hint(pf, e2, rows_lo, rows_hi, pol_first);
           pf = e2;
         }
       }
@@ -1154,29 +1182,36 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
       const uint32_t head = min((uint32_t)((16 - ((uintptr_t)d & 15)) & 15), S);
       for (uint32_t k = j; k < head; k += D) d[k] = slot[k];
       const uint32_t n16 = (S - head) / 16;
+      // output unit u is slot bytes [head + 16u, +16): the tail of slot unit u
+      // and the head of unit u + 1 (both inside the slot's 16 spare bytes)
       const uint32_t sh = (head & 3) * 8;
-      const uint32_t *sw = reinterpret_cast<const uint32_t *>(slot + (head & ~3u));
-      // four units per lane in flight: all loads before the stores
-      for (uint32_t u0 = j; u0 < n16; u0 += 4 * D) {
-        uint32_t a[4][5];
+      const bool w1 = head & 4, w2 = head & 8;
+      const uint4 *s4 = reinterpret_cast<const uint4 *>(slot);
+      for (uint32_t u0 = j; u0 < n16; u0 += 2 * D) {
+        uint4 A[2], B[2];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < 2; ++t) {
           const uint32_t u = u0 + t * D;
           if (u < n16) {
-            const uint32_t *q = sw + 4 * u;
-#pragma unroll
-            for (int e = 0; e < 5; ++e) a[t][e] = q[e];
+            A[t] = ld_global_v4_hint(s4 + u, pol_first);
+            B[t] = ld_global_v4_hint(s4 + u + 1, pol_first);
           }
         }
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < 2; ++t) {
           const uint32_t u = u0 + t * D;
           if (u < n16) {
+            // words head/4 .. head/4 + 4 of the pair
+            const uint32_t p0 = w2 ? A[t].z : A[t].x, p1 = w2 ? A[t].w : A[t].y;
+            const uint32_t p2 = w2 ? B[t].x : A[t].z, p3 = w2 ? B[t].y : A[t].w;
+            const uint32_t p4 = w2 ? B[t].z : B[t].x, p5 = w2 ? B[t].w : B[t].y;
+            const uint32_t a0 = w1 ? p1 : p0, a1 = w1 ? p2 : p1, a2 = w1 ? p3 : p2;
+            const uint32_t a3 = w1 ? p4 : p3, a4 = w1 ? p5 : p4;
             uint4 o;
-            o.x = __funnelshift_r(a[t][0], a[t][1], sh);
-            o.y = __funnelshift_r(a[t][1], a[t][2], sh);
-            o.z = __funnelshift_r(a[t][2], a[t][3], sh);
-            o.w = __funnelshift_r(a[t][3], a[t][4], sh);
+            o.x = __funnelshift_r(a0, a1, sh);
+            o.y = __funnelshift_r(a1, a2, sh);
+            o.z = __funnelshift_r(a2, a3, sh);
+            o.w = __funnelshift_r(a3, a4, sh);
             *reinterpret_cast<uint4 *>(d + head + 16 * u) = o;
           }
         }
