@@ -161,6 +161,16 @@ __device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t *p) {
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
+// Relaxed gpu-scope accesses: for flags whose own word is the only data
+// exchanged (no L1 invalidation, no fence).
+__device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 
 // Bulk prefetch of [p, p + bytes) into L2 (TMA unit; p and bytes multiples of 16).
 __device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) {

@@ -618,10 +618,11 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
   for (uint32_t b = 0; b < nb_max; ++b) {
     const bool here = live && b < nb;
     const bool need = here && rem == 0;
-    const uint32_t need_mask = __ballot_sync(0xFFFFFFFFu, need);
-    if (need) {
-      bool bad = rec >= nrec;
-      if (gslot == G) {
+    // a new record: its header group first (ring upkeep), then every lane
+    // reads its width code and the full warp scans them (lanes without a
+    // new record contribute nothing that is used)
+    if (need && gslot == G) {
+      {
         hdr = gpos;
         gpos += g.hdr_bytes;
         gslot = 0;
@@ -648,19 +649,21 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
         wait_upto(min(s_hi, (uint64_t)((B0 + hdr + gmax - 1) >> ssh)));
         ring_ok = __all_sync(seg_mask, ring_ok);
       }
-      const bool hdr_in = gpos <= packed;
-      bad |= !hdr_in || !ring_ok;
-      const uint32_t code = hdr_in ? rbits(hdr * 8 + (gslot * D + j) * hb, (1u << hb) - 1u) : 0u;
-      const uint32_t nw = code == (uint32_t)W - 1 ? (uint32_t)W : code;
-      uint32_t v = nw;
+    }
+    const bool hdr_in = gpos <= packed;
+    const uint32_t code = need && hdr_in ? rbits(hdr * 8 + (gslot * D + j) * hb, (1u << hb) - 1u) : 0u;
+    const uint32_t nw = code == (uint32_t)W - 1 ? (uint32_t)W : code;
+    uint32_t v = nw;
 #pragma unroll
-      for (uint32_t o = 1; o < 32; o <<= 1) {
-        if (o < D) {
-          const uint32_t t = __shfl_up_sync(need_mask, v, o);
-          if (j >= o) v += t;
-        }
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+      if (o < D) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        if (j >= o) v += t;
       }
-      const uint32_t total = __shfl_sync(need_mask, v, last);
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, v, last);
+    if (need) {
+      bool bad = rec >= nrec || !hdr_in || !ring_ok;
       if (total == 0) {
         uint32_t cnt = 0;
         if (gpos + 2 <= packed) cnt = rbits(gpos * 8, 0xFFFFu);
@@ -760,7 +763,7 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
 }
 
 template <int W, int DT>
-__global__ void __launch_bounds__(kLaneThreads) k_decode_lanes(DecParams p, LaneRing rg) {
+__global__ void __launch_bounds__(kLaneThreads, 7) k_decode_lanes(DecParams p, LaneRing rg) {
   extern __shared__ __align__(16) uint8_t dsm[];
   const uint32_t warp = threadIdx.x >> 5;
   const DecParams pp = p;

@@ -507,21 +507,24 @@ __device__ __forceinline__ void ring_or(uint32_t *ring, uint32_t ring_words, uin
 // Decoupled look-back over chunk groups with the whole warp: each lane reads
 // one of the 32 nearest unread predecessors' words; the run of published
 // aggregates up to the nearest inclusive prefix is summed at once.  The group
-// publishes its aggregate first and its inclusive prefix last.  Waits are
-// bounded (SPRINTZ_ERR_TIMEOUT).  Returns the exclusive prefix in every lane.
+// publishes its aggregate first and its inclusive prefix last.  A published
+// word carries its own value, so relaxed accesses suffice (acquire loads
+// would invalidate the SM's L1 on every poll).  Polls back off exponentially
+// and are bounded (SPRINTZ_ERR_TIMEOUT).  Returns the exclusive prefix in
+// every lane.
 __device__ uint64_t lookback_warp(uint64_t *lb, uint32_t grp, uint64_t total, int *status) {
   const uint32_t lane = threadIdx.x & 31;
   if (grp == 0) {
-    if (lane == 0) st_release_u64(&lb[0], kFlagPrefix | total);
+    if (lane == 0) st_relaxed_u64(&lb[0], kFlagPrefix | total);
     return 0;
   }
-  if (lane == 0) st_release_u64(&lb[grp], kFlagAggregate | total);
+  if (lane == 0) st_relaxed_u64(&lb[grp], kFlagAggregate | total);
   uint64_t prefix = 0;
   int64_t k = (int64_t)grp - 1;  // nearest predecessor not yet summed
-  uint32_t spins = 0;
+  uint32_t spins = 0, ns = 64;
   while (true) {
     const int64_t idx = k - (int64_t)lane;
-    const uint64_t w = idx >= 0 ? ld_acquire_u64(&lb[idx]) : kFlagPrefix;  // before group 0: prefix 0
+    const uint64_t w = idx >= 0 ? ld_relaxed_u64(&lb[idx]) : kFlagPrefix;  // before group 0: prefix 0
     const uint64_t flag = w & ~kValueMask;
     const uint32_t pend = __ballot_sync(0xFFFFFFFFu, flag == 0);
     const uint32_t pref = __ballot_sync(0xFFFFFFFFu, flag == kFlagPrefix);
@@ -540,10 +543,13 @@ __device__ uint64_t lookback_warp(uint64_t *lb, uint32_t grp, uint64_t total, in
         if (lane == 0) set_status(status, SPRINTZ_ERR_TIMEOUT);
         break;
       }
-      __nanosleep(32);
+      __nanosleep(ns);
+      ns = ns < 1024 ? ns * 2 : 1024;
+    } else {
+      ns = 64;
     }
   }
-  if (lane == 0) st_release_u64(&lb[grp], kFlagPrefix | (prefix + total));
+  if (lane == 0) st_relaxed_u64(&lb[grp], kFlagPrefix | (prefix + total));
   return prefix;
 }
 
