@@ -177,64 +177,6 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) 
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// L2 eviction-priority policies (createpolicy) and accesses that carry one.
-#ifndef SPZ_L2_HINTS
-#define SPZ_L2_HINTS 0
-#endif
-__device__ __forceinline__ uint64_t l2_evict_last_policy() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t l2_evict_first_policy() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ void st_global_v4_hint(void *ptr, uint4 v, uint64_t pol) {
-#if SPZ_L2_HINTS
-  asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(ptr), "r"(v.x), "r"(v.y),
-               "r"(v.z), "r"(v.w), "l"(pol)
-               : "memory");
-#else
-  (void)pol;
-  *reinterpret_cast<uint4 *>(ptr) = v;
-#endif
-}
-__device__ __forceinline__ uint4 ld_global_v4_hint(const void *ptr, uint64_t pol) {
-#if SPZ_L2_HINTS
-  uint4 v;
-  asm volatile("ld.global.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "l"(ptr), "l"(pol)
-               : "memory");
-  return v;
-#else
-  (void)pol;
-  return *reinterpret_cast<const uint4 *>(ptr);
-#endif
-}
-// read-only data (not written during the kernel)
-__device__ __forceinline__ unsigned long long ldg_u64_hint(const void *ptr, uint64_t pol) {
-#if SPZ_L2_HINTS
-  unsigned long long v;
-  asm("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
-  return v;
-#else
-  (void)pol;
-  return __ldg(reinterpret_cast<const unsigned long long *>(ptr));
-#endif
-}
-__device__ __forceinline__ void prefetch_l2_bulk_hint(const void *p, uint32_t bytes, uint64_t pol) {
-#if SPZ_L2_HINTS
-  asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(p), "r"(bytes), "l"(pol)
-               : "memory");
-#else
-  (void)pol;
-  prefetch_l2_bulk(p, bytes);
-#endif
-}
-
 // Prefetch the 16-byte-aligned part of [lo, hi) that lies inside [buf_lo, buf_hi).
 __device__ __forceinline__ void prefetch_l2_range(uintptr_t lo, uintptr_t hi, uintptr_t buf_lo,
                                                   uintptr_t buf_hi) {
@@ -243,14 +185,6 @@ __device__ __forceinline__ void prefetch_l2_range(uintptr_t lo, uintptr_t hi, ui
   uintptr_t b = hi < buf_hi ? hi : buf_hi;
   b &= ~(uintptr_t)15;
   if (b > a) prefetch_l2_bulk((const void *)a, (uint32_t)(b - a));
-}
-__device__ __forceinline__ void prefetch_l2_range_hint(uintptr_t lo, uintptr_t hi, uintptr_t buf_lo,
-                                                       uintptr_t buf_hi, uint64_t pol) {
-  uintptr_t a = (lo > buf_lo ? lo : buf_lo);
-  a = (a + 15) & ~(uintptr_t)15;
-  uintptr_t b = hi < buf_hi ? hi : buf_hi;
-  b &= ~(uintptr_t)15;
-  if (b > a) prefetch_l2_bulk_hint((const void *)a, (uint32_t)(b - a), pol);
 }
 
 // mbarrier and TMA bulk-copy helpers (shared-memory addresses are 32-bit).

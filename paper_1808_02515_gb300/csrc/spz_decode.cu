@@ -460,6 +460,7 @@ struct LaneRing {
   uint32_t bars_off;       // per-warp offsets inside the warp's shared region
   uint32_t rings_off;
   uint32_t per_warp;       // bytes of shared memory per warp
+  uint32_t mirror;         // bytes after each ring repeating its first bytes
 };
 
 constexpr uint32_t kRingWaitLimit = 1u << 22;
@@ -484,9 +485,8 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
   uint8_t *stage = wsm;
   uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + rg.bars_off) + kc * rg.nseg;
   const uint32_t ring_bytes = rg.seg * rg.nseg;
-  uint8_t *ring = wsm + rg.rings_off + kc * ring_bytes;
+  uint8_t *ring = wsm + rg.rings_off + kc * (ring_bytes + rg.mirror);
   const uint32_t *ring32 = reinterpret_cast<const uint32_t *>(ring);
-  const uint32_t ring_wmask = ring_bytes / 4 - 1;
   const uint32_t wb = W / 8;
   const uint32_t hb = g.hb, G = g.G;
   const uint32_t blk_bytes = kBlockRows * D * wb;  // one chunk's block of output
@@ -538,12 +538,22 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
     uintptr_t a = max((uintptr_t)(s << ssh), max(B0 & ~(uintptr_t)15, buf_lo));
     uintptr_t b = min((uintptr_t)((s + 1) << ssh), min((B1 + 15) & ~(uintptr_t)15, buf_hi));
     const uint32_t bytes = b > a ? (uint32_t)(b - a) : 0u;
-    mbar_arrive_expect_tx(&bars[h], bytes);
+    // slot 0's first bytes also go to the mirror after the ring, so that a
+    // header group that wraps around reads on linearly
+    const uintptr_t s0 = (uintptr_t)(s << ssh);
+    const uintptr_t mb = h == 0 ? min(b, s0 + rg.mirror) : a;
+    const uint32_t mbytes = mb > a ? (uint32_t)(mb - a) : 0u;
+    mbar_arrive_expect_tx(&bars[h], bytes + mbytes);
     if (bytes) tma_load_1d(ring + (a & (ring_bytes - 1)), reinterpret_cast<const void *>(a), bytes, &bars[h]);
+    if (mbytes) tma_load_1d(ring + ring_bytes + (a - s0), reinterpret_cast<const void *>(a), mbytes, &bars[h]);
     // body bytes in the buffer's last partial 16-byte unit: plain loads
     const uintptr_t t0 = max(buf_hi, max((uintptr_t)(s << ssh), B0));
     const uintptr_t t1 = min(B1, (uintptr_t)((s + 1) << ssh));
-    for (uintptr_t q = t0; q < t1; ++q) ring[q & (ring_bytes - 1)] = *reinterpret_cast<const uint8_t *>(q);
+    for (uintptr_t q = t0; q < t1; ++q) {
+      const uint8_t v = *reinterpret_cast<const uint8_t *>(q);
+      ring[q & (ring_bytes - 1)] = v;
+      if (h == 0 && q - s0 < rg.mirror) ring[ring_bytes + (q - s0)] = v;
+    }
   };
   auto wait_upto = [&](uint64_t s) {
     while (seg_waited <= s && seg_waited < seg_issued) {
@@ -570,11 +580,13 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
     prefetch_l2_range(pf_end & ~(uintptr_t)15, e2, buf_lo, buf_hi);
     pf_end = e2;
   }
-  const uint32_t rb0 = (uint32_t)(B0 & (ring_bytes - 1)) * 8;  // body bit 0 in the ring
+  // ring bit of body bit `bit` inside the current header group: the group's
+  // ring position plus the offset into it (mod 2^32), never past the mirror
+  uint32_t gq = (uint32_t)(B0 & (ring_bytes - 1)) * 8;
   auto rbits = [&](uint32_t bit, uint32_t mask) {
-    const uint32_t q = rb0 + bit;
-    const uint32_t i0 = (q >> 5) & ring_wmask;
-    return __funnelshift_r(ring32[i0], ring32[(i0 + 1) & ring_wmask], q) & mask;
+    const uint32_t q = gq + bit;
+    const uint32_t i0 = q >> 5;
+    return __funnelshift_r(ring32[i0], ring32[i0 + 1], q) & mask;
   };
 
   // output mapping of this lane's (up to two) 8-byte words of each block step
@@ -626,6 +638,7 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
         hdr = gpos;
         gpos += g.hdr_bytes;
         gslot = 0;
+        gq = (uint32_t)((B0 + hdr) & (ring_bytes - 1)) * 8 - hdr * 8;
         // ring: release segments before the group, load ahead, wait for the group
         const uint64_t s_cur = (B0 + hdr) >> ssh;
         if (seg_base < s_cur) {
@@ -879,15 +892,16 @@ static LaneRing lane_ring_plan(const Geom &g, const LaunchCfg &cfg, uint32_t nse
   const uint32_t gmax = g.hdr_bytes + g.G * g.D * g.w;
   r.seg = 128;
   r.seg_shift = 7;
-  while (r.seg < gmax) {
+  r.mirror = (gmax + 8 + 15) & ~15u;  // a group plus the word read past its end
+  while (r.seg < r.mirror) {
     r.seg <<= 1;
     r.seg_shift++;
   }
   r.nseg = nseg_want;
   auto layout = [&](LaneRing &x) {
-    x.bars_off = (K * blk_stage_stride(g.D, g.wb) + 15) & ~15u;
+    x.bars_off = kDecDirect ? 0u : (K * blk_stage_stride(g.D, g.wb) + 15) & ~15u;
     x.rings_off = x.bars_off + ((K * x.nseg * 8 + 15) & ~15u);
-    x.per_warp = x.rings_off + K * x.nseg * x.seg;
+    x.per_warp = x.rings_off + K * (x.nseg * x.seg + x.mirror);
   };
   layout(r);
   while (r.nseg > 2 && (uint64_t)r.per_warp * kLaneWarps > 64 * 1024) {

@@ -919,9 +919,6 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
   const uint32_t G = g.G, hb = g.hb, H = g.hdr_bytes;
   (void)warp;
   uint8_t *stage = wsm;
-  // rows are read once and bodies wait in their slots until the look-back:
-  // the slots are kept in L2 ahead of the streamed rows
-  const uint64_t pol_first = l2_evict_first_policy(), pol_last = l2_evict_last_policy();
   const uint32_t tile_stride = enc_tile_stride(D), tile_rw = enc_tile_row(D) / 4;
   const uint32_t st_stride = blk_stage_stride(D, wb), st_bytes = enc_stage_bytes(D, wb);
   uint32_t *tile = reinterpret_cast<uint32_t *>(wsm + st_bytes + kc * tile_stride);
@@ -970,7 +967,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
     uintptr_t pf = rows_lo;
     if (live && j == 0) {
       const uintptr_t e2 = min(rows_hi, pf + 8192);
-      prefetch_l2_range_hint(pf, e2, rows_lo, rows_hi, pol_first);
+      prefetch_l2_range(pf, e2, rows_lo, rows_hi);
       pf = e2;
     }
     if (live)
@@ -1014,7 +1011,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
       const uint32_t u1 = fin ? (limit + 15) >> 4 : (limit >> 5) << 1;
       for (uint32_t u = (flushed >> 4) + j; u < u1; u += D) {
         uint4 *r4 = reinterpret_cast<uint4 *>(&ring[(u * 4) & ring_wmask]);
-        st_global_v4_hint(slot + 16ull * u, *r4, pol_last);
+        *reinterpret_cast<uint4 *>(slot + 16ull * u) = *r4;
         *r4 = make_uint4(0, 0, 0, 0);
       }
       if (u1 * 16 > flushed) flushed = u1 * 16;
@@ -1022,7 +1019,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
 
     unsigned long long wcur[2], wnext[2];
 #pragma unroll
-    for (int t = 0; t < 2; ++t) wcur[t] = (has[t] && nbw[t] > 0) ? ldg_u64_hint(srcw[t], pol_first) : 0ull;
+    for (int t = 0; t < 2; ++t) wcur[t] = (has[t] && nbw[t] > 0) ? __ldg(srcw[t]) : 0ull;
     __syncwarp();
     for (uint32_t b = 0; b < nb_max; ++b) {
 #pragma unroll
@@ -1030,7 +1027,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
         if (has[t]) reinterpret_cast<unsigned long long *>(stage)[st_word[t]] = wcur[t];
 #pragma unroll
       for (int t = 0; t < 2; ++t)
-        wnext[t] = (has[t] && b + 1 < nbw[t]) ? ldg_u64_hint(srcw[t] + (uint64_t)(b + 1) * words_per, pol_first) : 0ull;
+        wnext[t] = (has[t] && b + 1 < nbw[t]) ? __ldg(srcw[t] + (uint64_t)(b + 1) * words_per) : 0ull;
       __syncwarp();
       const bool here = live && b < nb;
       uint32_t z[kBlockRows];
@@ -1151,7 +1148,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
         }
         if (j == 0 && pf < rows_hi && rows_lo + (uint64_t)(b + 1) * kBlockRows * D * wb + 4096 > pf) {
           const uintptr_t e2 = min(rows_hi, pf + 4096);
-          prefetch_l2_range_hint(pf, e2, rows_lo, rows_hi, pol_first);
+          prefetch_l2_range(pf, e2, rows_lo, rows_hi);
           pf = e2;
         }
       }
@@ -1199,8 +1196,8 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
         for (int t = 0; t < 2; ++t) {
           const uint32_t u = u0 + t * D;
           if (u < n16) {
-            A[t] = ld_global_v4_hint(s4 + u, pol_first);
-            B[t] = ld_global_v4_hint(s4 + u + 1, pol_first);
+            A[t] = s4[u];
+            B[t] = s4[u + 1];
           }
         }
 #pragma unroll
