@@ -899,7 +899,7 @@ __host__ __device__ inline uint32_t enc_slot_region(const Geom &g, uint32_t wind
 struct EncSlotCfg {
   uint32_t window;       // ring bytes per chunk (power of two)
   uint32_t n_groups;
-  uint32_t slot_stride;  // bytes per chunk slot (multiple of 16, >= the largest body + 16)
+  uint32_t slot_stride;  // bytes per chunk slot (multiple of 32, >= the largest body + 32)
   uint8_t *slots;        // [warp][K] slots
 };
 
@@ -960,15 +960,6 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
       nbw[t] = __shfl_sync(0xFFFFFFFFu, nb, k2[t] * D);
       const uint64_t c2 = (uint64_t)grp * K + k2[t];
       srcw[t] = reinterpret_cast<const unsigned long long *>(p.src + c2 * g.chunk_rows * D * wb) + wq[t];
-    }
-    // L2 prefetch of the chunk's rows (leader), windows ahead of the reads
-    const uintptr_t rows_lo = (uintptr_t)(p.src + row0 * D * wb);
-    const uintptr_t rows_hi = rows_lo + (uint64_t)nb * kBlockRows * D * wb;
-    uintptr_t pf = rows_lo;
-    if (live && j == 0) {
-      const uintptr_t e2 = min(rows_hi, pf + 8192);
-      prefetch_l2_range(pf, e2, rows_lo, rows_hi);
-      pf = e2;
     }
     if (live)
       for (uint32_t t = j; t < cfg.window / 16; t += D)
@@ -1145,11 +1136,6 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
             }
           }
           end_record(size);
-        }
-        if (j == 0 && pf < rows_hi && rows_lo + (uint64_t)(b + 1) * kBlockRows * D * wb + 4096 > pf) {
-          const uintptr_t e2 = min(rows_hi, pf + 4096);
-          prefetch_l2_range(pf, e2, rows_lo, rows_hi);
-          pf = e2;
         }
       }
       __syncwarp();
@@ -1420,7 +1406,7 @@ static SlotPlan slot_plan(const Geom &g, const LaunchCfg &cfg) {
   const uint32_t K = 32 / g.D;
   pl.sc.window = enc_window_bytes(g);
   pl.sc.n_groups = (uint32_t)((g.n_chunks + K - 1) / K);
-  pl.sc.slot_stride = (uint32_t)(((g.max_body + 15) & ~15ull) + 16);
+  pl.sc.slot_stride = (uint32_t)(((g.max_body + 31) & ~31ull) + 32);
   pl.smem = (uint64_t)kEncLaneWarps * enc_slot_region(g, pl.sc.window);
   if (pl.smem > (uint64_t)cfg.max_smem_optin) return pl;
   const uint64_t want = (pl.sc.n_groups + kEncLaneWarps - 1) / kEncLaneWarps;
@@ -1565,7 +1551,7 @@ int plan_batch_encode(const sprintz_batch_item *items, uint32_t n, const LaunchC
     e.p.lookback = reinterpret_cast<uint64_t *>(ws + 16 + 8 * lb_words);
     e.cfg.window = enc_window_bytes(g);
     e.cfg.n_groups = (uint32_t)((g.n_chunks + K - 1) / K);
-    e.cfg.slot_stride = (uint32_t)(((g.max_body + 15) & ~15ull) + 16);
+    e.cfg.slot_stride = (uint32_t)(((g.max_body + 31) & ~31ull) + 32);
     lb_words += e.cfg.n_groups;
     (*pre)[i + 1] = (*pre)[i] + e.cfg.n_groups;
     region = std::max<uint32_t>(region, enc_slot_region(g, e.cfg.window));
