@@ -620,8 +620,8 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
   // walk state (body-relative bytes / bits)
   uint32_t gpos = 0, hdr = 0;
   uint32_t gslot = G, rec = 0, rem = 0;
-  bool run = true;
   uint32_t pbit = 0, stride = 0, mask = 0;
+  bool bad_any = false;
   // forecaster state
   uint32_t xp = 0;
   int32_t dp = 0, acc = 0;
@@ -663,8 +663,12 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
         ring_ok = __all_sync(seg_mask, ring_ok);
       }
     }
+    // every lane reads its width code (reads stay inside the current group:
+    // a group spans at most gmax bytes whatever the data) and the full warp
+    // scans them; lanes without a new record contribute nothing that is used
     const bool hdr_in = gpos <= packed;
-    const uint32_t code = need && hdr_in ? rbits(hdr * 8 + (gslot * D + j) * hb, (1u << hb) - 1u) : 0u;
+    const uint32_t raw = rbits(hdr * 8 + (gslot * D + j) * hb, (1u << hb) - 1u);
+    const uint32_t code = need && hdr_in ? raw : 0u;
     const uint32_t nw = code == (uint32_t)W - 1 ? (uint32_t)W : code;
     uint32_t v = nw;
 #pragma unroll
@@ -675,49 +679,34 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
       }
     }
     const uint32_t total = __shfl_sync(0xFFFFFFFFu, v, last);
-    if (need) {
-      bool bad = rec >= nrec || !hdr_in || !ring_ok;
-      if (total == 0) {
-        uint32_t cnt = 0;
-        if (gpos + 2 <= packed) cnt = rbits(gpos * 8, 0xFFFFu);
-        gpos += 2;
-        run = true;
-        rem = cnt;
-        bad |= cnt == 0 || b + cnt > nb;
-      } else {
-        const uint32_t prefix = v - nw;
-        const uint32_t size = g.col_major ? total : 8 * ((total + 7) / 8);
-        run = false;
-        rem = 1;
-        mask = (1u << nw) - 1u;
-        if (g.col_major) {
-          pbit = (gpos + prefix) * 8;
-          stride = nw;
-        } else {
-          pbit = gpos * 8 + prefix;
-          stride = size;  // 8 * R bits between rows
-        }
-        gpos += size;
-      }
-      bad |= gpos > packed;
-      gslot++;
-      rec++;
-      if (bad) {
-        live = false;
-        if (j == 0) set_status(p.status, ring_ok ? SPRINTZ_ERR_CORRUPT : SPRINTZ_ERR_TIMEOUT);
-      }
+    // the new record, in select form: a zero-block run (all widths zero, a
+    // u16 count) or a block whose column starts at bit pbit with rows stride
+    // bits apart; corruption is only recorded, the walk stays in bounds
+    {
+      const bool isrun = total == 0;
+      const uint32_t cnt = rbits(gpos * 8, 0xFFFFu);
+      const uint32_t prefix = v - nw;
+      const uint32_t size = g.col_major ? total : 8 * ((total + 7) / 8);
+      const uint32_t rsize = isrun ? 2u : size;
+      const uint32_t pb = g.col_major ? (gpos + prefix) * 8 : gpos * 8 + prefix;
+      const bool bad = rec >= nrec || !hdr_in || !ring_ok || gpos + rsize > packed ||
+                       (isrun && (cnt == 0 || b + cnt > nb));
+      bad_any |= need && bad;
+      rem = need ? (isrun ? cnt : 1u) : rem;
+      mask = need ? (isrun ? 0u : (1u << nw) - 1u) : mask;
+      pbit = need ? (isrun ? gpos * 8 : pb) : pbit;
+      stride = need ? (isrun ? 0u : (g.col_major ? nw : size)) : stride;
+      gpos += need ? rsize : 0u;
+      gslot += need ? 1u : 0u;
+      rec += need ? 1u : 0u;
     }
-    const bool emit = here && live;
+    const bool emit = here;
     if (emit) {
-      // zigzagged errors of this lane's column, 8 rows
+      // zigzagged errors of this lane's column, 8 rows (all zero in a run:
+      // mask 0)
       uint32_t z[kBlockRows];
-      if (run || mask == 0) {
 #pragma unroll
-        for (int i = 0; i < kBlockRows; ++i) z[i] = 0;
-      } else {
-#pragma unroll
-        for (int i = 0; i < kBlockRows; ++i) z[i] = rbits(pbit + i * stride, mask);
-      }
+      for (int i = 0; i < kBlockRows; ++i) z[i] = rbits(pbit + i * stride, mask);
       if (g.forecaster == kFcDelta) {
 #pragma unroll
         for (int i = 0; i < kBlockRows; ++i) {
@@ -756,8 +745,9 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
       __syncwarp();
     }
   }
+  if (bad_any && j == 0) set_status(p.status, ring_ok ? SPRINTZ_ERR_CORRUPT : SPRINTZ_ERR_TIMEOUT);
   // every record consumed, the body used up, unused slots of the last group zero
-  if (live) {
+  if (live && !bad_any) {
     bool bad = rec != nrec || gpos != packed;
     for (uint32_t s = gslot; s < G && !bad; ++s)
       bad |= rbits(hdr * 8 + (s * D + j) * hb, (1u << hb) - 1u) != 0;
