@@ -181,7 +181,12 @@ static uint32_t code_to_width(uint32_t c, uint32_t w) { return c == w - 1 ? w : 
 /* Forecasters (Sec. 3.2)                                                   */
 /* ------------------------------------------------------------------------ */
 
-enum { FC_DELTA = 0, FC_FIRE = 1 };
+/* 0 delta coding (Sec. 3.2.1); 1 FIRE as used in practice: alpha per block,
+ * one averaged update per block from every other sample (Sec. 3.2.2, last
+ * paragraph); 2 double-delta coding, the a = 2, b = -1 case of the
+ * autoregressive model of Sec. 3.2.2 (predict x_{i-1} + delta_{i-1}); 3 FIRE
+ * exactly as Algorithm 3 prints it: alpha and an update at every sample. */
+enum { FC_DELTA = 0, FC_FIRE = 1, FC_DDELTA = 2, FC_FIRE_SAMPLE = 3 };
 enum { FIRE_NORMAL = 0, FIRE_NO_LEARNING = 1, FIRE_PINNED_ALPHA = 2 };
 
 typedef struct {
@@ -190,7 +195,7 @@ typedef struct {
   int32_t test_mode;
   int64_t pinned_alpha;
   int64_t prev[MAX_D];   /* x_{i-1}: the previous sample, zeros initially (Sec. 3.2.1) */
-  int64_t deltas[MAX_D]; /* FIRE self.deltas: x_{i-1} - x_{i-2}, signed w-bit */
+  int64_t deltas[MAX_D]; /* FIRE / double delta: x_{i-1} - x_{i-2}, signed w-bit */
   int64_t acc[MAX_D];    /* FIRE self.accumulators: signed 2w-bit */
   int64_t alpha[MAX_D];  /* FIRE alpha of the current block */
   int64_t grad[MAX_D];   /* FIRE sum of the block's sampled gradients */
@@ -226,7 +231,11 @@ static void fc_block_begin(forecaster *f) {
  * delta is (alpha * delta_{i-1}) >> w, the product taken in 2w bits. */
 static int64_t fc_predict(const forecaster *f, uint32_t j) {
   if (f->kind == FC_DELTA) return f->prev[j];
-  int64_t product = wrap_signed(f->alpha[j] * f->deltas[j], 2 * f->w);
+  /* double delta: linear extrapolation from the last two samples */
+  if (f->kind == FC_DDELTA) return wrap_unsigned(f->prev[j] + f->deltas[j], f->w);
+  /* Algorithm 3 Predict at every sample: alphas = accumulators >> learnShift */
+  int64_t alpha = f->kind == FC_FIRE_SAMPLE ? shift_right_floor(f->acc[j], f->learn_shift) : f->alpha[j];
+  int64_t product = wrap_signed(alpha * f->deltas[j], 2 * f->w);
   int64_t predicted_delta = shift_right_floor(product, f->w);
   return wrap_unsigned(f->prev[j] + predicted_delta, f->w);
 }
@@ -238,6 +247,13 @@ static int64_t fc_predict(const forecaster *f, uint32_t j) {
 static void fc_train(forecaster *f, uint32_t j, uint32_t i, int64_t x_i, int64_t err) {
   if (f->kind == FC_FIRE) {
     if (i % 2 == 0) f->grad[j] += sign_of(err) * f->deltas[j];
+    f->deltas[j] = wrap_signed(x_i - f->prev[j], f->w);
+  } else if (f->kind == FC_FIRE_SAMPLE) {
+    /* Algorithm 3 Train: gradients = -sign(err) * deltas; accumulators -=
+     * gradients (2w-bit wrap); deltas = x_i - x_{i-1} */
+    f->acc[j] = wrap_signed(f->acc[j] + sign_of(err) * f->deltas[j], 2 * f->w);
+    f->deltas[j] = wrap_signed(x_i - f->prev[j], f->w);
+  } else if (f->kind == FC_DDELTA) {
     f->deltas[j] = wrap_signed(x_i - f->prev[j], f->w);
   }
   f->prev[j] = x_i;
@@ -606,7 +622,7 @@ typedef struct {
 static int check_opts(uint32_t D, uint32_t w, const spo_opts *o) {
   if (w != 8 && w != 16) return SPO_ERR_UNSUPPORTED_W;
   if (D < 1 || D > MAX_D) return SPO_ERR_INVALID_ARG;
-  if (o->forecaster != FC_DELTA && o->forecaster != FC_FIRE) return SPO_ERR_INVALID_ARG;
+  if (o->forecaster < FC_DELTA || o->forecaster > FC_FIRE_SAMPLE) return SPO_ERR_INVALID_ARG;
   if (o->huffman != 0 && o->huffman != 1) return SPO_ERR_INVALID_ARG;
   if (o->group_blocks < 1 || o->group_blocks > 8) return SPO_ERR_INVALID_ARG;
   if (o->learn_shift < 0 || o->learn_shift > (int32_t)(2 * w - 1)) return SPO_ERR_INVALID_ARG;

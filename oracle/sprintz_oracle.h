@@ -30,7 +30,9 @@ extern "C" {
 #define SPO_ERR_CORRUPT (-5)
 
 typedef struct {
-  int32_t forecaster;   /* 0 = delta coding (Sec. 3.2.1), 1 = FIRE (Sec. 3.2.2) */
+  int32_t forecaster;   /* 0 = delta coding (Sec. 3.2.1), 1 = FIRE in its block form
+                           (Sec. 3.2.2), 2 = double delta (Sec. 3.2.2, a = 2, b = -1),
+                           3 = FIRE per sample (Algorithm 3 as printed) */
   int32_t huffman;      /* 1 = Huffman-code the bit-packed bytes (Sec. 3.4) */
   int32_t group_blocks; /* G: records whose headers are stored together (Sec. 3.3) */
   int32_t learn_shift;  /* FIRE: alpha = accumulator >> learn_shift (eta = 2^-shift) */

@@ -291,7 +291,9 @@ def _size_model(err, D, w, G, chunk_rows):
 @pytest.mark.parametrize("D,w,fc,G,cr", [(1, 8, 0, 2, 1024), (3, 8, 1, 2, 1024),
                                          (4, 8, 0, 3, 64), (5, 8, 1, 2, 256),
                                          (2, 16, 0, 2, 1024), (8, 16, 1, 2, 1024),
-                                         (3, 16, 1, 8, 128), (16, 16, 0, 1, 0)])
+                                         (3, 16, 1, 8, 128), (16, 16, 0, 1, 0),
+                                         (3, 8, 2, 2, 1024), (8, 16, 2, 4, 512),
+                                         (4, 8, 3, 2, 256), (8, 16, 3, 2, 1024)])
 def test_sizes_match_independent_model(oracle_mod, D, w, fc, G, cr):
     from paper_1808_02515_gb300 import synth
     rows = 4096
