@@ -28,7 +28,7 @@ int make_geom(uint64_t rows, uint32_t D, uint32_t w, const sprintz_opts *o, Geom
   if (!o) return SPRINTZ_ERR_INVALID_ARG;
   if (w != 8 && w != 16) return SPRINTZ_ERR_UNSUPPORTED_W;
   if (D < 1 || D > kMaxD) return SPRINTZ_ERR_INVALID_ARG;
-  if (o->forecaster > 1 || o->huffman > 1) return SPRINTZ_ERR_INVALID_ARG;
+  if (o->forecaster > 3 || o->huffman > 1) return SPRINTZ_ERR_INVALID_ARG;
   if (o->group_blocks < 1 || o->group_blocks > 8) return SPRINTZ_ERR_INVALID_ARG;
   if (o->learn_shift > 2 * w - 1) return SPRINTZ_ERR_INVALID_ARG;
   if (o->chunk_rows % kBlockRows) return SPRINTZ_ERR_INVALID_ARG;

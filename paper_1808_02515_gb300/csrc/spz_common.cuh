@@ -32,8 +32,10 @@ constexpr uint32_t kEntryBytes = 16;
 constexpr uint32_t kHuffTableBytes = 128;
 constexpr uint32_t kMaxRun = 65535;    // run counts are 16-bit
 constexpr uint32_t kMaxD = 1024;
-constexpr int kFcDelta = 0;
-constexpr int kFcFire = 1;
+constexpr int kFcDelta = 0;       // x_{i-1} (Sec. 3.2.1)
+constexpr int kFcFire = 1;        // FIRE, block form: alpha per block, one averaged update (Sec. 3.2.2)
+constexpr int kFcDDelta = 2;      // double delta x_{i-1} + delta_{i-1} (Sec. 3.2.2, a = 2, b = -1)
+constexpr int kFcFireSample = 3;  // FIRE as Algorithm 3 prints it: alpha and an update every sample
 
 // Everything about a stream's layout that the host knows before launch.
 struct Geom {

@@ -329,6 +329,9 @@ __device__ void decode_chunk(const DecParams &p, uint8_t *mem, uint32_t c, uint6
   } else {
     // FIRE: per column, delta_i = wrap_w(floor(alpha * delta_{i-1} / 2^w) + e_i)
     // computed as one multiply-add and shift in 32 bits, x_i = x_{i-1} + delta_i.
+    // Double delta: delta_i = wrap_w(delta_{i-1} + e_i).  FIRE per sample:
+    // alpha from the accumulator and acc += sign(e_i) * delta_{i-1} at every
+    // row (Algorithm 3 as printed).
     for (uint32_t j = threadIdx.x; j < D; j += blockDim.x) {
       int32_t acc = 0, dp = 0;
       uint32_t xp = 0;
@@ -340,13 +343,22 @@ __device__ void decode_chunk(const DecParams &p, uint8_t *mem, uint32_t c, uint6
         for (int i = 0; i < kBlockRows; ++i) {
           const uint64_t r = (uint64_t)b * kBlockRows + i;
           const int32_t ev = sext<W>(tile_get<W>(X, D, r, j));
-          const int32_t d = (int32_t)(A * (uint32_t)dp + ((uint32_t)ev << (32 - W))) >> (32 - W);
-          if ((i & 1) == 0) gsum += sign_of(ev) * dp;
+          int32_t d;
+          if (g.forecaster == kFcDDelta) {
+            d = sext<W>((uint32_t)dp + (uint32_t)ev);
+          } else if (g.forecaster == kFcFireSample) {
+            const uint32_t As = (uint32_t)(acc >> g.learn_shift) << (32 - 2 * W);
+            d = (int32_t)(As * (uint32_t)dp + ((uint32_t)ev << (32 - W))) >> (32 - W);
+            acc = wrap_acc<W>((int32_t)((uint32_t)acc + (uint32_t)(sign_of(ev) * dp)));
+          } else {
+            d = (int32_t)(A * (uint32_t)dp + ((uint32_t)ev << (32 - W))) >> (32 - W);
+            if ((i & 1) == 0) gsum += sign_of(ev) * dp;
+          }
           xp += (uint32_t)d;
           tile_put<W>(X, D, r, j, xp);
           dp = d;
         }
-        acc = wrap_acc<W>((int32_t)((uint32_t)acc + (uint32_t)(gsum >> 2)));
+        if (g.forecaster == kFcFire) acc = wrap_acc<W>((int32_t)((uint32_t)acc + (uint32_t)(gsum >> 2)));
       }
     }
   }
@@ -712,6 +724,30 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
         for (int i = 0; i < kBlockRows; ++i) {
           xp += (z[i] >> 1) ^ (0u - (z[i] & 1u));
           put(i, xp);
+        }
+      } else if (g.forecaster == kFcDDelta) {
+        // double delta: delta_i = wrap_w(delta_{i-1} + e_i)
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) {
+          const uint32_t ev = (z[i] >> 1) ^ (0u - (z[i] & 1u));
+          const int32_t d = sext<W>((uint32_t)dp + ev);
+          xp += (uint32_t)d;
+          put(i, xp);
+          dp = d;
+        }
+      } else if (g.forecaster == kFcFireSample) {
+        // Algorithm 3 at every sample: alpha from the accumulator, the
+        // delta as in the block form, then acc += sign(e_i) * delta_{i-1}
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) {
+          const uint32_t A = (uint32_t)(acc >> g.learn_shift) << (32 - 2 * W);
+          const uint32_t ev = (z[i] >> 1) ^ (0u - (z[i] & 1u));
+          const int32_t d = (int32_t)(A * (uint32_t)dp + (ev << (32 - W))) >> (32 - W);
+          const int32_t sg = z[i] == 0 ? 0 : ((z[i] & 1u) ? -dp : dp);
+          acc = wrap_acc<W>((int32_t)((uint32_t)acc + (uint32_t)sg));
+          xp += (uint32_t)d;
+          put(i, xp);
+          dp = d;
         }
       } else {
         // delta_i = wrap_w(floor(alpha * delta_{i-1} / 2^w) + e_i): one

@@ -50,7 +50,8 @@ __host__ __device__ inline EncLayout enc_layout(const Geom &g, bool stage_rows) 
   };
   L.x = stage_rows ? take(nb * kBlockRows * g.D * g.wb) : 0;
   L.width = take(nb * g.D);
-  L.alpha = take(g.forecaster == kFcFire ? nb * g.D * 4 : 0);
+  L.alpha = take(g.forecaster == kFcFire ? nb * g.D * 4
+                 : g.forecaster == kFcFireSample ? nb * kBlockRows * g.D * 4 : 0);
   L.bsum = take(nb * 4);
   L.rec_first = take(nb * 4);
   L.rec_run = take(nb * 4);
@@ -146,7 +147,16 @@ __device__ __forceinline__ int32_t error_at(const uint8_t *X, uint32_t D, uint64
   if (forecaster == kFcDelta) return sext<W>(x - xp);
   uint32_t xpp = r >= 2 ? sample<W>(X, D, r - 2, j) : 0u;
   int32_t dp = r >= 1 ? sext<W>(xp - xpp) : 0;
+  if (forecaster == kFcDDelta) return sext<W>(x - xp - (uint32_t)dp);
   return sext<W>(x - xp - fire_pred_delta<W>(alpha, dp));
+}
+
+// The alpha that error_at needs for row i of block b, column j.
+__device__ __forceinline__ int32_t alpha_at(const Geom &g, const int32_t *alpha, uint32_t D, uint32_t b,
+                                            uint32_t i, uint32_t j) {
+  if (g.forecaster == kFcFire) return alpha[(uint64_t)b * D + j];
+  if (g.forecaster == kFcFireSample) return alpha[((uint64_t)b * kBlockRows + i) * D + j];
+  return 0;
 }
 
 __device__ void write_stream_header(uint8_t *h, const Geom &g, uint64_t tail_off, uint64_t total) {
@@ -212,6 +222,24 @@ __device__ void encode_chunk(const EncParams &p, uint8_t *mem, uint32_t c) {
   }
   __syncthreads();
 
+  // 2. FIRE per sample: alpha of every row, one thread per column
+  // (Algorithm 3: alpha from the accumulator, then one gradient step).
+  if (g.forecaster == kFcFireSample) {
+    for (uint32_t j = threadIdx.x; j < D; j += blockDim.x) {
+      int32_t acc = 0, dp = 0;
+      uint32_t xp = 0;
+      for (uint64_t r = 0; r < (uint64_t)nb * kBlockRows; ++r) {
+        const int32_t a = acc >> g.learn_shift;
+        alpha[r * D + j] = a;
+        const uint32_t x = sample<W>(X, D, r, j);
+        const int32_t e = sext<W>(x - xp - fire_pred_delta<W>(a, dp));
+        acc = wrap_acc<W>((int32_t)((uint32_t)acc + (uint32_t)(sign_of(e) * dp)));
+        dp = sext<W>(x - xp);
+        xp = x;
+      }
+    }
+    __syncthreads();
+  }
   // 2. FIRE: alpha of every block, one thread per column.
   if (g.forecaster == kFcFire) {
     for (uint32_t j = threadIdx.x; j < D; j += blockDim.x) {
@@ -240,11 +268,11 @@ __device__ void encode_chunk(const EncParams &p, uint8_t *mem, uint32_t c) {
   // 3. widths of every (block, column)
   for (uint64_t q = threadIdx.x; q < (uint64_t)nb * D; q += blockDim.x) {
     uint32_t b = (uint32_t)(q / D), j = (uint32_t)(q % D);
-    int32_t a = g.forecaster == kFcFire ? alpha[q] : 0;
     uint32_t o = 0;
 #pragma unroll
     for (int i = 0; i < kBlockRows; ++i)
-      o |= zigzag<W>(error_at<W>(X, D, (uint64_t)b * kBlockRows + i, j, g.forecaster, a));
+      o |= zigzag<W>(error_at<W>(X, D, (uint64_t)b * kBlockRows + i, j, g.forecaster,
+                                 alpha_at(g, alpha, D, b, i, j)));
     uint32_t n = bit_len(o);
     width[q] = (uint8_t)(n == W - 1 ? W : n);
   }
@@ -326,10 +354,10 @@ __device__ void encode_chunk(const EncParams &p, uint8_t *mem, uint32_t c) {
       for (uint32_t j = 0; j < k; ++j) off += wr[j];
       uint32_t n = wr[k];
       if (!n) continue;
-      int32_t a = g.forecaster == kFcFire ? alpha[(uint64_t)b * D + k] : 0;
       uint64_t lo = 0, hi = 0;  // 128-bit little-endian bit buffer
       for (int i = 0; i < kBlockRows; ++i) {
-        uint64_t z = zigzag<W>(error_at<W>(X, D, (uint64_t)b * kBlockRows + i, k, g.forecaster, a));
+        uint64_t z = zigzag<W>(error_at<W>(X, D, (uint64_t)b * kBlockRows + i, k, g.forecaster,
+                                           alpha_at(g, alpha, D, b, i, k)));
         uint32_t bit = i * n;
         if (bit < 64) {
           lo |= z << bit;
@@ -350,8 +378,7 @@ __device__ void encode_chunk(const EncParams &p, uint8_t *mem, uint32_t c) {
       for (uint32_t j = 0; j < D; ++j) {
         uint32_t n = wr[j];
         if (!n) continue;
-        int32_t a = g.forecaster == kFcFire ? alpha[(uint64_t)b * D + j] : 0;
-        uint64_t z = zigzag<W>(error_at<W>(X, D, row, j, g.forecaster, a));
+        uint64_t z = zigzag<W>(error_at<W>(X, D, row, j, g.forecaster, alpha_at(g, alpha, D, b, k, j)));
         acc |= z << nacc;
         nacc += n;
         while (nacc >= 8) {
@@ -691,6 +718,24 @@ __device__ uint64_t encode_pass(const EncParams &p, const Geom &g, uint8_t *stag
           z[i] = zigzag<W>(sext<W>(x[i] - st.xp));
           st.xp = x[i];
           orz |= z[i];
+        }
+      } else if (g.forecaster == kFcDDelta) {
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) {
+          z[i] = zigzag<W>(sext<W>(x[i] - st.xp - (uint32_t)st.dp));
+          orz |= z[i];
+          st.dp = sext<W>(x[i] - st.xp);
+          st.xp = x[i];
+        }
+      } else if (g.forecaster == kFcFireSample) {
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) {
+          const int32_t e = sext<W>(x[i] - st.xp - fire_pred_delta<W>(st.acc >> g.learn_shift, st.dp));
+          st.acc = wrap_acc<W>((int32_t)((uint32_t)st.acc + (uint32_t)(sign_of(e) * st.dp)));
+          z[i] = zigzag<W>(e);
+          orz |= z[i];
+          st.dp = sext<W>(x[i] - st.xp);
+          st.xp = x[i];
         }
       } else {
         const int32_t a = st.acc >> g.learn_shift;
@@ -1036,6 +1081,27 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
             z[i] = zigzag<W>(sext<W>(x[i] - xp));
             xp = x[i];
             orz |= z[i];
+          }
+        } else if (g.forecaster == kFcDDelta) {
+          // double delta: predict x_{i-1} + delta_{i-1}
+#pragma unroll
+          for (int i = 0; i < kBlockRows; ++i) {
+            z[i] = zigzag<W>(sext<W>(x[i] - xp - (uint32_t)dp));
+            orz |= z[i];
+            dp = sext<W>(x[i] - xp);
+            xp = x[i];
+          }
+        } else if (g.forecaster == kFcFireSample) {
+          // Algorithm 3 at every sample: alpha = acc >> shift, then
+          // acc += sign(e) * delta_{i-1}
+#pragma unroll
+          for (int i = 0; i < kBlockRows; ++i) {
+            const int32_t e = sext<W>(x[i] - xp - fire_pred_delta<W>(acc >> g.learn_shift, dp));
+            acc = wrap_acc<W>((int32_t)((uint32_t)acc + (uint32_t)(sign_of(e) * dp)));
+            z[i] = zigzag<W>(e);
+            orz |= z[i];
+            dp = sext<W>(x[i] - xp);
+            xp = x[i];
           }
         } else {
           const int32_t a = acc >> g.learn_shift;

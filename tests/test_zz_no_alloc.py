@@ -36,6 +36,8 @@ def _workloads():
         (synth.random_walk_u8(200_000 + 5, 3, scale=1.5, const_frac=0.3, seed=22),
          dict(forecaster=0, group_blocks=3)),
         (synth.uniform(5000, 40, 8, seed=23), dict(forecaster=1, chunk_rows=256)),
+        (synth.sensor_u16(50_000 + 2, 4, seed=24), dict(forecaster=3)),
+        (synth.random_walk_u8(60_000 + 1, 5, scale=2.0, const_frac=0.2, seed=25), dict(forecaster=2)),
     ]
 
 
