@@ -5,11 +5,11 @@
  * Internet of Things", IMWUT 2018) compresses a multivariate integer time
  * series — T samples of D columns, every element a w-bit integer, stored
  * row-major (Sec. 2.1, Definitions 2.1-2.3) — in blocks of B = 8 rows:
- * forecast each sample (delta coding, Sec. 3.2.1, or the FIRE online
- * forecaster, Sec. 3.2.2 / Algorithm 3), zigzag the errors, store each
- * column's bit width in a header and bit-pack the errors (Sec. 3.3), replace
- * runs of all-zero blocks by their count (Sec. 3.1, Algorithm 1), and
- * optionally Huffman-code the packed bytes (Sec. 3.4).  Decoding inverts each
+ * forecast each sample (delta coding, Sec. 4.2.1, or the FIRE online
+ * forecaster, Sec. 4.2.2 / Algorithm 3), zigzag the errors, store each
+ * column's bit width in a header and bit-pack the errors (Sec. 4.3), replace
+ * runs of all-zero blocks by their count (Sec. 4.1, Algorithm 1), and
+ * optionally Huffman-code the packed bytes (Sec. 4.4).  Decoding inverts each
  * step (Algorithm 2).
  *
  * Conventions for every entry point:
@@ -50,13 +50,13 @@ extern "C" {
 #define SPRINTZ_ERR_CUDA (-7)          /* a CUDA runtime call failed */
 #define SPRINTZ_ERR_UNSUPPORTED (-8)   /* a valid option this build does not run */
 
-/* Codec options (the paper's knobs, Sec. 3.1 and 4.2: SprintzDelta,
+/* Codec options (the paper's knobs, Sec. 4.1 and 5.2: SprintzDelta,
  * SprintzFIRE, SprintzFIRE+Huf). */
 typedef struct {
-  uint8_t forecaster;   /* 0 = delta coding (Sec. 3.2.1), 1 = FIRE (Sec. 3.2.2) */
-  uint8_t huffman;      /* 1 = Huffman-code the bit-packed bytes (Sec. 3.4) */
-  uint8_t group_blocks; /* G, 1..8: record headers stored together (Sec. 3.3); the paper uses 2 */
-  uint8_t learn_shift;  /* FIRE: alpha = accumulator >> learn_shift; 1 gives eta = 1/2 (Sec. 3.2.2) */
+  uint8_t forecaster;   /* 0 = delta coding (Sec. 4.2.1), 1 = FIRE (Sec. 4.2.2) */
+  uint8_t huffman;      /* 1 = Huffman-code the bit-packed bytes (Sec. 4.4) */
+  uint8_t group_blocks; /* G, 1..8: record headers stored together (Sec. 4.3); the paper uses 2 */
+  uint8_t learn_shift;  /* FIRE: alpha = accumulator >> learn_shift; 1 gives eta = 1/2 (Sec. 4.2.2) */
   uint32_t chunk_rows;  /* rows per chunk, multiple of 8; the forecaster restarts at each chunk;
                            0 = one chunk for the whole series (the paper's single stream) */
   uint32_t huff_chunks; /* consecutive chunks sharing one Huffman table (huffman = 1), >= 1 */

@@ -17,7 +17,7 @@
  *   then             Huffman tables (huffman streams only), 128 bytes per segment:
  *                      256 code lengths, 4 bits each, symbol 2k in the low nibble
  *   data_off         chunk bodies, back to back
- *   tail_off         the rows % 8 trailing rows, stored raw (Sec. 4.3: the
+ *   tail_off         the rows % 8 trailing rows, stored raw (Sec. 5.4: the
  *                    paper memcpy's trailing bytes)
  *   total_bytes      end of stream
  * Parity of this container is unpinned by the paper: it is our format.
@@ -28,7 +28,7 @@
 #include <string.h>
 
 #define MAX_D 1024u
-#define BLOCK_ROWS 8u          /* B = 8 (Sec. 3.1) */
+#define BLOCK_ROWS 8u          /* B = 8 (Sec. 4.1) */
 #define HUFF_MAX_LEN 11u       /* our length limit for the byte Huffman code */
 #define MAX_RUN 65535u         /* a zero run's count is stored in 16 bits */
 #define HDR_BYTES 64u
@@ -138,10 +138,10 @@ static uint64_t br_bits(bit_reader *b, uint32_t n) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Zigzag and bit widths (Sec. 3.3)                                         */
+/* Zigzag and bit widths (Sec. 4.3)                                         */
 /* ------------------------------------------------------------------------ */
 
-/* Twice |e| for e >= 0, twice |e| minus one for e < 0 (Sec. 3.3). */
+/* Twice |e| for e >= 0, twice |e| minus one for e < 0 (Sec. 4.3). */
 uint32_t spo_zigzag(int32_t e, uint32_t w) {
   int64_t v = wrap_signed(e, w);
   int64_t z = v >= 0 ? 2 * v : -2 * v - 1;
@@ -162,7 +162,7 @@ uint32_t spo_bit_length(uint32_t v) {
   return n;
 }
 
-/* Width = bits of the OR of the column's zigzagged errors (Sec. 3.3: w minus
+/* Width = bits of the OR of the column's zigzagged errors (Sec. 4.3: w minus
  * the fewest leading zeros), and a width of w-1 is stored as w because the
  * log2(w)-bit header holds only w of the w+1 possible widths. */
 uint32_t spo_column_width(const uint32_t z[8], uint32_t w) {
@@ -178,13 +178,13 @@ static uint32_t width_to_code(uint32_t n, uint32_t w) { return n == w ? w - 1 : 
 static uint32_t code_to_width(uint32_t c, uint32_t w) { return c == w - 1 ? w : c; }
 
 /* ------------------------------------------------------------------------ */
-/* Forecasters (Sec. 3.2)                                                   */
+/* Forecasters (Sec. 4.2)                                                   */
 /* ------------------------------------------------------------------------ */
 
-/* 0 delta coding (Sec. 3.2.1); 1 FIRE as used in practice: alpha per block,
- * one averaged update per block from every other sample (Sec. 3.2.2, last
+/* 0 delta coding (Sec. 4.2.1); 1 FIRE as used in practice: alpha per block,
+ * one averaged update per block from every other sample (Sec. 4.2.2, last
  * paragraph); 2 double-delta coding, the a = 2, b = -1 case of the
- * autoregressive model of Sec. 3.2.2 (predict x_{i-1} + delta_{i-1}); 3 FIRE
+ * autoregressive model of Sec. 4.2.2 (predict x_{i-1} + delta_{i-1}); 3 FIRE
  * exactly as Algorithm 3 prints it: alpha and an update at every sample. */
 enum { FC_DELTA = 0, FC_FIRE = 1, FC_DDELTA = 2, FC_FIRE_SAMPLE = 3 };
 enum { FIRE_NORMAL = 0, FIRE_NO_LEARNING = 1, FIRE_PINNED_ALPHA = 2 };
@@ -194,7 +194,7 @@ typedef struct {
   uint32_t D, w, learn_shift;
   int32_t test_mode;
   int64_t pinned_alpha;
-  int64_t prev[MAX_D];   /* x_{i-1}: the previous sample, zeros initially (Sec. 3.2.1) */
+  int64_t prev[MAX_D];   /* x_{i-1}: the previous sample, zeros initially (Sec. 4.2.1) */
   int64_t deltas[MAX_D]; /* FIRE / double delta: x_{i-1} - x_{i-2}, signed w-bit */
   int64_t acc[MAX_D];    /* FIRE self.accumulators: signed 2w-bit */
   int64_t alpha[MAX_D];  /* FIRE alpha of the current block */
@@ -213,7 +213,7 @@ static void fc_init(forecaster *f, int32_t kind, uint32_t D, uint32_t w,
   f->pinned_alpha = pinned_alpha;
 }
 
-/* FIRE in practice (last paragraph of Sec. 3.2.2): alpha is computed once at
+/* FIRE in practice (last paragraph of Sec. 4.2.2): alpha is computed once at
  * the start of each block, alpha = accumulator >> learnShift. */
 static void fc_block_begin(forecaster *f) {
   if (f->kind != FC_FIRE) return;
@@ -300,7 +300,7 @@ static void fc_decode_block(forecaster *f, const int64_t *err /* 8 x D */,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Records, header groups and payloads (Algorithm 1 / Sec. 3.3)             */
+/* Records, header groups and payloads (Algorithm 1 / Sec. 4.3)             */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
@@ -390,7 +390,7 @@ static int encode_chunk(const uint8_t *src, uint64_t n_blocks, uint32_t D, uint3
   fc_init(f, o->forecaster, D, w, (uint32_t)o->learn_shift, FIRE_NORMAL, 0);
   uint32_t run = 0;
   for (uint64_t b = 0; b < n_blocks; ++b) {
-    /* Algorithm 1 lines 1-7: forecast the block and take the errors. */
+    /* Algorithm 1, first step: forecast the block and take the errors. */
     for (uint32_t i = 0; i < BLOCK_ROWS; ++i)
       for (uint32_t j = 0; j < D; ++j)
         x[i * D + j] = get_sample(src, b * BLOCK_ROWS + i, j, D, w);
@@ -440,7 +440,7 @@ static int encode_chunk(const uint8_t *src, uint64_t n_blocks, uint32_t D, uint3
 }
 
 /* ------------------------------------------------------------------------ */
-/* Length-limited Huffman codes (Sec. 3.4; our own coder in place of Huff0) */
+/* Length-limited Huffman codes (Sec. 4.4; our own coder in place of Huff0) */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
@@ -544,7 +544,7 @@ int spo_huff_code_lengths(const uint64_t freq[256], uint32_t max_len, uint8_t le
   return SPO_OK;
 }
 
-/* Canonical codes as in RFC 1951 Sec. 3.2.2: shorter codes first, and within
+/* Canonical codes as in RFC 1951 Sec. 4.2.2: shorter codes first, and within
  * one length in symbol order. */
 int spo_huff_canonical(const uint8_t len[256], uint32_t code_out[256]) {
   uint32_t bl_count[32] = {0};

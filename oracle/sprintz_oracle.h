@@ -30,11 +30,11 @@ extern "C" {
 #define SPO_ERR_CORRUPT (-5)
 
 typedef struct {
-  int32_t forecaster;   /* 0 = delta coding (Sec. 3.2.1), 1 = FIRE in its block form
-                           (Sec. 3.2.2), 2 = double delta (Sec. 3.2.2, a = 2, b = -1),
+  int32_t forecaster;   /* 0 = delta coding (Sec. 4.2.1), 1 = FIRE in its block form
+                           (Sec. 4.2.2), 2 = double delta (Sec. 4.2.2, a = 2, b = -1),
                            3 = FIRE per sample (Algorithm 3 as printed) */
-  int32_t huffman;      /* 1 = Huffman-code the bit-packed bytes (Sec. 3.4) */
-  int32_t group_blocks; /* G: records whose headers are stored together (Sec. 3.3) */
+  int32_t huffman;      /* 1 = Huffman-code the bit-packed bytes (Sec. 4.4) */
+  int32_t group_blocks; /* G: records whose headers are stored together (Sec. 4.3) */
   int32_t learn_shift;  /* FIRE: alpha = accumulator >> learn_shift (eta = 2^-shift) */
   uint32_t chunk_rows;  /* rows between forecaster resets; multiple of 8; 0 = one chunk */
   uint32_t huff_chunks; /* chunks that share one Huffman table */
@@ -61,7 +61,7 @@ int spo_decompress(const uint8_t *src, uint64_t n, void *dst, uint64_t dst_cap);
 
 /* ---- step-level entry points (used by the pin tests) ------------------- */
 
-/* Zigzag code of a signed w-bit error and its inverse (Sec. 3.3). */
+/* Zigzag code of a signed w-bit error and its inverse (Sec. 4.3). */
 uint32_t spo_zigzag(int32_t e, uint32_t w);
 int32_t spo_unzigzag(uint32_t z, uint32_t w);
 
@@ -69,7 +69,7 @@ int32_t spo_unzigzag(uint32_t z, uint32_t w);
 uint32_t spo_bit_length(uint32_t v);
 
 /* Stored width of one column of one block from its eight zigzagged errors,
- * with the w-1 -> w promotion of Sec. 3.3. */
+ * with the w-1 -> w promotion of Sec. 4.3. */
 uint32_t spo_column_width(const uint32_t z[8], uint32_t w);
 
 /* Forecaster-only pass: the prediction errors (signed, w-bit) of `rows` rows

@@ -26,15 +26,15 @@
 
 namespace spz {
 
-constexpr int kBlockRows = 8;          // B (Sec. 3.1)
+constexpr int kBlockRows = 8;          // B (Sec. 4.1)
 constexpr uint32_t kHdrBytes = 64;
 constexpr uint32_t kEntryBytes = 16;
 constexpr uint32_t kHuffTableBytes = 128;
 constexpr uint32_t kMaxRun = 65535;    // run counts are 16-bit
 constexpr uint32_t kMaxD = 1024;
-constexpr int kFcDelta = 0;       // x_{i-1} (Sec. 3.2.1)
-constexpr int kFcFire = 1;        // FIRE, block form: alpha per block, one averaged update (Sec. 3.2.2)
-constexpr int kFcDDelta = 2;      // double delta x_{i-1} + delta_{i-1} (Sec. 3.2.2, a = 2, b = -1)
+constexpr int kFcDelta = 0;       // x_{i-1} (Sec. 4.2.1)
+constexpr int kFcFire = 1;        // FIRE, block form: alpha per block, one averaged update (Sec. 4.2.2)
+constexpr int kFcDDelta = 2;      // double delta x_{i-1} + delta_{i-1} (Sec. 4.2.2, a = 2, b = -1)
 constexpr int kFcFireSample = 3;  // FIRE as Algorithm 3 prints it: alpha and an update every sample
 
 // Everything about a stream's layout that the host knows before launch.
@@ -105,7 +105,7 @@ __device__ __forceinline__ int32_t sext(uint32_t v) {
 
 __device__ __forceinline__ int32_t sign_of(int32_t v) { return (v > 0) - (v < 0); }
 
-// Zigzag of a signed W-bit value (Sec. 3.3) as an unsigned W-bit value.
+// Zigzag of a signed W-bit value (Sec. 4.3) as an unsigned W-bit value.
 template <int W>
 __device__ __forceinline__ uint32_t zigzag(int32_t e) {
   return ((uint32_t)e << 1 ^ (uint32_t)(e >> 31)) & ((1u << W) - 1u);

@@ -14,7 +14,7 @@
 //   4. the forecast is inverted in place: delta as a per-column wrap-around
 //      prefix sum split across threads; FIRE as one serial recurrence per
 //      column (Algorithm 2 with Algorithm 3's predict/train, alpha fixed per
-//      block, one averaged update per block — Sec. 3.2.2);
+//      block, one averaged update per block — Sec. 4.2.2);
 //   5. the tile is stored with 128-bit stores.
 // CTA 0 also checks the stream header against the host's view of it and
 // copies the raw trailing rows.  Chunks too large for shared memory use a

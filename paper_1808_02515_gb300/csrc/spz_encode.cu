@@ -7,13 +7,13 @@
 //   1. the chunk's rows are staged in shared memory (128-bit loads);
 //   2. FIRE only: one thread per column runs the block-level recurrence of
 //      alpha (Algorithm 3 with alpha fixed per block, one averaged update per
-//      block from the gradients of rows 0, 2, 4, 6 — Sec. 3.2.2);
+//      block from the gradients of rows 0, 2, 4, 6 — Sec. 4.2.2);
 //   3. every (block, column) recomputes its 8 errors, zigzags them and takes
-//      the width from the OR of the column (Sec. 3.3), promoting w-1 to w;
+//      the width from the OR of the column (Sec. 4.3), promoting w-1 to w;
 //   4. blocks whose widths are all zero merge into runs; records, groups of G
 //      record headers and payload offsets are laid out (Algorithm 1);
 //   5. headers and payloads are packed into a shared-memory copy of the body
-//      (column-major if D*w <= 32, else row-major — Sec. 3.3);
+//      (column-major if D*w <= 32, else row-major — Sec. 4.3);
 //   6. a decoupled look-back over the chunks' body sizes (single pass,
 //      bounded waits) gives the body's offset in the stream;
 //   7. the body and its chunk-table entry are written; the last chunk writes

@@ -1,10 +1,10 @@
-// Huffman stage of the CUDA Sprintz codec (Sec. 3.4: byte symbols, applied to
+// Huffman stage of the CUDA Sprintz codec (Sec. 4.4: byte symbols, applied to
 // the bit-packed bytes).  The paper uses Huff0; this is our own canonical,
 // length-limited code shared by a segment of `huff_chunks` consecutive chunks:
 //   lengths   package-merge (Larmore & Hirschberg 1990) with maximum length 11,
 //             leaves ordered by (frequency, symbol), a leaf before a package of
 //             equal weight, one used symbol -> length 1;
-//   codes     canonical (RFC 1951 Sec. 3.2.2: by length, then symbol), each
+//   codes     canonical (RFC 1951 Sec. 4.2.2: by length, then symbol), each
 //             code's most significant bit first in the least-significant-bit-
 //             first stream;
 //   raw       a segment whose coded bytes (each chunk padded to a byte) are not

@@ -4,7 +4,7 @@ These generators produce the integer time series that the CUDA codec and the
 CPU oracle are both run on. They hold none of the codec's arithmetic: they only
 draw samples. Each one stands in for a workload shape of the paper: the paper's
 own datasets (UCR, PAMAP, MSRC-12, UCI Gas, AMPDs) are not available, and its
-throughput experiment (Sec. 4.3) uses uniformly random values, which
+throughput experiment (Sec. 5.4) uses uniformly random values, which
 ``uniform`` reproduces.
 
 Workloads:

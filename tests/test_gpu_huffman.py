@@ -1,4 +1,4 @@
-"""The Huffman stage (Sec. 3.4, our length-limited canonical code per segment
+"""The Huffman stage (Sec. 4.4, our length-limited canonical code per segment
 of chunks): GPU streams equal the oracle's byte for byte, including segments
 stored raw, and decode bit-exactly; corrupt tables are flagged."""
 import numpy as np

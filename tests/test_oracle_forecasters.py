@@ -1,10 +1,10 @@
 """Pins of the oracle's two further forecasters against facts fixed outside it.
 
 Forecaster 2 is double-delta coding, the a = 2, b = -1 member of the
-autoregressive family of Sec. 3.2.2 (predict x_{i-1} + delta_{i-1}).
+autoregressive family of Sec. 4.2.2 (predict x_{i-1} + delta_{i-1}).
 Forecaster 3 is FIRE exactly as Algorithm 3 prints it: alpha derived from the
 accumulator and one gradient step at every sample, instead of the block form
-(alpha per block, one averaged update from every other sample) that Sec. 3.2.2
+(alpha per block, one averaged update from every other sample) that Sec. 4.2.2
 says is used in practice and that forecaster 1 implements.
 """
 import numpy as np

@@ -22,7 +22,7 @@ def golden():
 
 
 # --------------------------------------------------------------------------
-# Zigzag (Sec. 3.3)
+# Zigzag (Sec. 4.3)
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("w", [8, 16])
@@ -44,12 +44,12 @@ def test_zigzag_bitwise_definition_exhaustive(oracle_mod, w):
 
 
 def test_zigzag_paper_statement(oracle_mod):
-    """Sec. 3.3: twice |e| for nonnegative e, twice |e| minus one for negative."""
+    """Sec. 4.3: twice |e| for nonnegative e, twice |e| minus one for negative."""
     assert [oracle_mod.zigzag(e, 8) for e in (0, -1, 1, -2, 2, -64, 63)] == [0, 1, 2, 3, 4, 127, 126]
 
 
 # --------------------------------------------------------------------------
-# Bit widths (Sec. 3.3)
+# Bit widths (Sec. 4.3)
 # --------------------------------------------------------------------------
 
 def test_bit_length_matches_python(oracle_mod):
@@ -58,14 +58,14 @@ def test_bit_length_matches_python(oracle_mod):
 
 
 def test_width_worked_example(oracle_mod):
-    """Sec. 3.3 worked value: largest zigzagged value 16 = 00010000 has three
+    """Sec. 4.3 worked value: largest zigzagged value 16 = 00010000 has three
     leading zeros, so the column needs 8 - 3 = 5 bits."""
     assert oracle_mod.column_width([16, 3, 0, 7, 1, 0, 2, 5], 8) == 5
 
 
 @pytest.mark.parametrize("w", [8, 16])
 def test_width_promotion(oracle_mod, w):
-    """Sec. 3.3: width w-1 is stored and decoded as w; every other width is
+    """Sec. 4.3: width w-1 is stored and decoded as w; every other width is
     the bit length of the OR of the column."""
     assert oracle_mod.column_width([(1 << (w - 1)) - 1] + [0] * 7, w) == w
     assert oracle_mod.column_width([1 << (w - 2)] + [0] * 7, w) == w
@@ -80,11 +80,11 @@ def test_width_promotion(oracle_mod, w):
 
 
 # --------------------------------------------------------------------------
-# Delta coding (Sec. 3.2.1)
+# Delta coding (Sec. 4.2.1)
 # --------------------------------------------------------------------------
 
 def test_delta_paper_example(oracle_mod):
-    """Sec. 4.5: delta coding {0, -1, 0, 0} gives {0, -1, 1, 0}."""
+    """Sec. 5.7: delta coding {0, -1, 0, 0} gives {0, -1, 1, 0}."""
     x = np.array([0, 255, 0, 0, 0, 0, 0, 0], dtype=np.uint8)
     e = oracle_mod.forecast_errors(x, forecaster=0)[:, 0]
     assert list(e[:4]) == [0, -1, 1, 0]
@@ -105,7 +105,7 @@ def test_delta_is_numpy_diff(oracle_mod, w):
 
 
 # --------------------------------------------------------------------------
-# FIRE (Sec. 3.2.2, Algorithm 3)
+# FIRE (Sec. 4.2.2, Algorithm 3)
 # --------------------------------------------------------------------------
 
 def _wrap(v, w):
@@ -115,7 +115,7 @@ def _wrap(v, w):
 @pytest.mark.parametrize("w", [8, 16])
 def test_fire_without_learning_is_delta(oracle_mod, w):
     """alpha = 0 (learning disabled) predicts the previous sample: FIRE's
-    errors equal delta coding's (Sec. 3.2.2: a = 1, b = 0 is delta coding)."""
+    errors equal delta coding's (Sec. 4.2.2: a = 1, b = 0 is delta coding)."""
     rng = np.random.default_rng(1)
     dt = np.uint8 if w == 8 else np.uint16
     x = rng.integers(0, 1 << w, (128, 3)).astype(dt)
@@ -127,7 +127,7 @@ def test_fire_without_learning_is_delta(oracle_mod, w):
 @pytest.mark.parametrize("w", [8, 16])
 def test_fire_alpha_one_is_double_delta(oracle_mod, w):
     """alpha = 2^w (1.0 in fixed point) predicts x_{i-1} + delta_{i-1}: the
-    errors are second differences (Sec. 3.2.2: a = 2, b = -1)."""
+    errors are second differences (Sec. 4.2.2: a = 2, b = -1)."""
     rng = np.random.default_rng(2)
     dt = np.uint8 if w == 8 else np.uint16
     x = rng.integers(0, 1 << w, (96, 4)).astype(dt)
@@ -141,7 +141,7 @@ def test_fire_alpha_one_is_double_delta(oracle_mod, w):
 @pytest.mark.parametrize("w", [8, 16])
 def test_fire_alpha_minus_half_is_mean_of_two(oracle_mod, w):
     """alpha = -2^(w-1) (-1/2) predicts x_{i-1} - floor(delta_{i-1} / 2), i.e.
-    the mean of the previous two samples (Sec. 3.2.2: a = b = 1/2)."""
+    the mean of the previous two samples (Sec. 4.2.2: a = b = 1/2)."""
     rng = np.random.default_rng(3)
     dt = np.uint8 if w == 8 else np.uint16
     x = rng.integers(0, 1 << w, (64, 2)).astype(dt)
@@ -207,7 +207,7 @@ def test_fire_linear_series_closed_form(oracle_mod, w, slope):
 
 @pytest.mark.parametrize("fc", [0, 1])
 def test_constant_series_one_run_per_chunk(oracle_mod, fc):
-    """Sec. 3.2.1: delta gives zero errors exactly when the data is constant;
+    """Sec. 4.2.1: delta gives zero errors exactly when the data is constant;
     FIRE with alpha = 0 in the first block predicts the constant from row 1 on
     and never learns (sign(0) = 0). So each chunk is its first block plus one
     run record of the remaining blocks."""
@@ -317,7 +317,7 @@ def test_sizes_match_independent_model(oracle_mod, D, w, fc, G, cr):
 
 
 def test_column_major_payload_is_sum_of_widths(oracle_mod):
-    """Sec. 3.3: with column-major packing each column's 8 values fill
+    """Sec. 4.3: with column-major packing each column's 8 values fill
     exactly n_j bytes (no padding), for every width 0..w."""
     seen = set()
     for v in range(0, 256, 3):
