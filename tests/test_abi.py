@@ -56,7 +56,7 @@ def test_max_size_matches_oracle(spz, oracle_mod, rows, D, w, opts):
 
 def test_invalid_options_rejected(spz):
     bad = [dict(group_blocks=0), dict(group_blocks=9), dict(chunk_rows=12), dict(learn_shift=16),
-           dict(forecaster=2), dict(huffman=1, huff_chunks=0)]
+           dict(forecaster=4), dict(huffman=1, huff_chunks=0)]
     for b in bad:
         assert spz.max_compressed_size(100, 4, 8, spz.Opts(**b)) == 0, b
     assert spz.max_compressed_size(100, 0, 8, spz.Opts()) == 0
