@@ -53,7 +53,10 @@ extern "C" {
 /* Codec options (the paper's knobs, Sec. 4.1 and 5.2: SprintzDelta,
  * SprintzFIRE, SprintzFIRE+Huf). */
 typedef struct {
-  uint8_t forecaster;   /* 0 = delta coding (Sec. 4.2.1), 1 = FIRE (Sec. 4.2.2) */
+  uint8_t forecaster;   /* 0 = delta coding (Sec. 4.2.1); 1 = FIRE as used in practice, alpha
+                           per block and one averaged update (Sec. 4.2.2); 2 = double delta,
+                           the a = 2, b = -1 model of Sec. 4.2.2; 3 = FIRE exactly as
+                           Algorithm 3 prints it, alpha and an update at every sample */
   uint8_t huffman;      /* 1 = Huffman-code the bit-packed bytes (Sec. 4.4) */
   uint8_t group_blocks; /* G, 1..8: record headers stored together (Sec. 4.3); the paper uses 2 */
   uint8_t learn_shift;  /* FIRE: alpha = accumulator >> learn_shift; 1 gives eta = 1/2 (Sec. 4.2.2) */
@@ -178,6 +181,23 @@ int sprintz_batch_run(sprintz_ctx *ctx, void *workspace, uint64_t ws_bytes, void
 int sprintz_compress_noalloc(const void *src, uint64_t rows, uint32_t D, uint32_t w,
                              const sprintz_opts *opts, void *dst, uint64_t dst_cap,
                              uint64_t *d_out_size, void *stream);
+
+/* The forecasting step alone, the subroutine that the FIRE Speed experiment
+ * of Sec. 5.6 times: inverse = 0 turns samples into their forecast errors,
+ * inverse = 1 rebuilds the samples from such errors.  Neither changes the
+ * size: errors are signed w-bit values stored as w-bit two's complement in
+ * the samples' row-major layout.
+ *   - forecaster 0..3 as in sprintz_opts, learn_shift as there.
+ *   - The forecaster restarts every chunk_rows rows (a multiple of 8; 0 =
+ *     one chunk, a single sequential pass per column), as in the codec.
+ *   - Whole 8-row blocks are transformed; the rows % 8 trailing rows are
+ *     copied unchanged.
+ *   - src and dst: rows x D samples, 8-byte aligned (else
+ *     SPRINTZ_ERR_UNSUPPORTED); dst may equal src.  No workspace.
+ *   - 2^32 rows or more with chunk_rows = 0 is SPRINTZ_ERR_UNSUPPORTED. */
+int sprintz_forecast(sprintz_ctx *ctx, const void *src, uint64_t rows, uint32_t D, uint32_t w,
+                     uint32_t forecaster, uint32_t learn_shift, uint32_t chunk_rows, int inverse, void *dst,
+                     void *stream);
 
 /* Parse a HOST copy of a stream's first n >= 64 bytes. */
 int sprintz_query(const void *host_header, uint64_t n, sprintz_info *out);

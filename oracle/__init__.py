@@ -79,6 +79,8 @@ def lib():
         L.spo_column_width.argtypes = [vp, u32]
         L.spo_forecast_errors.restype = ctypes.c_int
         L.spo_forecast_errors.argtypes = [vp, u64, u32, u32, i32, i32, i32, i64, vp]
+        L.spo_forecast_reconstruct.restype = ctypes.c_int
+        L.spo_forecast_reconstruct.argtypes = [vp, u64, u32, u32, i32, i32, vp]
         L.spo_fire_trace.restype = ctypes.c_int
         L.spo_fire_trace.argtypes = [vp, u64, u32, u32, i32, vp, vp]
         L.spo_huff_code_lengths.restype = ctypes.c_int
@@ -197,6 +199,45 @@ def forecast_errors(x: np.ndarray, forecaster: int, learn_shift: int = 1, test_m
                                    test_mode, pinned_alpha, out.ctypes.data)
     if rc != OK:
         raise OracleError(rc, "forecast_errors")
+    return out
+
+
+def forecast_reconstruct(err: np.ndarray, w: int, forecaster: int, learn_shift: int = 1) -> np.ndarray:
+    """Samples (uint8/uint16, rows x D) rebuilt from forecast errors."""
+    e = np.ascontiguousarray(np.asarray(err, dtype=np.int32))
+    if e.ndim == 1:
+        e = e.reshape(-1, 1)
+    rows, D = e.shape
+    out = np.zeros((rows, D), dtype=np.uint8 if w == 8 else np.uint16)
+    rc = lib().spo_forecast_reconstruct(e.ctypes.data, rows, D, w, forecaster, learn_shift, out.ctypes.data)
+    if rc != OK:
+        raise OracleError(rc, "forecast_reconstruct")
+    return out
+
+
+def forecast_transform(x: np.ndarray, forecaster: int, learn_shift: int = 1, chunk_rows: int = 1024,
+                       inverse: bool = False) -> np.ndarray:
+    """The forecast step alone, chunk by chunk (the state restarts every
+    chunk_rows rows; 0 = one chunk); whole 8-row blocks are transformed and the
+    rows % 8 trailing rows copied. Errors are returned as w-bit two's
+    complement in the samples' dtype, and inverse=True takes that form."""
+    x = np.ascontiguousarray(x)
+    if x.ndim == 1:
+        x = x.reshape(-1, 1)
+    w = 8 * x.itemsize
+    rows = x.shape[0]
+    full = rows - rows % 8
+    out = x.copy()
+    cr = chunk_rows or max(full, 8)
+    for r0 in range(0, full, cr):
+        part = x[r0:min(full, r0 + cr)]
+        if not inverse:
+            e = forecast_errors(part, forecaster, learn_shift)
+            out[r0:r0 + part.shape[0]] = (e.astype(np.int64) % (1 << w)).astype(x.dtype)
+        else:
+            sgn = part.astype(np.int64)
+            sgn = np.where(sgn >= 1 << (w - 1), sgn - (1 << w), sgn)
+            out[r0:r0 + part.shape[0]] = forecast_reconstruct(sgn, w, forecaster, learn_shift)
     return out
 
 

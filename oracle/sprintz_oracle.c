@@ -1037,6 +1037,28 @@ int spo_forecast_errors(const void *src_v, uint64_t rows, uint32_t D, uint32_t w
   return SPO_OK;
 }
 
+/* The inverse of spo_forecast_errors: the samples rebuilt from their errors
+ * (Algorithm 2's non-run branch applied to every block). */
+int spo_forecast_reconstruct(const int32_t *err_in, uint64_t rows, uint32_t D, uint32_t w,
+                             int32_t kind, int32_t learn_shift, void *dst_v) {
+  uint8_t *dst = (uint8_t *)dst_v;
+  if ((w != 8 && w != 16) || D < 1 || D > MAX_D || rows % BLOCK_ROWS) return SPO_ERR_INVALID_ARG;
+  forecaster *f = (forecaster *)malloc(sizeof(forecaster));
+  int64_t *x = (int64_t *)malloc(sizeof(int64_t) * BLOCK_ROWS * D);
+  int64_t *err = (int64_t *)malloc(sizeof(int64_t) * BLOCK_ROWS * D);
+  fc_init(f, kind, D, w, (uint32_t)learn_shift, FIRE_NORMAL, 0);
+  for (uint64_t b = 0; b < rows / BLOCK_ROWS; ++b) {
+    for (uint32_t q = 0; q < BLOCK_ROWS * D; ++q) err[q] = err_in[b * BLOCK_ROWS * D + q];
+    fc_decode_block(f, err, x);
+    for (uint32_t i = 0; i < BLOCK_ROWS; ++i)
+      for (uint32_t j = 0; j < D; ++j) put_sample(dst, b * BLOCK_ROWS + i, j, D, w, x[i * D + j]);
+  }
+  free(f);
+  free(x);
+  free(err);
+  return SPO_OK;
+}
+
 int spo_fire_trace(const void *src_v, uint64_t rows, uint32_t D, uint32_t w,
                    int32_t learn_shift, int64_t *alpha_out, int64_t *acc_out) {
   const uint8_t *src = (const uint8_t *)src_v;

@@ -80,6 +80,11 @@ int spo_forecast_errors(const void *src, uint64_t rows, uint32_t D, uint32_t w,
                         int32_t forecaster, int32_t learn_shift, int32_t test_mode,
                         int64_t pinned_alpha, int32_t *err_out);
 
+/* The inverse of spo_forecast_errors: rebuild `rows` x D samples (written
+ * as little-endian w-bit values) from their errors. */
+int spo_forecast_reconstruct(const int32_t *err_in, uint64_t rows, uint32_t D, uint32_t w,
+                             int32_t forecaster, int32_t learn_shift, void *dst);
+
 /* FIRE per-block state trace: after each block k, alpha_k used in it and the
  * accumulator after its update (arrays of n_blocks x D). */
 int spo_fire_trace(const void *src, uint64_t rows, uint32_t D, uint32_t w,

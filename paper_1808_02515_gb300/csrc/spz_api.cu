@@ -164,6 +164,20 @@ int sprintz_compress(sprintz_ctx *ctx, const void *src, uint64_t rows, uint32_t 
                                  (uint8_t *)workspace, ws_bytes, ctx->d_status, (cudaStream_t)stream);
 }
 
+int sprintz_forecast(sprintz_ctx *ctx, const void *src, uint64_t rows, uint32_t D, uint32_t w,
+                     uint32_t forecaster, uint32_t learn_shift, uint32_t chunk_rows, int inverse, void *dst,
+                     void *stream) {
+  if (!ctx || (rows && (!src || !dst))) return SPRINTZ_ERR_INVALID_ARG;
+  if (w != 8 && w != 16) return SPRINTZ_ERR_UNSUPPORTED_W;
+  if (D < 1 || D > 1024 || forecaster > 3 || learn_shift > 2 * w - 1 || chunk_rows % 8 ||
+      (inverse != 0 && inverse != 1))
+    return SPRINTZ_ERR_INVALID_ARG;
+  if (((uintptr_t)src | (uintptr_t)dst) & 7) return SPRINTZ_ERR_UNSUPPORTED;
+  if (!rows) return SPRINTZ_OK;
+  return spz::launch_forecast(ctx->cfg, (const uint8_t *)src, rows, D, w, forecaster, learn_shift, chunk_rows,
+                              inverse != 0, (uint8_t *)dst, (cudaStream_t)stream);
+}
+
 int sprintz_query(const void *host_header, uint64_t n, sprintz_info *out) {
   if (!host_header || !out) return SPRINTZ_ERR_INVALID_ARG;
   const uint8_t *h = (const uint8_t *)host_header;

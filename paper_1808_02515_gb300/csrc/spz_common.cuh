@@ -241,6 +241,11 @@ struct LaunchCfg {
 
 int make_geom(uint64_t rows, uint32_t D, uint32_t w, const sprintz_opts *o, Geom *g);
 
+// Forecast transform alone (spz_forecast.cu).
+int launch_forecast(const LaunchCfg &cfg, const uint8_t *src, uint64_t rows, uint32_t D, uint32_t w,
+                    uint32_t forecaster, uint32_t learn_shift, uint32_t chunk_rows, bool inverse, uint8_t *dst,
+                    cudaStream_t stream);
+
 // Encoder / decoder launchers (spz_encode.cu, spz_decode.cu).
 uint64_t encode_workspace_bytes(const Geom &g, const LaunchCfg &cfg);
 int launch_encode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint8_t *dst,

@@ -28,7 +28,7 @@ ERR_TIMEOUT = -6
 ERR_CUDA = -7
 ERR_UNSUPPORTED = -8
 
-DELTA, FIRE = 0, 1
+DELTA, FIRE, DDELTA, FIRE_SAMPLE = 0, 1, 2, 3
 
 
 class _Opts(ctypes.Structure):
@@ -106,6 +106,8 @@ def lib() -> ctypes.CDLL:
         L.sprintz_batch_plan.argtypes = [vp, PB, u32, i32, vp, u64, vp]
         L.sprintz_batch_run.restype = i32
         L.sprintz_batch_run.argtypes = [vp, vp, u64, vp]
+        L.sprintz_forecast.restype = i32
+        L.sprintz_forecast.argtypes = [vp, vp, u64, u32, u32, u32, u32, u32, i32, vp, vp]
         L.sprintz_query.restype = i32
         L.sprintz_query.argtypes = [vp, u64, PI]
         L.sprintz_get_status.restype = i32
@@ -229,6 +231,26 @@ class Codec:
                                     ctypes.c_void_p(ws.data_ptr() if ws is not None else 0),
                                     ws.numel() if ws is not None else 0, self._stream(stream))
         _check(rc, "sprintz_compress")
+
+    def forecast(self, x, forecaster: int = FIRE, learn_shift: int = 1, chunk_rows: int = 1024,
+                 inverse: bool = False, out=None, stream=None):
+        """The forecast step alone (sprintz_forecast): samples -> errors, or
+        errors -> samples with inverse=True, on a (rows, D) uint8 / 16-bit
+        CUDA tensor; the result has x's shape and dtype (out may be x)."""
+        torch = self.torch
+        if x.dim() == 1:
+            x = x.view(-1, 1)
+        if x.dtype not in (torch.uint8, torch.int16, torch.uint16):
+            raise TypeError("samples must be uint8 or 16-bit")
+        x = x.contiguous()
+        rows, D = x.shape
+        w = 8 if x.dtype == torch.uint8 else 16
+        y = torch.empty_like(x) if out is None else out
+        rc = lib().sprintz_forecast(self.ctx, ctypes.c_void_p(x.data_ptr() if rows else 0), rows, D, w,
+                                    forecaster, learn_shift, chunk_rows, 1 if inverse else 0,
+                                    ctypes.c_void_p(y.data_ptr() if rows else 0), self._stream(stream))
+        _check(rc, "sprintz_forecast")
+        return y
 
     def compress(self, x, opts: Opts = Opts(), stream=None):
         """Compress a (rows, D) uint8 / uint16 (or int16) CUDA tensor.

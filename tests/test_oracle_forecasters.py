@@ -151,3 +151,36 @@ def test_forecaster_out_of_range_rejected(oracle_mod):
     x = np.zeros((16, 1), np.uint8)
     with pytest.raises(Exception):
         oracle_mod.compress(x, forecaster=4)
+
+
+# --------------------------------------------------------------------------
+# The forecast step alone and its inverse (the FIRE Speed subroutines)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("w", [8, 16])
+def test_reconstruct_delta_is_cumsum(oracle_mod, w):
+    """Delta's inverse is numpy's cumulative sum mod 2^w."""
+    rng = np.random.default_rng(60 + w)
+    e = rng.integers(-(1 << (w - 1)), 1 << (w - 1), (96, 3))
+    x = oracle_mod.forecast_reconstruct(e, w, forecaster=0)
+    assert np.array_equal(x.astype(np.int64), np.cumsum(e, axis=0) % (1 << w))
+
+
+@pytest.mark.parametrize("w", [8, 16])
+def test_reconstruct_double_delta_is_double_cumsum(oracle_mod, w):
+    rng = np.random.default_rng(70 + w)
+    e = rng.integers(-(1 << (w - 1)), 1 << (w - 1), (96, 2))
+    x = oracle_mod.forecast_reconstruct(e, w, forecaster=2)
+    assert np.array_equal(x.astype(np.int64), np.cumsum(np.cumsum(e, axis=0), axis=0) % (1 << w))
+
+
+@pytest.mark.parametrize("fc", [0, 1, 2, 3])
+@pytest.mark.parametrize("w", [8, 16])
+def test_transform_round_trip(oracle_mod, fc, w):
+    """Chunked transform and inverse undo each other, tail rows included."""
+    rng = np.random.default_rng(80 + fc + w)
+    x = rng.integers(0, 1 << w, (1000 + 5, 3)).astype(_dtype(w))
+    e = oracle_mod.forecast_transform(x, fc, chunk_rows=256)
+    assert np.array_equal(e[1000:], x[1000:])
+    assert not np.array_equal(e[:1000], x[:1000])
+    assert np.array_equal(oracle_mod.forecast_transform(e, fc, chunk_rows=256, inverse=True), x)
