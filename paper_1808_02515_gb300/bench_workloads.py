@@ -1,7 +1,9 @@
 """Benchmark runners of the workloads other than the headline one (selected
 with bench.py --workload): the small single stream, the batch of 10,000
-streams (batched launch vs per-stream launches), the Huffman workload and
-the serving loop. Each prints one JSON line like bench.py's."""
+streams (batched launch vs per-stream launches), the Huffman workload,
+the serving loop, and the paper's speed sweeps (the forecast step alone over
+forecasters and column counts, the codec over column counts, header groups
+G and chunk lengths). Each prints one JSON line like bench.py's."""
 from __future__ import annotations
 
 import json
@@ -95,6 +97,12 @@ def run(args, metric, ClockSampler, peaks):
         run_batch(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, synth, spz)
     elif args.workload == "serve":
         run_serve(args, codec, dev, line, synth, spz)
+    elif args.workload == "fire_speed":
+        run_fire_speed(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, synth, spz)
+    elif args.workload == "dsweep":
+        run_dsweep(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, synth, spz)
+    elif args.workload == "gsweep":
+        run_gsweep(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, synth, spz)
     codec.close()
     print(json.dumps(line), flush=True)
 
@@ -201,3 +209,152 @@ def run_serve(args, codec, dev, line, synth, spz):
         "serving": {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                     "gbs": served / span / 1e9, "batches": stats["batches"], "peak_mem": stats["peak_mem"],
                     "wall_s": stats["wall_s"]}})
+
+
+SWEEP_D = (1, 2, 3, 4, 5, 6, 8, 12, 16, 24, 32, 40, 48, 64, 80)
+SWEEP_VALUES = 100_000_000  # the paper's 100M uniformly random values
+
+
+def run_fire_speed(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, synth, spz):
+    """The FIRE Speed experiment (Sec. 5.6): the forecast step alone
+    (samples -> errors and back, no packing) on 100M uniform values viewed as
+    D columns, for delta, FIRE, double delta and FIRE per sample. GB/s count
+    the samples' bytes; the kernel moves twice that (read + write)."""
+    import torch
+    names = {0: "delta", 1: "fire", 2: "double_delta", 3: "fire_per_sample"}
+    table = []
+    with ClockSampler(0) as clk:
+        for w in (8, 16):
+            base = synth.uniform_torch(SWEEP_VALUES, 1, w, seed=6, device=dev).view(-1)
+            for D in SWEEP_D:
+                rows = SWEEP_VALUES // D
+                x = base[:rows * D].view(rows, D)
+                U = x.numel() * x.element_size()
+                e = torch.empty_like(x)
+                y = torch.empty_like(x)
+                for fc in (0, 1, 2, 3):
+                    for _ in range(args.warmup):
+                        codec.forecast(x, forecaster=fc, out=e)
+                        codec.forecast(e, forecaster=fc, inverse=True, out=y)
+                    torch.cuda.synchronize()
+                    assert torch.equal(y, x), ("forecast round trip", w, D, fc)
+                    enc = _time(lambda: codec.forecast(x, forecaster=fc, out=e), args.steps, stream)
+                    dec = _time(lambda: codec.forecast(e, forecaster=fc, inverse=True, out=y), args.steps, stream)
+                    table.append({"w": w, "D": D, "forecaster": names[fc], "encode_gbs": U / (enc * 1e-3) / 1e9,
+                                  "decode_gbs": U / (dec * 1e-3) / 1e9, "encode_ms": enc, "decode_ms": dec,
+                                  "hbm_frac_encode": 2 * U / (enc * 1e-3) / 1e9 / peak,
+                                  "hbm_frac_decode": 2 * U / (dec * 1e-3) / 1e9 / peak})
+            del base
+    fire = [r for r in table if r["forecaster"] == "fire"]
+    best = max(fire, key=lambda r: r["decode_gbs"])
+    line.update({"metric": "forecast-only (FIRE Speed) encode/decode GB/s over column counts",
+                 "value": best["decode_gbs"], "dtype": "u8/u16",
+                 "config": {"workload": "uniform_100M_values_D1-80_forecast_only", "values": SWEEP_VALUES,
+                            "chunk_rows": 1024, "learn_shift": 1, "D": list(SWEEP_D),
+                            "value_is": f"best FIRE decode GB/s (w={best['w']}, D={best['D']})"},
+                 "roofline": {"bound": "hbm", "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                              "kernel": "k_forecast", "bytes_per_launch": "2 x samples (read + write)",
+                              "frac": max(r["hbm_frac_decode"] for r in fire), "traffic": None},
+                 "table": table, "clocks": clk.summary()})
+
+
+def run_dsweep(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, synth, spz):
+    """The codec over column counts (Sec. 5.4 / 5.5): 100M uniform values as
+    D columns (rows % 8 stored raw), SprintzDelta, SprintzFIRE and
+    SprintzFIRE+Huf, compress and decompress GB/s of the samples' bytes."""
+    import torch
+    variants = (("delta", spz.Opts(forecaster=0)), ("fire", spz.Opts(forecaster=1)),
+                ("fire_huf", spz.Opts(forecaster=1, huffman=1)))
+    table = []
+    with ClockSampler(0) as clk:
+        for w in (8, 16):
+            base = synth.uniform_torch(SWEEP_VALUES, 1, w, seed=7, device=dev).view(-1)
+            for D in SWEEP_D:
+                rows = SWEEP_VALUES // D
+                x = base[:rows * D].view(rows, D)
+                U = x.numel() * x.element_size()
+                out = torch.empty_like(x)
+                for name, o in variants:
+                    cap = spz.max_compressed_size(rows, D, w, o)
+                    dst = torch.empty(cap, dtype=torch.uint8, device=dev)
+                    size = torch.zeros(1, dtype=torch.int64, device=dev)
+                    wsn = spz.compress_workspace_size(rows, D, w, o)
+                    ws = torch.empty(max(wsn, 1), dtype=torch.uint8, device=dev)
+                    codec.compress_into(x, rows, D, w, o, dst, size, ws)
+                    torch.cuda.synchronize()
+                    codec.check()
+                    C = int(size.item())
+                    info = spz.query(dst[:64].cpu().numpy().tobytes())
+                    ws_d = torch.empty(max(spz.decompress_workspace_size(info), 1), dtype=torch.uint8, device=dev)
+                    for _ in range(args.warmup):
+                        codec.compress_into(x, rows, D, w, o, dst, size, ws)
+                        codec.decompress_into(dst, C, info, out, ws_d)
+                    torch.cuda.synchronize()
+                    codec.check()
+                    assert torch.equal(out, x), ("round trip", w, D, name)
+                    enc = _time(lambda: codec.compress_into(x, rows, D, w, o, dst, size, ws), args.steps, stream)
+                    dec = _time(lambda: codec.decompress_into(dst, C, info, out, ws_d), args.steps, stream)
+                    table.append({"w": w, "D": D, "variant": name, "ratio": U / C,
+                                  "compress_gbs": U / (enc * 1e-3) / 1e9, "decompress_gbs": U / (dec * 1e-3) / 1e9,
+                                  "compress_ms": enc, "decompress_ms": dec,
+                                  "hbm_frac_decode": (U + C) / (dec * 1e-3) / 1e9 / peak,
+                                  "hbm_frac_encode": (U + C) / (enc * 1e-3) / 1e9 / peak})
+                    del dst, ws, ws_d
+            del base
+    fire = [r for r in table if r["variant"] == "fire"]
+    best = max(fire, key=lambda r: r["decompress_gbs"])
+    line.update({"metric": "decompress and compress GB/s over column counts (uniform data)",
+                 "value": best["decompress_gbs"], "dtype": "u8/u16",
+                 "config": {"workload": "uniform_100M_values_D1-80_codec", "values": SWEEP_VALUES,
+                            "chunk_rows": 1024, "D": list(SWEEP_D),
+                            "value_is": f"best SprintzFIRE decompress GB/s (w={best['w']}, D={best['D']})"},
+                 "roofline": {"bound": "hbm", "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                              "frac": best["hbm_frac_decode"], "traffic": None},
+                 "table": table, "clocks": clk.summary()})
+
+
+def run_gsweep(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, synth, spz):
+    """Header groups G and chunk lengths on the 2^24-row sensor workload
+    (FIRE): ratio and compress / decompress GB/s (Sec. 4.3 states the paper's
+    G = 2; larger G amortizes header reads)."""
+    import torch
+    x = synth.sensor_u16_torch(1 << 24, 8, seed=1, device=dev)
+    rows, D, w = x.shape[0], 8, 16
+    U = x.numel() * x.element_size()
+    out = torch.empty_like(x)
+    table = []
+    with ClockSampler(0) as clk:
+        for G in (1, 2, 4, 8):
+            for cr in (256, 1024, 4096, 16384):
+                o = spz.Opts(forecaster=1, group_blocks=G, chunk_rows=cr)
+                cap = spz.max_compressed_size(rows, D, w, o)
+                dst = torch.empty(cap, dtype=torch.uint8, device=dev)
+                size = torch.zeros(1, dtype=torch.int64, device=dev)
+                ws = torch.empty(max(spz.compress_workspace_size(rows, D, w, o), 1), dtype=torch.uint8, device=dev)
+                codec.compress_into(x, rows, D, w, o, dst, size, ws)
+                torch.cuda.synchronize()
+                codec.check()
+                C = int(size.item())
+                info = spz.query(dst[:64].cpu().numpy().tobytes())
+                ws_d = torch.empty(max(spz.decompress_workspace_size(info), 1), dtype=torch.uint8, device=dev)
+                for _ in range(args.warmup):
+                    codec.compress_into(x, rows, D, w, o, dst, size, ws)
+                    codec.decompress_into(dst, C, info, out, ws_d)
+                torch.cuda.synchronize()
+                codec.check()
+                assert torch.equal(out, x), ("round trip", G, cr)
+                enc = _time(lambda: codec.compress_into(x, rows, D, w, o, dst, size, ws), args.steps, stream)
+                dec = _time(lambda: codec.decompress_into(dst, C, info, out, ws_d), args.steps, stream)
+                table.append({"G": G, "chunk_rows": cr, "ratio": U / C,
+                              "compress_gbs": U / (enc * 1e-3) / 1e9, "decompress_gbs": U / (dec * 1e-3) / 1e9,
+                              "hbm_frac_decode": (U + C) / (dec * 1e-3) / 1e9 / peak,
+                              "hbm_frac_encode": (U + C) / (enc * 1e-3) / 1e9 / peak})
+                del dst, ws, ws_d
+    ref = next(r for r in table if r["G"] == 2 and r["chunk_rows"] == 1024)
+    line.update({"metric": "decompress and compress GB/s and ratio over header groups and chunk lengths",
+                 "value": ref["decompress_gbs"], "dtype": "u16",
+                 "config": {"workload": "sensor_u16_D8_2^24rows_FIRE_G_CR_sweep", "G": [1, 2, 4, 8],
+                            "chunk_rows": [256, 1024, 4096, 16384], "value_is": "decompress GB/s at G=2, CR=1024"},
+                 "roofline": {"bound": "hbm", "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                              "frac": ref["hbm_frac_decode"], "traffic": None},
+                 "table": table, "clocks": clk.summary()})

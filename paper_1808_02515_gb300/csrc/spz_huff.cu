@@ -170,6 +170,8 @@ struct HuffEncParams {
   uint32_t *chunk_coded; // [n_chunks] coded bytes of each chunk
   uint64_t *seg_total;   // [n_segments] coded bytes of each segment
   uint64_t *seg_prefix;  // [n_segments + 1]
+  uint32_t *gbuf;        // per-segment code buffers in global memory when a chunk's code
+  uint64_t gbuf_words;   // does not fit shared memory (else null)
 };
 
 // Chunk c of P: body offset (from P's data), records, packed bytes.
@@ -312,7 +314,8 @@ __global__ void __launch_bounds__(kHuffThreads) k_huff_encode(HuffEncParams p) {
       for (uint32_t k = k0; k < k1; ++k) nb += sm.len[bytes[off + k]];
       s_bits[t] = nb;
       const uint32_t words = (coded + 3) / 4;
-      for (uint32_t k = t; k < words; k += blockDim.x) obuf[k] = 0;
+      uint32_t *ob32 = p.gbuf ? p.gbuf + (uint64_t)s * p.gbuf_words : obuf;
+      for (uint32_t k = t; k < words; k += blockDim.x) ob32[k] = 0;
       __syncthreads();
       // exclusive scan of s_bits (Hillis-Steele in place)
       for (uint32_t o = 1; o < blockDim.x; o <<= 1) {
@@ -327,12 +330,12 @@ __global__ void __launch_bounds__(kHuffThreads) k_huff_encode(HuffEncParams p) {
         const uint32_t l = sm.len[sym];
         const uint32_t v = bitrev(sm.code[sym], l);
         const uint32_t wi = bit >> 5, sh = bit & 31;
-        atomicOr(&obuf[wi], v << sh);
-        if (sh + l > 32) atomicOr(&obuf[wi + 1], v >> (32 - sh));
+        atomicOr(&ob32[wi], v << sh);
+        if (sh + l > 32) atomicOr(&ob32[wi + 1], v >> (32 - sh));
         bit += l;
       }
       __syncthreads();
-      const uint8_t *ob = reinterpret_cast<const uint8_t *>(obuf);
+      const uint8_t *ob = reinterpret_cast<const uint8_t *>(ob32);
       for (uint32_t k = t; k < coded; k += blockDim.x) d[k] = ob[k];
     }
     __syncthreads();
@@ -571,8 +574,18 @@ static uint64_t plain_cap(const Geom &g) {
 }
 
 struct HuffEncLayout {
-  uint64_t P, P_cap, size_word, coded, seg_total, seg_prefix, inner, inner_bytes, total;
+  uint64_t P, P_cap, size_word, coded, seg_total, seg_prefix, gbuf, gbuf_bytes, inner, inner_bytes, total;
+  uint64_t obytes;  // one chunk's code buffer
+  bool global_buf;  // the buffer lives in the workspace (too large for shared memory)
 };
+
+// Static shared memory of the Huffman encoder (its per-chunk code buffer is
+// dynamic shared memory on top of it).
+static uint64_t huff_encode_static_smem() {
+  cudaFuncAttributes a{};
+  if (cudaFuncGetAttributes(&a, k_huff_encode) != cudaSuccess) return 64 * 1024;
+  return a.sharedSizeBytes;
+}
 
 static HuffEncLayout huff_enc_layout(const Geom &g, const LaunchCfg &cfg) {
   HuffEncLayout L{};
@@ -583,7 +596,11 @@ static HuffEncLayout huff_enc_layout(const Geom &g, const LaunchCfg &cfg) {
   L.coded = L.size_word + 256;
   L.seg_total = a256(L.coded + 4ull * g.n_chunks);
   L.seg_prefix = a256(L.seg_total + 8ull * g.n_segments);
-  L.inner = a256(L.seg_prefix + 8ull * (g.n_segments + 1));
+  L.obytes = ((g.max_body * kHuffMaxLen / 8 + 16) + 15) & ~15ull;
+  L.global_buf = L.obytes + huff_encode_static_smem() > (uint64_t)cfg.max_smem_optin;
+  L.gbuf = a256(L.seg_prefix + 8ull * (g.n_segments + 1));
+  L.gbuf_bytes = L.global_buf ? (uint64_t)g.n_segments * L.obytes : 0;
+  L.inner = a256(L.gbuf + L.gbuf_bytes);
   L.inner_bytes = encode_workspace_bytes(gp, cfg);
   L.total = L.inner + L.inner_bytes;
   return L;
@@ -619,11 +636,15 @@ int launch_encode_huffman(const Geom &g, const LaunchCfg &cfg, const uint8_t *sr
   hp.seg_prefix = reinterpret_cast<uint64_t *>(ws + L.seg_prefix);
   k_huff_build<<<g.n_segments, kHuffThreads, 0, stream>>>(hp);
   k_huff_scan<<<1, 1024, 0, stream>>>(hp.seg_total, hp.seg_prefix, g.n_segments);
-  const uint64_t obytes = ((g.max_body * kHuffMaxLen / 8 + 16) + 15) & ~15ull;
-  if (obytes > 48 * 1024 &&
-      cudaFuncSetAttribute(k_huff_encode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)obytes) !=
-          cudaSuccess)
-    return SPRINTZ_ERR_UNSUPPORTED;
+  uint64_t obytes = L.obytes;
+  if (L.global_buf) {
+    hp.gbuf = reinterpret_cast<uint32_t *>(ws + L.gbuf);
+    hp.gbuf_words = L.obytes / 4;
+    obytes = 0;
+  } else if (cudaFuncSetAttribute(k_huff_encode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)obytes) !=
+             cudaSuccess) {
+    return SPRINTZ_ERR_CUDA;
+  }
   k_huff_encode<<<g.n_segments, kHuffThreads, obytes, stream>>>(hp);
   return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
 }

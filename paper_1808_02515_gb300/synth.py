@@ -168,6 +168,16 @@ def _tgen(seed: int, device):
     return g
 
 
+def uniform_torch(rows: int, cols: int, w: int, seed: int, device="cuda"):
+    """Uniformly random w-bit values drawn on the device (uint8, or int16
+    holding the 16-bit patterns)."""
+    import torch
+    g = _tgen(seed, device)
+    if w == 8:
+        return torch.randint(0, 256, (rows, cols), generator=g, device=device, dtype=torch.int32).to(torch.uint8)
+    return torch.randint(-32768, 32768, (rows, cols), generator=g, device=device, dtype=torch.int32).to(torch.int16)
+
+
 def random_walk_u8_torch(rows: int, cols: int, scale: float, const_frac: float, seed: int,
                          device="cuda"):
     import torch

@@ -61,6 +61,17 @@ def test_huffman_u16_and_wide(codec, oracle_mod):
     _rt(codec, oracle_mod, synth.random_walk_u8(9000, 40, scale=1.0, seed=3), huff_chunks=4)
 
 
+@pytest.mark.parametrize("w,D", [(8, 24), (8, 32), (16, 40), (16, 80), (16, 200)])
+def test_huffman_large_chunk_bodies(codec, oracle_mod, w, D):
+    """Chunk bodies whose code buffer needs more than 48 KB of shared memory,
+    or more than a CTA can have (then the buffer is in the workspace)."""
+    from paper_1808_02515_gb300 import synth
+    x = synth.uniform(2048 + 3, D, w, seed=D)
+    _rt(codec, oracle_mod, x, huff_chunks=1)
+    xs = synth.random_walk_u8(3000, D, scale=3.0, seed=D) if w == 8 else synth.sensor_u16(3000, D, seed=D)
+    _rt(codec, oracle_mod, xs, huff_chunks=2)
+
+
 def test_huffman_raw_segments(codec, oracle_mod):
     """Near-uniform packed bytes: the segments are stored raw (zero tables)."""
     from helpers import flat_bytes_u8
