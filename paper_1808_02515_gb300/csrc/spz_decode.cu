@@ -824,6 +824,180 @@ static const void *lane_decoder(uint32_t D) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Column-per-thread decoder for wide rows (32 < D <= 1024)
+//
+// One CTA decodes one chunk; thread j owns column j.  The chunk's record
+// state is the same in every thread.  At each header group the CTA copies
+// the group's bytes (at most gmax) into shared memory; every thread reads its
+// width code there, a block-wide scan of the widths gives its bit offset and
+// the record's size, and each thread unpacks, un-zigzags and inverts its
+// column's forecast in registers, writing its samples of each row (the
+// threads of a row write consecutive samples).
+// ---------------------------------------------------------------------------
+
+template <int W>
+__global__ void __launch_bounds__(1024) k_decode_wide(DecParams p) {
+  extern __shared__ __align__(16) uint8_t gsm[];  // the current header group (+ 8 spare bytes)
+  __shared__ uint32_t s_wsum[2][32];              // per-warp width sums, two records in turn
+  const Geom &g = p.g;
+  const uint32_t D = g.D, j = threadIdx.x, lane = j & 31, warp = j >> 5;
+  const uint32_t nwarps = blockDim.x >> 5;
+  const bool col = j < D;
+  constexpr uint32_t wb = W / 8;
+  const uint32_t hb = g.hb, G = g.G, H = g.hdr_bytes;
+  const uint32_t gmax = H + G * D * W;
+  const uint64_t c = (uint64_t)p.c_begin + blockIdx.x;
+  if (c >= p.c_end) return;
+
+  const uint64_t tail_off = le_u64(p.src + 48);
+  const bool hdr_ok = tail_off >= g.data_off && tail_off <= p.src_size;
+  const uint64_t data_bytes = hdr_ok ? tail_off - g.data_off : 0;
+  const uint8_t *e = p.src + kHdrBytes + c * kEntryBytes;
+  const uint64_t off = le_u64(e);
+  const uint32_t nrec = le_u32(e + 8);
+  const uint32_t packed = le_u32(e + 12);
+  const uint64_t end = c + 1 < g.n_chunks ? le_u64(e + kEntryBytes) : data_bytes;
+  const uint64_t row0 = c * g.chunk_rows;
+  const uint32_t nb = (uint32_t)(min((uint64_t)g.chunk_rows, g.full_rows - row0) / kBlockRows);
+  if (!hdr_ok || off > end || end > data_bytes || end - off != packed || nrec < 1 || nrec > nb) {
+    if (j == 0) set_status(p.status, SPRINTZ_ERR_CORRUPT);
+    return;
+  }
+  const uint8_t *body = p.src + g.data_off + off;
+  const uint32_t *g32 = reinterpret_cast<const uint32_t *>(gsm);
+  uint32_t hdr = 0;  // body offset of the staged group
+  // bits [bit, bit + n) of the body, bit inside the staged group
+  auto rbits = [&](uint32_t bit, uint32_t mask) {
+    const uint32_t q = bit - hdr * 8;
+    const uint32_t i0 = q >> 5;
+    return __funnelshift_r(g32[i0], g32[i0 + 1], q) & mask;
+  };
+  uint8_t *out = p.dst + (row0 - (uint64_t)p.c_begin * g.chunk_rows) * D * wb + j * wb;
+  const uint32_t row_stride = D * wb;
+
+  uint32_t gpos = 0, gslot = G, rec = 0, rem = 0, pbit = 0, stride = 0, mask = 0, par = 0;
+  bool bad_any = false;
+  uint32_t xp = 0;
+  int32_t dp = 0, acc = 0;
+  for (uint32_t b = 0; b < nb; ++b) {
+    if (rem == 0) {
+      if (gslot == G) {
+        // stage the next group: [gpos, gpos + gmax) clipped to the body
+        hdr = gpos;
+        gpos += H;
+        gslot = 0;
+        __syncthreads();  // every thread is done with the previous group
+        const uint32_t n = hdr < packed ? min(gmax, packed - hdr) : 0u;
+        for (uint32_t k = j; k < (gmax + 8 + 3) / 4; k += blockDim.x) {
+          uint32_t v = 0;
+          for (uint32_t t = 0; t < 4; ++t) {
+            const uint32_t q = 4 * k + t;
+            if (q < n) v |= (uint32_t)body[hdr + q] << (8 * t);
+          }
+          reinterpret_cast<uint32_t *>(gsm)[k] = v;
+        }
+        __syncthreads();
+      }
+      const bool hdr_in = gpos <= packed;
+      const uint32_t code = col && hdr_in ? rbits(hdr * 8 + (gslot * D + j) * hb, (1u << hb) - 1u) : 0u;
+      const uint32_t nw = code == (uint32_t)W - 1 ? (uint32_t)W : code;
+      // block-wide exclusive scan of the widths
+      uint32_t v = nw;
+#pragma unroll
+      for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        if (lane >= o) v += t;
+      }
+      if (lane == 31) s_wsum[par][warp] = v;
+      __syncthreads();
+      if (warp == 0) {
+        uint32_t t = lane < nwarps ? s_wsum[par][lane] : 0u;
+#pragma unroll
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+          const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, t, o);
+          if (lane >= o) t += u;
+        }
+        if (lane < nwarps) s_wsum[par][lane] = t;
+      }
+      __syncthreads();
+      const uint32_t prefix = v - nw + (warp ? s_wsum[par][warp - 1] : 0u);
+      const uint32_t total = s_wsum[par][nwarps - 1];
+      par ^= 1;
+      // the record: a zero-block run (u16 count) or a block
+      const bool isrun = total == 0;
+      const uint32_t cnt = rbits(gpos * 8, 0xFFFFu);
+      const uint32_t size = g.col_major ? total : 8 * ((total + 7) / 8);
+      const uint32_t rsize = isrun ? 2u : size;
+      bad_any |= rec >= nrec || !hdr_in || gpos + rsize > packed || (isrun && (cnt == 0 || b + cnt > nb));
+      rem = isrun ? cnt : 1u;
+      mask = isrun ? 0u : (1u << nw) - 1u;
+      pbit = isrun ? gpos * 8 : (g.col_major ? (gpos + prefix) * 8 : gpos * 8 + prefix);
+      stride = isrun ? 0u : (g.col_major ? nw : size);
+      gpos += rsize;
+      gslot++;
+      rec++;
+    }
+    if (col) {
+      uint32_t z[kBlockRows];
+#pragma unroll
+      for (int i = 0; i < kBlockRows; ++i) z[i] = rbits(pbit + i * stride, mask);
+      uint8_t *ob = out + (uint64_t)b * kBlockRows * row_stride;
+      auto put = [&](int i, uint32_t x) {
+        if (W == 8)
+          ob[i * row_stride] = (uint8_t)x;
+        else
+          *reinterpret_cast<uint16_t *>(ob + i * row_stride) = (uint16_t)x;
+      };
+      if (g.forecaster == kFcDelta) {
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) {
+          xp += (z[i] >> 1) ^ (0u - (z[i] & 1u));
+          put(i, xp);
+        }
+      } else if (g.forecaster == kFcDDelta) {
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) {
+          const int32_t d = sext<W>((uint32_t)dp + ((z[i] >> 1) ^ (0u - (z[i] & 1u))));
+          xp += (uint32_t)d;
+          put(i, xp);
+          dp = d;
+        }
+      } else if (g.forecaster == kFcFireSample) {
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) {
+          const uint32_t A = (uint32_t)(acc >> g.learn_shift) << (32 - 2 * W);
+          const uint32_t ev = (z[i] >> 1) ^ (0u - (z[i] & 1u));
+          const int32_t d = (int32_t)(A * (uint32_t)dp + (ev << (32 - W))) >> (32 - W);
+          acc = wrap_acc<W>((int32_t)((uint32_t)acc + (uint32_t)(z[i] == 0 ? 0 : ((z[i] & 1u) ? -dp : dp))));
+          xp += (uint32_t)d;
+          put(i, xp);
+          dp = d;
+        }
+      } else {
+        const uint32_t A = (uint32_t)(acc >> g.learn_shift) << (32 - 2 * W);
+        int32_t gsum = 0;
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) {
+          const uint32_t ev = (z[i] >> 1) ^ (0u - (z[i] & 1u));
+          const int32_t d = (int32_t)(A * (uint32_t)dp + (ev << (32 - W))) >> (32 - W);
+          if ((i & 1) == 0) gsum += z[i] == 0 ? 0 : ((z[i] & 1u) ? -dp : dp);
+          xp += (uint32_t)d;
+          put(i, xp);
+          dp = d;
+        }
+        acc = wrap_acc<W>((int32_t)((uint32_t)acc + (uint32_t)(gsum >> 2)));
+      }
+    }
+    rem--;
+  }
+  // every record consumed, the body used up, unused slots of the last group zero
+  bool bad = bad_any || rec != nrec || gpos != packed;
+  if (!bad && col)
+    for (uint32_t s = gslot; s < G && !bad; ++s) bad |= rbits(hdr * 8 + (s * D + j) * hb, (1u << hb) - 1u) != 0;
+  if (bad) set_status(p.status, SPRINTZ_ERR_CORRUPT);
+}
+
 // One stream of a batched decode.
 struct DecBatchItem {
   DecParams p;
@@ -1131,6 +1305,17 @@ int launch_decode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint6
       return SPRINTZ_ERR_CUDA;
     void *args[] = {&p, &rg};
     if (cudaLaunchKernel(fn, dim3((uint32_t)grid), dim3(kLaneThreads), args, smem, stream) != cudaSuccess)
+      return SPRINTZ_ERR_CUDA;
+  } else if (g.n_chunks > 0 && g.D > 32 && g.n_chunks <= 0x7FFFFFFFull) {
+    const uint32_t threads = (g.D + 31) & ~31u;
+    const uint64_t smem = (((uint64_t)g.hdr_bytes + (uint64_t)g.G * g.D * g.w + 8 + 15) & ~15ull);
+    if (smem > (uint64_t)cfg.max_smem_optin) return SPRINTZ_ERR_UNSUPPORTED;
+    const void *fn = g.w == 8 ? (const void *)k_decode_wide<8> : (const void *)k_decode_wide<16>;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return SPRINTZ_ERR_CUDA;
+    void *args[] = {&p};
+    if (cudaLaunchKernel(fn, dim3((uint32_t)g.n_chunks), dim3(threads), args, smem, stream) != cudaSuccess)
       return SPRINTZ_ERR_CUDA;
   } else if (g.n_chunks > 0) {
     DecPlan pl = dec_plan(g, cfg);
