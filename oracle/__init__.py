@@ -44,8 +44,8 @@ def build(force: bool = False) -> str:
     if force or stale:
         fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
         os.close(fd)
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-Wall", "-fPIC", "-shared",
-                               "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-Wall", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -81,6 +81,12 @@ def lib():
         L.spo_forecast_errors.argtypes = [vp, u64, u32, u32, i32, i32, i32, i64, vp]
         L.spo_forecast_reconstruct.restype = ctypes.c_int
         L.spo_forecast_reconstruct.argtypes = [vp, u64, u32, u32, i32, i32, vp]
+        L.spo_quantize.restype = ctypes.c_int
+        L.spo_quantize.argtypes = [vp, u64, u32, u32, vp, vp]
+        L.spo_dequantize.restype = ctypes.c_int
+        L.spo_dequantize.argtypes = [vp, u64, u32, u32, vp, vp]
+        L.spo_quant_nmse.restype = ctypes.c_int
+        L.spo_quant_nmse.argtypes = [vp, vp, u64, u32, u32, vp, vp]
         L.spo_fire_trace.restype = ctypes.c_int
         L.spo_fire_trace.argtypes = [vp, u64, u32, u32, i32, vp, vp]
         L.spo_huff_code_lengths.restype = ctypes.c_int
@@ -238,6 +244,48 @@ def forecast_transform(x: np.ndarray, forecaster: int, learn_shift: int = 1, chu
             sgn = part.astype(np.int64)
             sgn = np.where(sgn >= 1 << (w - 1), sgn - (1 << w), sgn)
             out[r0:r0 + part.shape[0]] = forecast_reconstruct(sgn, w, forecaster, learn_shift)
+    return out
+
+
+def quantize(x: np.ndarray, w: int) -> tuple[np.ndarray, np.ndarray]:
+    """Sec. 5.8 quantization of float32 columns to w-bit codes; returns
+    (codes, lo_hi) with lo_hi[2 j] = min, lo_hi[2 j + 1] = max of column j."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    if x.ndim == 1:
+        x = x.reshape(-1, 1)
+    rows, D = x.shape
+    q = np.zeros((rows, D), dtype=np.uint8 if w == 8 else np.uint16)
+    lh = np.zeros(2 * D, dtype=np.float64)
+    rc = lib().spo_quantize(x.ctypes.data, rows, D, w, q.ctypes.data, lh.ctypes.data)
+    if rc != OK:
+        raise OracleError(rc, "quantize")
+    return q, lh
+
+
+def dequantize(q: np.ndarray, lo_hi: np.ndarray) -> np.ndarray:
+    q = np.ascontiguousarray(q)
+    rows, D = q.shape
+    w = 8 * q.itemsize
+    lh = np.ascontiguousarray(lo_hi, dtype=np.float64)
+    out = np.zeros((rows, D), dtype=np.float32)
+    rc = lib().spo_dequantize(q.ctypes.data, rows, D, w, lh.ctypes.data, out.ctypes.data)
+    if rc != OK:
+        raise OracleError(rc, "dequantize")
+    return out
+
+
+def quant_nmse(x: np.ndarray, q: np.ndarray, lo_hi: np.ndarray) -> np.ndarray:
+    """Per column: mean squared error of the reconstruction over the
+    column's variance (0 for a constant column)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    q = np.ascontiguousarray(q)
+    rows, D = x.shape
+    w = 8 * q.itemsize
+    lh = np.ascontiguousarray(lo_hi, dtype=np.float64)
+    out = np.zeros(D, dtype=np.float64)
+    rc = lib().spo_quant_nmse(x.ctypes.data, q.ctypes.data, rows, D, w, lh.ctypes.data, out.ctypes.data)
+    if rc != OK:
+        raise OracleError(rc, "quant_nmse")
     return out
 
 

@@ -24,6 +24,7 @@
  */
 #include "sprintz_oracle.h"
 
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -1056,6 +1057,80 @@ int spo_forecast_reconstruct(const int32_t *err_in, uint64_t rows, uint32_t D, u
   free(f);
   free(x);
   free(err);
+  return SPO_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Quantizing floats (Sec. 5.8)                                             */
+/* ------------------------------------------------------------------------ */
+
+static double quant_scale(double lo, double hi, uint32_t w) {
+  const double range = hi - lo;
+  return range > 0.0 ? (double)((1u << w) - 1u) / range : 0.0;
+}
+
+/* The inverse map's step: one code is (max - min) / (2^w - 1) in x. */
+static double quant_step(double lo, double hi, uint32_t w) { return (hi - lo) / (double)((1u << w) - 1u); }
+
+int spo_quantize(const float *src, uint64_t rows, uint32_t D, uint32_t w, void *codes, double *lo_hi) {
+  if ((w != 8 && w != 16) || D < 1) return SPO_ERR_INVALID_ARG;
+  uint8_t *out = (uint8_t *)codes;
+  for (uint32_t j = 0; j < D; ++j) {
+    /* the column's extremes */
+    double lo = 0.0, hi = 0.0;
+    for (uint64_t r = 0; r < rows; ++r) {
+      const double v = (double)src[r * D + j];
+      if (r == 0 || v < lo) lo = v;
+      if (r == 0 || v > hi) hi = v;
+    }
+    lo_hi[2 * j] = lo;
+    lo_hi[2 * j + 1] = hi;
+    /* linear map of [min, max] onto [0, 2^w - 1], then floor */
+    const double s = quant_scale(lo, hi, w);
+    const double top = (double)((1u << w) - 1u);
+    for (uint64_t r = 0; r < rows; ++r) {
+      const double t = ((double)src[r * D + j] - lo) * s;
+      double q = floor(t);
+      if (q > top) q = top;
+      if (q < 0.0) q = 0.0;
+      put_sample(out, r, j, D, w, (int64_t)q);
+    }
+  }
+  return SPO_OK;
+}
+
+int spo_dequantize(const void *codes, uint64_t rows, uint32_t D, uint32_t w, const double *lo_hi, float *dst) {
+  if ((w != 8 && w != 16) || D < 1) return SPO_ERR_INVALID_ARG;
+  const uint8_t *in = (const uint8_t *)codes;
+  for (uint32_t j = 0; j < D; ++j) {
+    const double lo = lo_hi[2 * j], h = quant_step(lo, lo_hi[2 * j + 1], w);
+    for (uint64_t r = 0; r < rows; ++r) {
+      const double q = (double)get_sample(in, r, j, D, w);
+      dst[r * D + j] = (float)(q * h + lo);
+    }
+  }
+  return SPO_OK;
+}
+
+int spo_quant_nmse(const float *src, const void *codes, uint64_t rows, uint32_t D, uint32_t w,
+                   const double *lo_hi, double *nmse) {
+  if ((w != 8 && w != 16) || D < 1 || rows == 0) return SPO_ERR_INVALID_ARG;
+  const uint8_t *in = (const uint8_t *)codes;
+  for (uint32_t j = 0; j < D; ++j) {
+    const double lo = lo_hi[2 * j], h = quant_step(lo, lo_hi[2 * j + 1], w);
+    double mean = 0.0;
+    for (uint64_t r = 0; r < rows; ++r) mean += (double)src[r * D + j];
+    mean /= (double)rows;
+    double var = 0.0, mse = 0.0;
+    for (uint64_t r = 0; r < rows; ++r) {
+      const double x = (double)src[r * D + j];
+      const double q = (double)get_sample(in, r, j, D, w);
+      const double xh = (double)(float)(q * h + lo);
+      var += (x - mean) * (x - mean);
+      mse += (x - xh) * (x - xh);
+    }
+    nmse[j] = var > 0.0 ? mse / var : 0.0;
+  }
   return SPO_OK;
 }
 

@@ -85,6 +85,25 @@ int spo_forecast_errors(const void *src, uint64_t rows, uint32_t D, uint32_t w,
 int spo_forecast_reconstruct(const int32_t *err_in, uint64_t rows, uint32_t D, uint32_t w,
                              int32_t forecaster, int32_t learn_shift, void *dst);
 
+/* Float data (Sec. 5.8): each column of `rows` x D float32 samples is
+ * offset and rescaled linearly so that its minimum and maximum map to 0 and
+ * 2^w - 1, then floored.  In double precision, each operation rounded on its
+ * own: s = (2^w - 1) / (max - min) (0 for a constant column), code =
+ * floor((x - min) * s), capped at 2^w - 1.  lo_hi receives min and max of
+ * each column (2 D doubles).  Codes are little-endian w-bit samples. */
+int spo_quantize(const float *src, uint64_t rows, uint32_t D, uint32_t w, void *codes, double *lo_hi);
+
+/* The inverse transform: x = (float)(code * h + min) with the step
+ * h = (max - min) / (2^w - 1), each operation rounded on its own. */
+int spo_dequantize(const void *codes, uint64_t rows, uint32_t D, uint32_t w, const double *lo_hi,
+                   float *dst);
+
+/* Per column: mean squared reconstruction error divided by the column's
+ * variance (population variance, two-pass), both in double; 0 for a
+ * constant column. */
+int spo_quant_nmse(const float *src, const void *codes, uint64_t rows, uint32_t D, uint32_t w,
+                   const double *lo_hi, double *nmse);
+
 /* FIRE per-block state trace: after each block k, alpha_k used in it and the
  * accumulator after its update (arrays of n_blocks x D). */
 int spo_fire_trace(const void *src, uint64_t rows, uint32_t D, uint32_t w,
