@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="sensor",
-                    choices=["sensor", "walk", "batch", "huffman", "serve", "fire_speed", "dsweep", "gsweep"])
+                    choices=["sensor", "walk", "batch", "huffman", "serve", "fire_speed", "dsweep", "gsweep",
+                             "quantize"])
     ap.add_argument("--streams", type=int, default=10_000, help="batch: number of streams")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     return ap.parse_args()

@@ -199,6 +199,33 @@ int sprintz_forecast(sprintz_ctx *ctx, const void *src, uint64_t rows, uint32_t 
                      uint32_t forecaster, uint32_t learn_shift, uint32_t chunk_rows, int inverse, void *dst,
                      void *stream);
 
+/* Float data (Sec. 5.8: quantize, then compress the integers).  Each column
+ * of a row-major rows x D float32 series (1 <= D <= 1024) is offset and
+ * rescaled linearly so that its minimum and maximum map to 0 and 2^w - 1,
+ * then floored: in double precision, every operation rounded on its own,
+ *   s = (2^w - 1) / (max - min)  (0 for a constant column),
+ *   code = min(floor((x - min) * s), 2^w - 1).
+ * The codes are rows x D little-endian w-bit samples, ready for
+ * sprintz_compress.  lo_hi (device, 2 D doubles) receives min and max of each
+ * column; the inverse needs it.  NaN inputs are not supported.  The
+ * workspace holds sprintz_quant_workspace_size(D) bytes (0 for a bad D). */
+uint64_t sprintz_quant_workspace_size(uint32_t D);
+int sprintz_quantize(sprintz_ctx *ctx, const float *src, uint64_t rows, uint32_t D, uint32_t w, void *codes,
+                     double *lo_hi, void *workspace, uint64_t ws_bytes, void *stream);
+
+/* The inverse map: x = (float)(code * h + min), h = (max - min) / (2^w - 1),
+ * each operation rounded on its own.  No workspace. */
+int sprintz_dequantize(sprintz_ctx *ctx, const void *codes, uint64_t rows, uint32_t D, uint32_t w,
+                       const double *lo_hi, float *dst, void *stream);
+
+/* The quantization error of Sec. 5.8, per column: the mean squared error of
+ * the reconstruction over the column's (population) variance, in double; 0
+ * for a constant column.  nmse: device, D doubles.  The sums are double
+ * atomics, so their rounding depends on the order of the additions. */
+int sprintz_quant_nmse(sprintz_ctx *ctx, const float *src, const void *codes, uint64_t rows, uint32_t D,
+                       uint32_t w, const double *lo_hi, double *nmse, void *workspace, uint64_t ws_bytes,
+                       void *stream);
+
 /* Parse a HOST copy of a stream's first n >= 64 bytes. */
 int sprintz_query(const void *host_header, uint64_t n, sprintz_info *out);
 

@@ -101,6 +101,8 @@ def run(args, metric, ClockSampler, peaks):
         run_fire_speed(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, synth, spz)
     elif args.workload == "dsweep":
         run_dsweep(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, synth, spz)
+    elif args.workload == "quantize":
+        run_quantize(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, synth, spz)
     elif args.workload == "gsweep":
         run_gsweep(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, synth, spz)
     codec.close()
@@ -357,4 +359,44 @@ def run_gsweep(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, sy
                             "chunk_rows": [256, 1024, 4096, 16384], "value_is": "decompress GB/s at G=2, CR=1024"},
                  "roofline": {"bound": "hbm", "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                               "frac": ref["hbm_frac_decode"], "traffic": None},
+                 "table": table, "clocks": clk.summary()})
+
+
+def run_quantize(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, synth, spz):
+    """Float data (Sec. 5.8): 2^24 x 8 float32 samples (the sensor recipe's
+    sinusoids plus noise, as floats) quantized to 8 and 16 bits, compressed
+    with FIRE, decompressed and mapped back. GB/s count the float bytes;
+    the normalized errors are the paper's quality measure."""
+    import torch
+    rows, D = 1 << 24, 8
+    x = (synth.sensor_u16_torch(rows, D, seed=1, device=dev).to(torch.int32) & 0xFFFF).to(torch.float32)
+    x = (x - 32768.0) / 8000.0 + 0.001 * torch.randn((rows, D), device=dev, generator=synth._tgen(9, dev))
+    F = x.numel() * 4
+    table = []
+    with ClockSampler(0) as clk:
+        for w in (8, 16):
+            q, lh = codec.quantize(x, w)
+            o = spz.Opts(forecaster=1)
+            dst, size = codec.compress(q, o)
+            torch.cuda.synchronize()
+            C = int(size.item())
+            info = spz.query(dst[:64].cpu().numpy().tobytes())
+            y = codec.decompress(dst, info, src_size=C).view(q.shape)
+            xr = codec.dequantize(y, lh)
+            nm = codec.quant_nmse(x, q, lh).cpu().numpy()
+            torch.cuda.synchronize()
+            tq = _time(lambda: codec.quantize(x, w), args.steps, stream)
+            td = _time(lambda: codec.dequantize(q, lh, out=xr), args.steps, stream)
+            table.append({"w": w, "quantize_gbs": F / (tq * 1e-3) / 1e9, "dequantize_gbs": F / (td * 1e-3) / 1e9,
+                          "quantize_ms": tq, "dequantize_ms": td, "ratio_vs_float": F / C,
+                          "nmse_max": float(nm.max()), "nmse_min": float(nm.min())})
+    r16 = table[1]
+    line.update({"metric": "float quantization GB/s (float bytes) and normalized MSE",
+                 "value": r16["quantize_gbs"], "dtype": "f32->u16",
+                 "config": {"workload": "float32_sensor_D8_2^24rows_quantize", "rows": rows, "D": D,
+                            "value_is": "quantize GB/s at w = 16"},
+                 "roofline": {"bound": "hbm", "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                              "frac": (F + F / 2) / (r16["quantize_ms"] * 1e-3) / 1e9 / peak,
+                              "bytes_per_launch": "float reads (twice: extremes, codes) + code writes",
+                              "traffic": None},
                  "table": table, "clocks": clk.summary()})

@@ -178,6 +178,46 @@ int sprintz_forecast(sprintz_ctx *ctx, const void *src, uint64_t rows, uint32_t 
                               inverse != 0, (uint8_t *)dst, (cudaStream_t)stream);
 }
 
+uint64_t sprintz_quant_workspace_size(uint32_t D) { return D >= 1 && D <= 1024 ? 32ull * D : 0; }
+
+static int quant_args(sprintz_ctx *ctx, uint64_t rows, uint32_t D, uint32_t w) {
+  if (!ctx) return SPRINTZ_ERR_INVALID_ARG;
+  if (w != 8 && w != 16) return SPRINTZ_ERR_UNSUPPORTED_W;
+  if (D < 1 || D > 1024 || rows > (1ull << 40)) return SPRINTZ_ERR_INVALID_ARG;
+  return SPRINTZ_OK;
+}
+
+int sprintz_quantize(sprintz_ctx *ctx, const float *src, uint64_t rows, uint32_t D, uint32_t w, void *codes,
+                     double *lo_hi, void *workspace, uint64_t ws_bytes, void *stream) {
+  int rc = quant_args(ctx, rows, D, w);
+  if (rc != SPRINTZ_OK) return rc;
+  if (!rows) return SPRINTZ_OK;
+  if (!src || !codes || !lo_hi || !workspace) return SPRINTZ_ERR_INVALID_ARG;
+  if (ws_bytes < sprintz_quant_workspace_size(D)) return SPRINTZ_ERR_WS_TOO_SMALL;
+  return spz::launch_quantize(ctx->cfg, src, rows, D, w, (uint8_t *)codes, lo_hi, (uint8_t *)workspace,
+                              (cudaStream_t)stream);
+}
+
+int sprintz_dequantize(sprintz_ctx *ctx, const void *codes, uint64_t rows, uint32_t D, uint32_t w,
+                       const double *lo_hi, float *dst, void *stream) {
+  int rc = quant_args(ctx, rows, D, w);
+  if (rc != SPRINTZ_OK) return rc;
+  if (!rows) return SPRINTZ_OK;
+  if (!codes || !lo_hi || !dst) return SPRINTZ_ERR_INVALID_ARG;
+  return spz::launch_dequantize(ctx->cfg, (const uint8_t *)codes, rows, D, w, lo_hi, dst, (cudaStream_t)stream);
+}
+
+int sprintz_quant_nmse(sprintz_ctx *ctx, const float *src, const void *codes, uint64_t rows, uint32_t D,
+                       uint32_t w, const double *lo_hi, double *nmse, void *workspace, uint64_t ws_bytes,
+                       void *stream) {
+  int rc = quant_args(ctx, rows, D, w);
+  if (rc != SPRINTZ_OK) return rc;
+  if (!rows || !src || !codes || !lo_hi || !nmse || !workspace) return SPRINTZ_ERR_INVALID_ARG;
+  if (ws_bytes < sprintz_quant_workspace_size(D)) return SPRINTZ_ERR_WS_TOO_SMALL;
+  return spz::launch_quant_nmse(ctx->cfg, src, (const uint8_t *)codes, rows, D, w, lo_hi, nmse,
+                                (uint8_t *)workspace, (cudaStream_t)stream);
+}
+
 int sprintz_query(const void *host_header, uint64_t n, sprintz_info *out) {
   if (!host_header || !out) return SPRINTZ_ERR_INVALID_ARG;
   const uint8_t *h = (const uint8_t *)host_header;

@@ -241,6 +241,14 @@ struct LaunchCfg {
 
 int make_geom(uint64_t rows, uint32_t D, uint32_t w, const sprintz_opts *o, Geom *g);
 
+// Float quantization (spz_quant.cu).
+int launch_quantize(const LaunchCfg &cfg, const float *x, uint64_t rows, uint32_t D, uint32_t w, uint8_t *codes,
+                    double *lo_hi, uint8_t *ws, cudaStream_t stream);
+int launch_dequantize(const LaunchCfg &cfg, const uint8_t *codes, uint64_t rows, uint32_t D, uint32_t w,
+                      const double *lo_hi, float *y, cudaStream_t stream);
+int launch_quant_nmse(const LaunchCfg &cfg, const float *x, const uint8_t *codes, uint64_t rows, uint32_t D,
+                      uint32_t w, const double *lo_hi, double *nmse, uint8_t *ws, cudaStream_t stream);
+
 // Forecast transform alone (spz_forecast.cu).
 int launch_forecast(const LaunchCfg &cfg, const uint8_t *src, uint64_t rows, uint32_t D, uint32_t w,
                     uint32_t forecaster, uint32_t learn_shift, uint32_t chunk_rows, bool inverse, uint8_t *dst,

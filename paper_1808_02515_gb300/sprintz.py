@@ -108,6 +108,14 @@ def lib() -> ctypes.CDLL:
         L.sprintz_batch_run.argtypes = [vp, vp, u64, vp]
         L.sprintz_forecast.restype = i32
         L.sprintz_forecast.argtypes = [vp, vp, u64, u32, u32, u32, u32, u32, i32, vp, vp]
+        L.sprintz_quant_workspace_size.restype = u64
+        L.sprintz_quant_workspace_size.argtypes = [u32]
+        L.sprintz_quantize.restype = i32
+        L.sprintz_quantize.argtypes = [vp, vp, u64, u32, u32, vp, vp, vp, u64, vp]
+        L.sprintz_dequantize.restype = i32
+        L.sprintz_dequantize.argtypes = [vp, vp, u64, u32, u32, vp, vp, vp]
+        L.sprintz_quant_nmse.restype = i32
+        L.sprintz_quant_nmse.argtypes = [vp, vp, vp, u64, u32, u32, vp, vp, vp, u64, vp]
         L.sprintz_query.restype = i32
         L.sprintz_query.argtypes = [vp, u64, PI]
         L.sprintz_get_status.restype = i32
@@ -251,6 +259,54 @@ class Codec:
                                     ctypes.c_void_p(y.data_ptr() if rows else 0), self._stream(stream))
         _check(rc, "sprintz_forecast")
         return y
+
+    def quantize(self, x, w: int = 16, stream=None):
+        """Float quantization (sprintz_quantize) of a (rows, D) float32 CUDA
+        tensor: returns (codes, lo_hi), codes uint8 (w = 8) or int16 holding
+        the 16-bit codes, lo_hi a (D, 2) float64 tensor of column min/max."""
+        torch = self.torch
+        if x.dim() == 1:
+            x = x.view(-1, 1)
+        x = x.contiguous()
+        if x.dtype != torch.float32:
+            raise TypeError("float32 samples expected")
+        rows, D = x.shape
+        codes = torch.empty((rows, D), dtype=torch.uint8 if w == 8 else torch.int16, device=x.device)
+        lo_hi = torch.empty((D, 2), dtype=torch.float64, device=x.device)
+        wsn = int(lib().sprintz_quant_workspace_size(D))
+        ws = torch.empty(max(wsn, 1), dtype=torch.uint8, device=x.device)
+        rc = lib().sprintz_quantize(self.ctx, ctypes.c_void_p(x.data_ptr()), rows, D, w,
+                                    ctypes.c_void_p(codes.data_ptr()), ctypes.c_void_p(lo_hi.data_ptr()),
+                                    ctypes.c_void_p(ws.data_ptr()), wsn, self._stream(stream))
+        _check(rc, "sprintz_quantize")
+        self._keep = ws
+        return codes, lo_hi
+
+    def dequantize(self, codes, lo_hi, out=None, stream=None):
+        torch = self.torch
+        rows, D = codes.shape
+        w = 8 if codes.dtype == torch.uint8 else 16
+        y = torch.empty((rows, D), dtype=torch.float32, device=codes.device) if out is None else out
+        rc = lib().sprintz_dequantize(self.ctx, ctypes.c_void_p(codes.data_ptr()), rows, D, w,
+                                      ctypes.c_void_p(lo_hi.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                      self._stream(stream))
+        _check(rc, "sprintz_dequantize")
+        return y
+
+    def quant_nmse(self, x, codes, lo_hi, stream=None):
+        """Per column: reconstruction MSE over variance (a (D,) float64 tensor)."""
+        torch = self.torch
+        rows, D = codes.shape
+        w = 8 if codes.dtype == torch.uint8 else 16
+        out = torch.empty(D, dtype=torch.float64, device=codes.device)
+        wsn = int(lib().sprintz_quant_workspace_size(D))
+        ws = torch.empty(max(wsn, 1), dtype=torch.uint8, device=codes.device)
+        rc = lib().sprintz_quant_nmse(self.ctx, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(codes.data_ptr()),
+                                      rows, D, w, ctypes.c_void_p(lo_hi.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                      ctypes.c_void_p(ws.data_ptr()), wsn, self._stream(stream))
+        _check(rc, "sprintz_quant_nmse")
+        self._keep = ws
+        return out
 
     def compress(self, x, opts: Opts = Opts(), stream=None):
         """Compress a (rows, D) uint8 / uint16 (or int16) CUDA tensor.

@@ -92,3 +92,10 @@ def test_null_arguments_rejected_without_gpu(spz):
     rc = L.sprintz_decompress(None, None, 0, None, None, 0, None, 0, None)
     assert rc == spz.ERR_INVALID_ARG
     assert L.sprintz_get_status(None, None) == spz.ERR_INVALID_ARG
+
+
+def test_quant_workspace_size(spz):
+    L = spz.lib()
+    assert L.sprintz_quant_workspace_size(0) == 0
+    assert L.sprintz_quant_workspace_size(1025) == 0
+    assert L.sprintz_quant_workspace_size(8) == 256
