@@ -10,7 +10,7 @@
 //   k_quant_minmax   per-column extremes: a grid-stride pass keeps each
 //                    thread's running min/max, a CTA reduction per column,
 //                    then one atomic per column on an order-preserving
-//                    integer image of the double (exact, order independent)
+//                    integer image of the float (exact, order independent)
 //   k_quant_codes    code = min(floor((x - min) * s), 2^w - 1), s per column
 //   k_dequant        x = (float)(code * h + min)
 //   k_quant_err      per column sum of x, then squared deviations and
@@ -24,14 +24,15 @@ namespace spz {
 
 constexpr int kQThreads = 256;
 
-// Order-preserving map of a double onto uint64 (and back).
-__device__ __forceinline__ unsigned long long dbl_key(double v) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+// Order-preserving map of a float onto uint32 (and back).  float -> double
+// is exact and monotone, so the extremes are found on the floats.
+__device__ __forceinline__ uint32_t flt_key(float v) {
+  const uint32_t b = __float_as_uint(v);
+  return (b >> 31) ? ~b : (b | 0x80000000u);
 }
-__device__ __forceinline__ double key_dbl(unsigned long long k) {
-  const unsigned long long b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
-  return __longlong_as_double((long long)b);
+__device__ __forceinline__ float key_flt(uint32_t k) {
+  const uint32_t b = (k >> 31) ? (k & 0x7FFFFFFFu) : ~k;
+  return __uint_as_float(b);
 }
 
 // Threads of a CTA cover (column, row-lane) pairs: column j = t % D for
@@ -47,17 +48,17 @@ __device__ __forceinline__ QMap qmap(uint32_t D) {
 }
 
 __global__ void __launch_bounds__(kQThreads) k_quant_minmax(const float *x, uint64_t rows, uint32_t D,
-                                                           unsigned long long *keys /* 2 D */) {
-  __shared__ unsigned long long s_lo[kQThreads], s_hi[kQThreads];
+                                                           uint32_t *keys /* 2 D */) {
+  __shared__ uint32_t s_lo[kQThreads], s_hi[kQThreads];
   const QMap m = qmap(D);
   for (uint32_t j0 = 0; j0 < D; j0 += kQThreads / m.lanes) {
     const uint32_t t = threadIdx.x, lane = t / min(D, (uint32_t)kQThreads), jj = t % min(D, (uint32_t)kQThreads);
     const uint32_t j = j0 + jj;
     const bool act = lane < m.lanes && j < D;
-    unsigned long long lo = ~0ull, hi = 0ull;
+    uint32_t lo = ~0u, hi = 0u;
     if (act)
       for (uint64_t r = (uint64_t)blockIdx.x * m.lanes + lane; r < rows; r += (uint64_t)gridDim.x * m.lanes) {
-        const unsigned long long k = dbl_key((double)x[r * D + j]);
+        const uint32_t k = flt_key(x[r * D + j]);
         lo = min(lo, k);
         hi = max(hi, k);
       }
@@ -76,10 +77,10 @@ __global__ void __launch_bounds__(kQThreads) k_quant_minmax(const float *x, uint
   }
 }
 
-__global__ void k_quant_finish_minmax(const unsigned long long *keys, uint32_t D, double *lo_hi) {
+__global__ void k_quant_finish_minmax(const uint32_t *keys, uint32_t D, double *lo_hi) {
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < D; j += gridDim.x * blockDim.x) {
-    lo_hi[2 * j] = key_dbl(keys[2 * j]);
-    lo_hi[2 * j + 1] = key_dbl(keys[2 * j + 1]);
+    lo_hi[2 * j] = (double)key_flt(keys[2 * j]);
+    lo_hi[2 * j + 1] = (double)key_flt(keys[2 * j + 1]);
   }
 }
 
@@ -101,8 +102,10 @@ __global__ void __launch_bounds__(kQThreads) k_quant_codes(const float *x, uint6
   extern __shared__ double s_scale[];
   constexpr double kTop = (double)((1u << W) - 1u);
   column_consts<W>(lo_hi, D, s_scale, false);
-  for (uint64_t i = (uint64_t)blockIdx.x * kQThreads + threadIdx.x; i < n; i += (uint64_t)gridDim.x * kQThreads) {
-    const uint32_t j = (uint32_t)(i % D);
+  const uint64_t step = (uint64_t)gridDim.x * kQThreads;
+  const uint32_t jstep = (uint32_t)(step % D);
+  uint64_t i = (uint64_t)blockIdx.x * kQThreads + threadIdx.x;
+  for (uint32_t j = (uint32_t)(i % D); i < n; i += step, j = j + jstep >= D ? j + jstep - D : j + jstep) {
     double q = floor(__dmul_rn(__dsub_rn((double)x[i], lo_hi[2 * j]), s_scale[j]));
     q = q > kTop ? kTop : (q < 0.0 ? 0.0 : q);
     if (W == 8)
@@ -117,8 +120,10 @@ __global__ void __launch_bounds__(kQThreads) k_dequant(const uint8_t *codes, uin
                                                       const double *lo_hi, float *y) {
   extern __shared__ double s_step[];
   column_consts<W>(lo_hi, D, s_step, true);
-  for (uint64_t i = (uint64_t)blockIdx.x * kQThreads + threadIdx.x; i < n; i += (uint64_t)gridDim.x * kQThreads) {
-    const uint32_t j = (uint32_t)(i % D);
+  const uint64_t step = (uint64_t)gridDim.x * kQThreads;
+  const uint32_t jstep = (uint32_t)(step % D);
+  uint64_t i = (uint64_t)blockIdx.x * kQThreads + threadIdx.x;
+  for (uint32_t j = (uint32_t)(i % D); i < n; i += step, j = j + jstep >= D ? j + jstep - D : j + jstep) {
     const double lo = lo_hi[2 * j], h = s_step[j];
     const double q = W == 8 ? (double)codes[i] : (double)reinterpret_cast<const uint16_t *>(codes)[i];
     y[i] = __double2float_rn(__dadd_rn(__dmul_rn(q, h), lo));
@@ -189,10 +194,10 @@ static uint32_t q_grid(const LaunchCfg &cfg, uint64_t work) {
 
 int launch_quantize(const LaunchCfg &cfg, const float *x, uint64_t rows, uint32_t D, uint32_t w, uint8_t *codes,
                     double *lo_hi, uint8_t *ws, cudaStream_t stream) {
-  unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws);
+  uint32_t *keys = reinterpret_cast<uint32_t *>(ws);
   // keys start at (lo = all ones, hi = zero): an empty min and max
-  if (cudaMemsetAsync(keys, 0, 16ull * D, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
-  if (cudaMemset2DAsync(keys, 16, 0xFF, 8, D, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  if (cudaMemsetAsync(keys, 0, 8ull * D, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  if (cudaMemset2DAsync(keys, 8, 0xFF, 4, D, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
   k_quant_minmax<<<q_grid(cfg, rows), kQThreads, 0, stream>>>(x, rows, D, keys);
   k_quant_finish_minmax<<<(D + 255) / 256, 256, 0, stream>>>(keys, D, lo_hi);
   const uint64_t n = rows * D;
