@@ -40,8 +40,8 @@ ROWS, COLS, SEED = 1 << 24, 8, 1
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rows", type=int, default=ROWS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -69,7 +69,9 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
+    """nvidia-smi clock/throttle sampling (every 50 ms). Each sample is stamped
+    on arrival; mark(start, end) keeps only the samples inside the timed
+    region when it held any (else all samples are kept)."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -78,36 +80,75 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.lines = []
+        self.window = None
+
+    def _reader(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.monotonic(), line.strip()))
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._reader, daemon=True)
+            self.thread.start()
         except Exception:
             self.proc = None
         return self
 
     def __exit__(self, *a):
-        self.out = ""
         if self.proc:
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def mark(self, t0: float, t1: float):
+        self.window = (t0, t1)
 
     def summary(self):
-        rows = [r.split(", ") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
-        if not rows:
+        rows = [(t, r.split(", ")) for t, r in self.lines if r.count(",") >= 8]
+        inside = [r for t, r in rows if self.window and self.window[0] <= t <= self.window[1]]
+        sel = inside if inside else [r for _, r in rows]
+        if not sel:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[1]) for r in sel if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in sel if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        reasons = sorted({names[k] for r in sel for k in range(4) if r[5 + k].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(sel),
+                "samples_in_timed_region": len(inside)}
+
+
+def traffic_bytes(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/traffic.json), or None when the kernel sources changed since
+    the counters were taken."""
+    import hashlib
+    root = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(root, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    csrc = os.path.join(root, "paper_1808_02515_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    if rec.get("sources_sha256") != h.hexdigest():
+        return None
+    k = rec.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch")
 
 
 def run_reference(args, rank, world):
@@ -205,25 +246,31 @@ def main():
         if ev is not None:
             ev[2].record(stream)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    codec.check()
-    if not torch.equal(out, xd):
-        raise SystemExit("round trip mismatch")
-
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        # keep the GPU busy until the clock sampler delivers (at most 2 s)
+        t_w = time.monotonic()
+        while not clk.lines and time.monotonic() - t_w < 2.0:
+            step()
+            torch.cuda.synchronize()
+        codec.check()
+        if not torch.equal(out, xd):
+            raise SystemExit("round trip mismatch")
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        h0 = time.monotonic()
         t_start.record(stream)
         for k in range(args.steps):
             step(evs[k])
         t_end.record(stream)
         torch.cuda.synchronize()
+        clk.mark(h0, time.monotonic())
     if dist:
         dist.barrier()
     total_ms = t_start.elapsed_time(t_end)
@@ -273,6 +320,7 @@ def main():
     table = 16 * info.n_chunks
     enc_bytes, dec_bytes = U + C + table, C + U
     dom = "decode" if dec_avg >= enc_avg else "encode"
+    dom_kernel = "k_decode_lanes" if dom == "decode" else "k_encode_slots"
     dom_ms = dec_avg if dom == "decode" else enc_avg
     dom_bytes = dec_bytes if dom == "decode" else enc_bytes
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
@@ -289,9 +337,9 @@ def main():
         "decompress_gbs": U / (dec_avg * 1e-3) / 1e9,
         "compress_gbs": U / (enc_avg * 1e-3) / 1e9,
         "decompress_ms": dec_avg, "compress_ms": enc_avg,
-        "roofline": {"bound": "hbm", "kernel": "k_decode" if dom == "decode" else "k_encode",
+        "roofline": {"bound": "hbm", "kernel": dom_kernel,
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic_bytes(dom_kernel),
                      "algorithmic_bytes_per_launch": dom_bytes,
                      "decode_frac": dec_bytes / (dec_avg * 1e-3) / 1e9 / peak,
                      "encode_frac": enc_bytes / (enc_avg * 1e-3) / 1e9 / peak},

@@ -1483,10 +1483,7 @@ static SlotPlan slot_plan(const Geom &g, const LaunchCfg &cfg) {
   return pl;
 }
 
-uint64_t encode_workspace_bytes(const Geom &g, const LaunchCfg &cfg) {
-  const SlotPlan sp = slot_plan(g, cfg);
-  return std::max<uint64_t>(encode_workspace_basic(g, cfg), sp.grid ? sp.ws_total : 0ull);
-}
+
 
 int launch_encode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint8_t *dst,
                   uint64_t dst_cap, uint64_t *d_out_size, uint8_t *ws, uint64_t ws_bytes,
@@ -1550,9 +1547,327 @@ namespace spz {
 
 // Compression through the fastest applicable encoder: the single-pass slot
 // encoder when the workspace holds its slots, else launch_encode's choice.
+// ---------------------------------------------------------------------------
+// Column-per-thread encoder for wide rows (32 < D <= 1024)
+//
+// Persistent CTAs take chunks in order from a ticket; thread j owns column j.
+// Per block: the column's 8 samples (the threads of a row read consecutive
+// samples), its forecast errors, zigzag and width; a block-wide scan of the
+// widths gives each thread its bit offset in a row and the record's size.
+// Header codes and row fields are OR-ed into a shared ring (rows are
+// row-major: D * w > 32); completed 32-byte sectors go to the CTA's slot in
+// the workspace.  At the chunk's end the look-back over chunks gives its
+// offset and the CTA copies the slot to its place in the stream.
+// ---------------------------------------------------------------------------
+
+struct EncWideCfg {
+  uint32_t window;       // ring bytes (power of two)
+  uint32_t slot_stride;  // bytes per CTA slot (multiple of 32)
+  uint8_t *slots;
+};
+
+template <int W>
+__global__ void __launch_bounds__(1024) k_encode_wide(EncParams p, EncWideCfg cfg) {
+  extern __shared__ __align__(16) uint8_t wsm_[];
+  __shared__ uint32_t s_wsum[2][32];
+  __shared__ uint32_t s_grp;
+  __shared__ uint64_t s_prefix;
+  const Geom &g = p.g;
+  const uint32_t D = g.D, j = threadIdx.x, lane = j & 31, warp = j >> 5, nwarps = blockDim.x >> 5;
+  const bool col = j < D;
+  constexpr uint32_t wb = W / 8;
+  constexpr uint32_t HB = W == 8 ? 3u : 4u;
+  const uint32_t G = g.G, H = g.hdr_bytes;
+  uint32_t *ring = reinterpret_cast<uint32_t *>(wsm_);
+  const uint32_t ring_wmask = cfg.window / 4 - 1;
+  uint8_t *slot = cfg.slots + (uint64_t)blockIdx.x * cfg.slot_stride;
+  auto ror = [&](uint32_t bit, uint32_t v, uint32_t n) {
+    if (!v) return;
+    const uint32_t wi = (bit >> 5) & ring_wmask, sh = bit & 31;
+    atomicOr(&ring[wi], v << sh);
+    if (sh + n > 32) atomicOr(&ring[(wi + 1) & ring_wmask], v >> (32 - sh));
+  };
+  uint32_t par = 0;
+  for (;;) {
+    __syncthreads();
+    if (j == 0) s_grp = atomicAdd(p.ticket, 1u);
+    for (uint32_t t = j; t < cfg.window / 16; t += blockDim.x) reinterpret_cast<uint4 *>(ring)[t] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    const uint32_t c = s_grp;
+    if (c >= g.n_chunks) break;
+    const uint64_t row0 = (uint64_t)c * g.chunk_rows;
+    const uint32_t nb = (uint32_t)(min((uint64_t)g.chunk_rows, g.full_rows - row0) / kBlockRows);
+    const uint8_t *xs = p.src + row0 * D * wb + j * wb;
+    const uint32_t row_stride = D * wb;
+    uint32_t xp = 0, run = 0, nrec = 0, gs = 0, pos = 0, hpos = 0, flushed = 0;
+    int32_t dp = 0, acc = 0;
+    bool open = false;
+    auto start_record = [&]() {
+      if (gs == 0) {
+        hpos = pos;
+        pos += H;
+        open = true;
+      }
+    };
+    auto end_record = [&](uint32_t size) {
+      pos += size;
+      nrec++;
+      if (++gs == G) {
+        gs = 0;
+        open = false;
+      }
+    };
+    auto emit_run = [&](uint32_t len) {
+      start_record();
+      if (j == 0) ror(pos * 8, len, 16);
+      end_record(2);
+    };
+    // completed bytes to the slot in whole 32-byte sectors (a final partial
+    // 16-byte unit at the chunk's end)
+    auto flush = [&](uint32_t limit, bool fin) {
+      __syncthreads();
+      const uint32_t u1 = fin ? (limit + 15) >> 4 : (limit >> 5) << 1;
+      for (uint32_t u = (flushed >> 4) + j; u < u1; u += blockDim.x) {
+        uint4 *r4 = reinterpret_cast<uint4 *>(&ring[(u * 4) & ring_wmask]);
+        *reinterpret_cast<uint4 *>(slot + 16ull * u) = *r4;
+        *r4 = make_uint4(0, 0, 0, 0);
+      }
+      if (u1 * 16 > flushed) flushed = u1 * 16;
+      __syncthreads();
+    };
+    uint32_t xn[kBlockRows];
+#pragma unroll
+    for (int i = 0; i < kBlockRows; ++i)
+      xn[i] = col && nb ? (W == 8 ? (uint32_t)xs[i * row_stride]
+                                  : (uint32_t)*reinterpret_cast<const uint16_t *>(xs + i * row_stride))
+                        : 0u;
+    for (uint32_t b = 0; b < nb; ++b) {
+      uint32_t x[kBlockRows];
+#pragma unroll
+      for (int i = 0; i < kBlockRows; ++i) x[i] = xn[i];
+      if (b + 1 < nb && col) {
+        const uint8_t *q = xs + (uint64_t)(b + 1) * kBlockRows * row_stride;
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i)
+          xn[i] = W == 8 ? (uint32_t)q[i * row_stride] : (uint32_t)*reinterpret_cast<const uint16_t *>(q + i * row_stride);
+      }
+      uint32_t z[kBlockRows];
+      uint32_t orz = 0;
+      if (g.forecaster == kFcDelta) {
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) {
+          z[i] = zigzag<W>(sext<W>(x[i] - xp));
+          xp = x[i];
+          orz |= z[i];
+        }
+      } else if (g.forecaster == kFcDDelta) {
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) {
+          z[i] = zigzag<W>(sext<W>(x[i] - xp - (uint32_t)dp));
+          orz |= z[i];
+          dp = sext<W>(x[i] - xp);
+          xp = x[i];
+        }
+      } else if (g.forecaster == kFcFireSample) {
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) {
+          const int32_t e = sext<W>(x[i] - xp - fire_pred_delta<W>(acc >> g.learn_shift, dp));
+          acc = wrap_acc<W>((int32_t)((uint32_t)acc + (uint32_t)(sign_of(e) * dp)));
+          z[i] = zigzag<W>(e);
+          orz |= z[i];
+          dp = sext<W>(x[i] - xp);
+          xp = x[i];
+        }
+      } else {
+        const int32_t a = acc >> g.learn_shift;
+        int32_t gsum = 0;
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) {
+          const int32_t e = sext<W>(x[i] - xp - fire_pred_delta<W>(a, dp));
+          if ((i & 1) == 0) gsum += sign_of(e) * dp;
+          z[i] = zigzag<W>(e);
+          orz |= z[i];
+          dp = sext<W>(x[i] - xp);
+          xp = x[i];
+        }
+        acc = wrap_acc<W>((int32_t)((uint32_t)acc + (uint32_t)(gsum >> 2)));
+      }
+      uint32_t n = 32u - __clz(orz);
+      if (n == W - 1) n = W;
+      if (!col) n = 0;
+      // block-wide exclusive scan of the widths
+      uint32_t v = n;
+#pragma unroll
+      for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        if (lane >= o) v += t;
+      }
+      if (lane == 31) s_wsum[par][warp] = v;
+      __syncthreads();
+      if (warp == 0) {
+        uint32_t t = lane < nwarps ? s_wsum[par][lane] : 0u;
+#pragma unroll
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+          const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, t, o);
+          if (lane >= o) t += u;
+        }
+        if (lane < nwarps) s_wsum[par][lane] = t;
+      }
+      __syncthreads();
+      const uint32_t prefix = v - n + (warp ? s_wsum[par][warp - 1] : 0u);
+      const uint32_t total = s_wsum[par][nwarps - 1];
+      par ^= 1;
+      if (total == 0) {
+        if (++run == kMaxRun) {
+          emit_run(run);
+          run = 0;
+        }
+      } else {
+        if (run) {
+          emit_run(run);
+          run = 0;
+        }
+        start_record();
+        const uint32_t size = (total + 7) & ~7u;  // bits per row (row-major)
+        if (col) {
+          ror(hpos * 8 + (gs * D + j) * HB, n == W ? W - 1 : n, HB);
+          if (n) {
+            const uint32_t b0 = pos * 8 + prefix;
+#pragma unroll
+            for (int i = 0; i < kBlockRows; ++i) ror(b0 + i * size, z[i], n);
+          }
+        }
+        end_record(size);
+      }
+      flush(open ? hpos : pos, false);
+    }
+    if (run) emit_run(run);
+    open = false;
+    flush(pos, true);
+    const uint32_t S = pos;
+
+    // offset of the body: look-back over chunks (warp 0), then the copy
+    if (warp == 0) {
+      const uint64_t pre = lookback_warp(p.lookback, c, S, p.status);
+      if (lane == 0) s_prefix = pre;
+    }
+    __syncthreads();
+    const uint64_t off = s_prefix;
+    if (g.data_off + off + S <= p.dst_cap) {
+      uint8_t *d = p.dst + g.data_off + off;
+      const uint32_t head = min((uint32_t)((16 - ((uintptr_t)d & 15)) & 15), S);
+      for (uint32_t k = j; k < head; k += blockDim.x) d[k] = slot[k];
+      const uint32_t n16 = (S - head) / 16;
+      const uint32_t sh = (head & 3) * 8;
+      const bool w1 = head & 4, w2 = head & 8;
+      const uint4 *s4 = reinterpret_cast<const uint4 *>(slot);
+      for (uint32_t u = j; u < n16; u += blockDim.x) {
+        const uint4 A = s4[u], B = s4[u + 1];
+        const uint32_t p0 = w2 ? A.z : A.x, p1 = w2 ? A.w : A.y, p2 = w2 ? B.x : A.z, p3 = w2 ? B.y : A.w;
+        const uint32_t p4 = w2 ? B.z : B.x, p5 = w2 ? B.w : B.y;
+        const uint32_t a0 = w1 ? p1 : p0, a1 = w1 ? p2 : p1, a2 = w1 ? p3 : p2, a3 = w1 ? p4 : p3,
+                       a4 = w1 ? p5 : p4;
+        uint4 o;
+        o.x = __funnelshift_r(a0, a1, sh);
+        o.y = __funnelshift_r(a1, a2, sh);
+        o.z = __funnelshift_r(a2, a3, sh);
+        o.w = __funnelshift_r(a3, a4, sh);
+        *reinterpret_cast<uint4 *>(d + head + 16 * u) = o;
+      }
+      for (uint32_t k = head + 16 * n16 + j; k < S; k += blockDim.x) d[k] = slot[k];
+      if (j == 0) {
+        uint8_t *e = p.dst + kHdrBytes + (uint64_t)c * kEntryBytes;
+        const uint64_t w1v = (uint64_t)nrec | ((uint64_t)S << 32);
+        for (int k = 0; k < 8; ++k) {
+          e[k] = (uint8_t)(off >> (8 * k));
+          e[8 + k] = (uint8_t)(w1v >> (8 * k));
+        }
+      }
+      if (c == g.n_chunks - 1) {
+        const uint64_t tail_off = g.data_off + off + S;
+        const uint64_t tail_bytes = g.tail_rows * D * wb;
+        const uint64_t tot = tail_off + tail_bytes;
+        if (tot <= p.dst_cap) {
+          for (uint64_t k = j; k < tail_bytes; k += blockDim.x) p.dst[tail_off + k] = p.src[g.full_rows * D * wb + k];
+          if (j == 0) {
+            write_stream_header(p.dst, g, tail_off, tot);
+            *p.out_size = tot;
+          }
+        } else if (j == 0) {
+          set_status(p.status, SPRINTZ_ERR_DST_TOO_SMALL);
+        }
+      }
+    } else if (j == 0) {
+      set_status(p.status, SPRINTZ_ERR_DST_TOO_SMALL);
+    }
+  }
+}
+
+struct WidePlan {
+  EncWideCfg wc;
+  uint32_t grid, threads;
+  uint64_t smem, ws_base, ws_total;
+};
+
+static WidePlan wide_plan(const Geom &g, const LaunchCfg &cfg) {
+  WidePlan pl{};
+  if (g.n_chunks == 0 || g.D <= 32 || g.D > 1024 || g.max_body >= (1ull << 31)) return pl;
+  pl.wc.window = enc_window_bytes(g);
+  pl.smem = pl.wc.window;
+  if (pl.smem > (uint64_t)cfg.max_smem_optin - 1024) return pl;
+  pl.threads = (g.D + 31) & ~31u;
+  pl.wc.slot_stride = (uint32_t)(((g.max_body + 31) & ~31ull) + 32);
+  // persistent CTAs: up to 2048 / threads per SM, with the slots' total kept
+  // below 1 GiB
+  const uint64_t per_sm = std::max<uint64_t>(1, 2048 / pl.threads);
+  uint64_t grid = std::min<uint64_t>(g.n_chunks, (uint64_t)cfg.sm_count * per_sm);
+  while (grid > (uint64_t)cfg.sm_count && grid * pl.wc.slot_stride > (1ull << 30)) grid /= 2;
+  pl.grid = (uint32_t)std::max<uint64_t>(1, grid);
+  pl.ws_base = align256(16 + 8ull * g.n_chunks);
+  pl.ws_total = pl.ws_base + (uint64_t)pl.grid * pl.wc.slot_stride;
+  return pl;
+}
+
+static int launch_encode_wide(const Geom &g, const LaunchCfg &cfg, const WidePlan &pl, const uint8_t *src,
+                              uint8_t *dst, uint64_t dst_cap, uint64_t *d_out_size, uint8_t *ws, int *d_status,
+                              cudaStream_t stream) {
+  EncParams p{};
+  p.src = src;
+  p.dst = dst;
+  p.dst_cap = dst_cap;
+  p.out_size = d_out_size;
+  p.status = d_status;
+  p.g = g;
+  p.ticket = reinterpret_cast<uint32_t *>(ws);
+  p.lookback = reinterpret_cast<uint64_t *>(ws + 16);
+  EncWideCfg wc = pl.wc;
+  wc.slots = ws + pl.ws_base;
+  const void *fn = g.w == 8 ? (const void *)k_encode_wide<8> : (const void *)k_encode_wide<16>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem) != cudaSuccess)
+    return SPRINTZ_ERR_CUDA;
+  if (cudaMemsetAsync(ws, 0, 16 + 8ull * g.n_chunks, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  void *args[] = {&p, &wc};
+  if (cudaLaunchKernel(fn, dim3(pl.grid), dim3(pl.threads), args, pl.smem, stream) != cudaSuccess)
+    return SPRINTZ_ERR_CUDA;
+  return SPRINTZ_OK;
+}
+
+uint64_t encode_workspace_bytes(const Geom &g, const LaunchCfg &cfg) {
+  const SlotPlan sp = slot_plan(g, cfg);
+  const WidePlan wp = wide_plan(g, cfg);
+  return std::max<uint64_t>(std::max<uint64_t>(encode_workspace_basic(g, cfg), sp.grid ? sp.ws_total : 0ull),
+                            wp.grid ? wp.ws_total : 0ull);
+}
+
 int launch_encode_fast(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint8_t *dst,
                        uint64_t dst_cap, uint64_t *d_out_size, uint8_t *ws, uint64_t ws_bytes,
                        int *d_status, cudaStream_t stream) {
+  if (g.D > 32) {
+    const WidePlan wp = wide_plan(g, cfg);
+    if (wp.grid && ws_bytes >= wp.ws_total)
+      return launch_encode_wide(g, cfg, wp, src, dst, dst_cap, d_out_size, ws, d_status, stream);
+    return launch_encode(g, cfg, src, dst, dst_cap, d_out_size, ws, ws_bytes, d_status, stream);
+  }
   const SlotPlan sp = slot_plan(g, cfg);
   if (!sp.grid || ((uintptr_t)src & 7) != 0 || ws_bytes < sp.ws_total)
     return launch_encode(g, cfg, src, dst, dst_cap, d_out_size, ws, ws_bytes, d_status, stream);
