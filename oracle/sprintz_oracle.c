@@ -545,7 +545,7 @@ int spo_huff_code_lengths(const uint64_t freq[256], uint32_t max_len, uint8_t le
   return SPO_OK;
 }
 
-/* Canonical codes as in RFC 1951 Sec. 4.2.2: shorter codes first, and within
+/* Canonical codes as in RFC 1951 Sec. 3.2.2: shorter codes first, and within
  * one length in symbol order. */
 int spo_huff_canonical(const uint8_t len[256], uint32_t code_out[256]) {
   uint32_t bl_count[32] = {0};

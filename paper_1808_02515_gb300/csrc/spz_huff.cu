@@ -4,7 +4,7 @@
 //   lengths   package-merge (Larmore & Hirschberg 1990) with maximum length 11,
 //             leaves ordered by (frequency, symbol), a leaf before a package of
 //             equal weight, one used symbol -> length 1;
-//   codes     canonical (RFC 1951 Sec. 4.2.2: by length, then symbol), each
+//   codes     canonical (RFC 1951 Sec. 3.2.2: by length, then symbol), each
 //             code's most significant bit first in the least-significant-bit-
 //             first stream;
 //   raw       a segment whose coded bytes (each chunk padded to a byte) are not

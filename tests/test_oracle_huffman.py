@@ -4,7 +4,7 @@ canonical code in place of Huff0).
 Code lengths: Kraft inequality, the length limit, optimality against brute
 force over all length vectors on tiny alphabets, and equality with the cost
 of an unrestricted Huffman code (heapq construction) when the limit does not
-bind. Canonical codes: the worked example of RFC 1951 Sec. 4.2.2.
+bind. Canonical codes: the worked example of RFC 1951 Sec. 3.2.2.
 """
 import heapq
 import itertools
