@@ -535,7 +535,11 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
   const uintptr_t buf_hi = ((uintptr_t)p.src + p.src_size) & ~(uintptr_t)15;
   const uint32_t ssh = rg.seg_shift;
   const uint64_t s_lo = live ? B0 >> ssh : 0, s_hi = live ? (B1 - 1) >> ssh : 0;
-  uint64_t seg_base = s_lo, seg_issued = s_lo, seg_waited = s_lo;
+  // segment counters relative to the body's first segment s_lo
+  const uint32_t n_segs = live ? (uint32_t)(s_hi - s_lo) + 1 : 0u;
+  const uint32_t b0r = (uint32_t)(B0 & (rg.seg - 1));  // body start inside its first segment
+  const uint32_t slot0 = (uint32_t)s_lo;
+  uint32_t seg_base = 0, seg_issued = 0, seg_waited = 0;
   uint32_t parity = 0;  // bit h: parity of the next completion of slot h
   bool ring_ok = true;
   if (live && j == 0) {
@@ -567,9 +571,9 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
       if (h == 0 && q - s0 < rg.mirror) ring[ring_bytes + (q - s0)] = v;
     }
   };
-  auto wait_upto = [&](uint64_t s) {
+  auto wait_upto = [&](uint32_t s) {
     while (seg_waited <= s && seg_waited < seg_issued) {
-      const uint32_t h = (uint32_t)(seg_waited & (rg.nseg - 1));
+      const uint32_t h = (slot0 + seg_waited) & (rg.nseg - 1);
       if (!mbar_wait(&bars[h], (parity >> h) & 1u, kRingWaitLimit)) {
         ring_ok = false;
         return;
@@ -579,9 +583,9 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
     }
   };
   if (live) {
-    const uint64_t first_end = min(s_hi + 1, s_lo + rg.nseg);
+    const uint32_t first_end = min(n_segs, rg.nseg);
     if (j == 0)
-      for (uint64_t s = s_lo; s < first_end; ++s) issue(s);
+      for (uint32_t r = 0; r < first_end; ++r) issue(s_lo + r);
     seg_issued = first_end;
   }
   // L2 prefetch ahead of the ring (segment leader)
@@ -652,16 +656,16 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
         gslot = 0;
         gq = (uint32_t)((B0 + hdr) & (ring_bytes - 1)) * 8 - hdr * 8;
         // ring: release segments before the group, load ahead, wait for the group
-        const uint64_t s_cur = (B0 + hdr) >> ssh;
-        if (seg_base < s_cur) {
-          wait_upto(s_cur - 1);
+        const uint32_t r_cur = (b0r + hdr) >> ssh;
+        if (seg_base < r_cur) {
+          wait_upto(r_cur - 1);
           ring_ok = __all_sync(seg_mask, ring_ok);
           if (j == 0) fence_proxy_async_smem();
-          while (seg_base < s_cur) {
-            const uint64_t s_new = seg_base + rg.nseg;
-            if (s_new <= s_hi) {
-              if (j == 0) issue(s_new);
-              seg_issued = s_new + 1;
+          while (seg_base < r_cur) {
+            const uint32_t r_new = seg_base + rg.nseg;
+            if (r_new < n_segs) {
+              if (j == 0) issue(s_lo + r_new);
+              seg_issued = r_new + 1;
             }
             seg_base++;
           }
@@ -671,8 +675,13 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
             pf_end = e2;
           }
         }
-        wait_upto(min(s_hi, (uint64_t)((B0 + hdr + gmax - 1) >> ssh)));
-        ring_ok = __all_sync(seg_mask, ring_ok);
+        // wait for the group's last segment unless it already arrived (the
+        // condition is the same in every lane of the chunk)
+        const uint32_t r_need = min(n_segs - 1, (b0r + hdr + gmax - 1) >> ssh);
+        if (r_need >= seg_waited && seg_waited < seg_issued) {
+          wait_upto(r_need);
+          ring_ok = __all_sync(seg_mask, ring_ok);
+        }
       }
     }
     // every lane reads its width code (reads stay inside the current group:
@@ -793,9 +802,9 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
   // reused or the CTA exits; then the barriers are retired
   if (kk < K && c64 < p.c_end && hdr_ok) {
     ring_ok = true;
-    wait_upto(~0ull);
+    wait_upto(0xFFFFFFFFu);
     if (!ring_ok && j == 0) set_status(p.status, SPRINTZ_ERR_TIMEOUT);
-    if (j == 0 && s_hi >= s_lo && seg_issued > s_lo)
+    if (j == 0 && seg_issued > 0)
       for (uint32_t h = 0; h < rg.nseg; ++h) mbar_inval(&bars[h]);
   }
   __syncwarp();
