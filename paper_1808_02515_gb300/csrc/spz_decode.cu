@@ -598,7 +598,8 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
   }
   // ring bit of body bit `bit` inside the current header group: the group's
   // ring position plus the offset into it (mod 2^32), never past the mirror
-  uint32_t gq = (uint32_t)(B0 & (ring_bytes - 1)) * 8;
+  const uint32_t b0ring = (uint32_t)(B0 & (ring_bytes - 1));
+  uint32_t gq = b0ring * 8;
   auto rbits = [&](uint32_t bit, uint32_t mask) {
     const uint32_t q = gq + bit;
     const uint32_t i0 = q >> 5;
@@ -654,7 +655,7 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
         hdr = gpos;
         gpos += g.hdr_bytes;
         gslot = 0;
-        gq = (uint32_t)((B0 + hdr) & (ring_bytes - 1)) * 8 - hdr * 8;
+        gq = ((b0ring + hdr) & (ring_bytes - 1)) * 8 - hdr * 8;
         // ring: release segments before the group, load ahead, wait for the group
         const uint32_t r_cur = (b0r + hdr) >> ssh;
         if (seg_base < r_cur) {
@@ -669,7 +670,7 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
             }
             seg_base++;
           }
-          if (j == 0 && pf_end < B1 && B0 + hdr + rg.seg * rg.nseg + kPrefetchWin / 2 > pf_end) {
+          if (j == 0 && pf_end < B1 && hdr + rg.seg * rg.nseg + kPrefetchWin / 2 > (uint32_t)(pf_end - B0)) {
             const uintptr_t e2 = min(B1, pf_end + kPrefetchWin);
             prefetch_l2_range(pf_end & ~(uintptr_t)15, e2, buf_lo, buf_hi);
             pf_end = e2;
@@ -687,9 +688,8 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
     // every lane reads its width code (reads stay inside the current group:
     // a group spans at most gmax bytes whatever the data) and the full warp
     // scans them; lanes without a new record contribute nothing that is used
-    const bool hdr_in = gpos <= packed;
     const uint32_t raw = rbits(hdr * 8 + (gslot * D + j) * hb, (1u << hb) - 1u);
-    const uint32_t code = need && hdr_in ? raw : 0u;
+    const uint32_t code = need ? raw : 0u;
     const uint32_t nw = code == (uint32_t)W - 1 ? (uint32_t)W : code;
     uint32_t v = nw;
 #pragma unroll
@@ -702,7 +702,9 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
     const uint32_t total = __shfl_sync(0xFFFFFFFFu, v, last);
     // the new record, in select form: a zero-block run (all widths zero, a
     // u16 count) or a block whose column starts at bit pbit with rows stride
-    // bits apart; corruption is only recorded, the walk stays in bounds
+    // bits apart.  The walk stays in bounds whatever the data; a record or
+    // byte count that overruns shows in the totals checked at the chunk's
+    // end, a zero run count here.
     {
       const bool isrun = total == 0;
       const uint32_t cnt = rbits(gpos * 8, 0xFFFFu);
@@ -710,9 +712,7 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
       const uint32_t size = g.col_major ? total : 8 * ((total + 7) / 8);
       const uint32_t rsize = isrun ? 2u : size;
       const uint32_t pb = g.col_major ? (gpos + prefix) * 8 : gpos * 8 + prefix;
-      const bool bad = rec >= nrec || !hdr_in || !ring_ok || gpos + rsize > packed ||
-                       (isrun && (cnt == 0 || b + cnt > nb));
-      bad_any |= need && bad;
+      bad_any |= need && isrun && cnt == 0;
       rem = need ? (isrun ? cnt : 1u) : rem;
       mask = need ? (isrun ? 0u : (1u << nw) - 1u) : mask;
       pbit = need ? (isrun ? gpos * 8 : pb) : pbit;
@@ -790,13 +790,13 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
       __syncwarp();
     }
   }
-  if (bad_any && j == 0) set_status(p.status, ring_ok ? SPRINTZ_ERR_CORRUPT : SPRINTZ_ERR_TIMEOUT);
-  // every record consumed, the body used up, unused slots of the last group zero
-  if (live && !bad_any) {
-    bool bad = rec != nrec || gpos != packed;
+  // every record consumed, the body used up, no run past the chunk's end,
+  // unused slots of the last group zero
+  if (live) {
+    bool bad = bad_any || rec != nrec || gpos != packed || rem != 0;
     for (uint32_t s = gslot; s < G && !bad; ++s)
       bad |= rbits(hdr * 8 + (s * D + j) * hb, (1u << hb) - 1u) != 0;
-    if (bad) set_status(p.status, SPRINTZ_ERR_CORRUPT);
+    if (bad || !ring_ok) set_status(p.status, ring_ok ? SPRINTZ_ERR_CORRUPT : SPRINTZ_ERR_TIMEOUT);
   }
   // no bulk copy may still be writing this warp's shared memory when it is
   // reused or the CTA exits; then the barriers are retired
