@@ -500,7 +500,10 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
   uint8_t *ring = wsm + rg.rings_off + kc * (ring_bytes + rg.mirror);
   const uint32_t *ring32 = reinterpret_cast<const uint32_t *>(ring);
   const uint32_t wb = W / 8;
-  const uint32_t hb = g.hb, G = g.G;
+  // header bits and layout: compile-time for a specialised column count
+  constexpr uint32_t hb = W == 8 ? 3u : 4u;
+  const uint32_t G = g.G;
+  const bool colmaj = DT ? (DT * W <= 32) : (g.col_major != 0);
   const uint32_t blk_bytes = kBlockRows * D * wb;  // one chunk's block of output
   const uint32_t stage_stride = blk_stage_stride(D, wb);
   const uint32_t gmax = g.hdr_bytes + G * D * W;   // largest header group (bytes)
@@ -709,14 +712,14 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
       const bool isrun = total == 0;
       const uint32_t cnt = rbits(gpos * 8, 0xFFFFu);
       const uint32_t prefix = v - nw;
-      const uint32_t size = g.col_major ? total : 8 * ((total + 7) / 8);
+      const uint32_t size = colmaj ? total : 8 * ((total + 7) / 8);
       const uint32_t rsize = isrun ? 2u : size;
-      const uint32_t pb = g.col_major ? (gpos + prefix) * 8 : gpos * 8 + prefix;
+      const uint32_t pb = colmaj ? (gpos + prefix) * 8 : gpos * 8 + prefix;
       bad_any |= need && isrun && cnt == 0;
       rem = need ? (isrun ? cnt : 1u) : rem;
       mask = need ? (isrun ? 0u : (1u << nw) - 1u) : mask;
       pbit = need ? (isrun ? gpos * 8 : pb) : pbit;
-      stride = need ? (isrun ? 0u : (g.col_major ? nw : size)) : stride;
+      stride = need ? (isrun ? 0u : (colmaj ? nw : size)) : stride;
       gpos += need ? rsize : 0u;
       gslot += need ? 1u : 0u;
       rec += need ? 1u : 0u;

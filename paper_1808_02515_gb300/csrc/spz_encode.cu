@@ -973,6 +973,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
   // the chunk's header codes fit one word and combine by butterfly shuffles
   constexpr uint32_t HB = W == 8 ? 3u : 4u;
   constexpr bool kHdrShfl = DT >= 2 && (DT & (DT - 1)) == 0 && DT * HB <= 32;
+  const bool colmaj = DT ? (DT * W <= 32) : (g.col_major != 0);
   uint8_t *slot = wslots + (uint64_t)kc * cfg.slot_stride;
 
   // cooperative stage loads: this lane's (up to two) 8-byte words of a block step
@@ -1130,7 +1131,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
         }
       }
       const uint32_t total = __shfl_sync(0xFFFFFFFFu, v, last);
-      if (here && !g.col_major) {
+      if (here && !colmaj) {
         const uint32_t nh = n << 16;
 #pragma unroll
         for (int i = 0; i < kBlockRows; ++i) tile[i * tile_rw + j] = z[i] | nh;
@@ -1149,7 +1150,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
           }
           start_record();
           const uint32_t prefix = v - n;
-          const uint32_t size = g.col_major ? total : (total + 7) & ~7u;
+          const uint32_t size = colmaj ? total : (total + 7) & ~7u;
           const uint32_t code = n == W ? W - 1 : n;
           if (kHdrShfl) {
             uint32_t hv = code << (j * HB);
@@ -1164,7 +1165,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
           } else {
             ror(hpos * 8 + (gs * D + j) * hb, code, hb);
           }
-          if (g.col_major) {
+          if (colmaj) {
             // column j: its 8 values of n bits, contiguous from byte pos + prefix
             if (n) {
               BitSink bs(ring, ring_wmask, (pos + prefix) * 8);
