@@ -288,6 +288,8 @@ __global__ void __launch_bounds__(kHuffThreads) k_huff_encode(HuffEncParams p) {
   sm.len[t] = (tab[t >> 1] >> ((t & 1) * 4)) & 15u;
   __syncthreads();
   huff_codes(sm);
+  // codes bit-reversed once: the stream is least significant bit first
+  sm.code[t] = bitrev(sm.code[t], sm.len[t]);
   const bool raw = __syncthreads_or(sm.len[t] != 0) == 0;
   const uint8_t *bytes = p.P + p.p_data_off;
   uint64_t pos = p.seg_prefix[s];
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(kHuffThreads) k_huff_encode(HuffEncParams p) {
       for (uint32_t k = k0; k < k1; ++k) {
         const uint32_t sym = bytes[off + k];
         const uint32_t l = sm.len[sym];
-        const uint32_t v = bitrev(sm.code[sym], l);
+        const uint32_t v = sm.code[sym];
         const uint32_t wi = bit >> 5, sh = bit & 31;
         atomicOr(&ob32[wi], v << sh);
         if (sh + l > 32) atomicOr(&ob32[wi + 1], v >> (32 - sh));
@@ -489,26 +491,65 @@ __global__ void __launch_bounds__(64) k_huff_decode(HuffDecParams p) {
       if (!bad)
         for (uint32_t k = 0; k < packed; ++k) out[k] = in[k];
     } else if (!bad) {
-      // bit buffer: least significant bit first
+      // bit buffer, least significant bit first, refilled with aligned
+      // 32-bit loads (bytes only past the end of the buffer); symbols leave
+      // in 8-byte stores once the output is aligned
+      const uintptr_t ia = (uintptr_t)in;
+      const uint32_t *w32 = reinterpret_cast<const uint32_t *>(ia & ~(uintptr_t)3);
+      const uint32_t lead = (uint32_t)(ia & 3);  // bytes of the first word before the chunk
+      const uint64_t words = (coded + lead + 3) / 4;
+      const uintptr_t buf_end = (uintptr_t)p.src + p.src_size;
       uint64_t buf = 0;
       uint32_t have = 0;
-      uint64_t next = 0;  // next input byte
+      uint64_t wi = 0;
       uint64_t used = 0;  // bits consumed
-      for (uint32_t k = 0; k < packed && !bad; ++k) {
-        while (have <= 56 && next < coded) {
-          buf |= (uint64_t)in[next++] << have;
-          have += 8;
+      auto refill = [&]() {
+        while (have <= 32 && wi < words) {
+          const uintptr_t a = (uintptr_t)(w32 + wi);
+          uint32_t v = 0;
+          if (a + 4 <= buf_end) {
+            v = __ldg(w32 + wi);
+          } else {
+            for (uint32_t q = 0; q < 4; ++q)
+              if (a + q < buf_end) v |= (uint32_t)*reinterpret_cast<const uint8_t *>(a + q) << (8 * q);
+          }
+          buf |= (uint64_t)v << have;
+          have += 32;
+          ++wi;
         }
+      };
+      refill();
+      buf >>= 8 * lead;
+      have -= 8 * lead;
+      auto next = [&](uint32_t *sym) -> bool {
+        refill();
         const uint32_t ent = lut[buf & ((1u << kHuffMaxLen) - 1)];
         const uint32_t l = ent >> 8;
-        if (l == 0 || l > have) {
-          bad = true;
-          break;
-        }
-        out[k] = (uint8_t)ent;
+        if (l == 0 || l > have) return false;
+        *sym = ent & 0xFFu;
         buf >>= l;
         have -= l;
         used += l;
+        return true;
+      };
+      const uint32_t head = min((uint32_t)((8 - ((uintptr_t)out & 7)) & 7), packed);
+      uint32_t k = 0, sym = 0;
+      for (; k < head && !bad; ++k) {
+        if (!next(&sym)) bad = true;
+        else out[k] = (uint8_t)sym;
+      }
+      for (; k + 8 <= packed && !bad; k += 8) {
+        uint64_t o = 0;
+#pragma unroll
+        for (uint32_t q = 0; q < 8; ++q) {
+          if (!next(&sym)) bad = true;
+          o |= (uint64_t)sym << (8 * q);
+        }
+        if (!bad) *reinterpret_cast<uint64_t *>(out + k) = o;
+      }
+      for (; k < packed && !bad; ++k) {
+        if (!next(&sym)) bad = true;
+        else out[k] = (uint8_t)sym;
       }
       if (!bad && (used + 7) / 8 != coded) bad = true;
     }
