@@ -46,6 +46,7 @@ struct HuffSmem {
   uint32_t hist[256];
   uint32_t sorted_sym[256];  // used symbols by (frequency, symbol)
   uint64_t w[2][kMaxItems + 1];
+  uint64_t wl[256];  // leaf weights in (frequency, symbol) order
   uint8_t leaf[kHuffLists][kMaxItems + 1];  // list k: item is a leaf (1) or a package (0)
   uint32_t list_len[kHuffLists];
   uint32_t take[kHuffLists];  // leaves of list k inside the selection
@@ -82,37 +83,61 @@ __device__ void huff_lengths(HuffSmem &sm) {
     __syncthreads();
     return;
   }
-  if (t == 0) {
-    // list 0: the leaves; list k: merge(leaves, packages of list k-1)
-    for (uint32_t i = 0; i < n; ++i) {
-      sm.w[0][i] = sm.hist[sm.sorted_sym[i]];
-      sm.leaf[0][i] = 1;
-    }
-    sm.list_len[0] = n;
-    for (uint32_t k = 1; k < kHuffLists; ++k) {
-      const uint64_t *A = sm.w[(k - 1) & 1];
-      uint64_t *B = sm.w[k & 1];
-      const uint32_t np = sm.list_len[k - 1] / 2;
-      uint32_t a = 0, b = 0, o = 0;
-      while (a < n || b < np) {
-        const uint64_t wl = a < n ? sm.hist[sm.sorted_sym[a]] : 0;
-        const uint64_t wp = b < np ? A[2 * b] + A[2 * b + 1] : 0;
-        const bool take_leaf = a < n && (b >= np || wl <= wp);
-        B[o] = take_leaf ? wl : wp;
-        sm.leaf[k][o] = take_leaf;
-        take_leaf ? ++a : ++b;
-        ++o;
+  // list 0: the leaves; list k: merge(leaves, packages of list k-1).  The
+  // merge is done in parallel: each leaf and each package finds its place by
+  // a binary search in the other sorted sequence (a leaf goes before a
+  // package of equal weight).
+  if (t < n) {
+    const uint64_t w0 = sm.hist[sm.sorted_sym[t]];
+    sm.wl[t] = w0;
+    sm.w[0][t] = w0;
+    sm.leaf[0][t] = 1;
+  }
+  if (t == 0) sm.list_len[0] = n;
+  __syncthreads();
+  for (uint32_t k = 1; k < kHuffLists; ++k) {
+    const uint64_t *A = sm.w[(k - 1) & 1];
+    uint64_t *B = sm.w[k & 1];
+    const uint32_t np = sm.list_len[k - 1] / 2;
+    for (uint32_t i = t; i < n; i += blockDim.x) {
+      // packages lighter than this leaf
+      const uint64_t wv = sm.wl[i];
+      uint32_t lo = 0, hi = np;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (A[2 * mid] + A[2 * mid + 1] < wv) lo = mid + 1;
+        else hi = mid;
       }
-      sm.list_len[k] = o;
+      B[i + lo] = wv;
+      sm.leaf[k][i + lo] = 1;
     }
-    // selection: the first 2n - 2 items of the last list; the packages among
-    // them select the first 2p items of the list before, and so on
+    for (uint32_t q = t; q < np; q += blockDim.x) {
+      // leaves no heavier than this package
+      const uint64_t wv = A[2 * q] + A[2 * q + 1];
+      uint32_t lo = 0, hi = n;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (sm.wl[mid] <= wv) lo = mid + 1;
+        else hi = mid;
+      }
+      B[q + lo] = wv;
+      sm.leaf[k][q + lo] = 0;
+    }
+    if (t == 0) sm.list_len[k] = n + np;
+    __syncthreads();
+  }
+  // selection: the first 2n - 2 items of the last list; the packages among
+  // them select the first 2p items of the list before, and so on
+  {
     uint32_t m = 2 * n - 2;
     for (int k = (int)kHuffLists - 1; k >= 0; --k) {
-      uint32_t leaves = 0, pk = 0;
-      for (uint32_t i = 0; i < m; ++i) sm.leaf[k][i] ? ++leaves : ++pk;
-      sm.take[k] = leaves;
-      m = 2 * pk;
+      uint32_t leaves = 0;
+      for (uint32_t base = 0; base < m; base += blockDim.x) {
+        const uint32_t i = base + t;
+        leaves += __syncthreads_count(i < m && sm.leaf[k][i]);
+      }
+      if (t == 0) sm.take[k] = leaves;
+      m = 2 * (m - leaves);
     }
   }
   __syncthreads();
@@ -203,25 +228,26 @@ __global__ void __launch_bounds__(kHuffThreads) k_huff_build(HuffEncParams p) {
   for (uint64_t k = o0 + t; k < o1; k += blockDim.x) atomicAdd(&sm.hist[bytes[k]], 1u);
   __syncthreads();
   huff_lengths(sm);
-  // coded size of every chunk of the segment
-  uint64_t coded_total = 0;
-  for (uint32_t c = c0; c < c1; ++c) {
-    uint64_t off;
-    uint32_t nrec, packed;
-    p_entry(p, c, &off, &nrec, &packed);
-    uint64_t bits = 0;
-    for (uint64_t k = off + t; k < off + packed; k += blockDim.x) bits += sm.len[bytes[k]];
-    for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xFFFFFFFFu, bits, o);
-    if ((t & 31) == 0) s_bits[t >> 5] = bits;
-    __syncthreads();
-    if (t == 0) {
-      uint64_t tb = 0;
-      for (int w = 0; w < kHuffThreads / 32; ++w) tb += s_bits[w];
-      p.chunk_coded[c] = (uint32_t)((tb + 7) / 8);
+  // coded size of every chunk of the segment: one warp per chunk
+  {
+    const uint32_t lane = t & 31, wid = t >> 5;
+    uint64_t mine = 0;
+    for (uint32_t c = c0 + wid; c < c1; c += kHuffThreads / 32) {
+      uint64_t off;
+      uint32_t nrec, packed;
+      p_entry(p, c, &off, &nrec, &packed);
+      uint64_t bits = 0;
+      for (uint64_t k = off + lane; k < off + packed; k += 32) bits += sm.len[bytes[k]];
+      for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xFFFFFFFFu, bits, o);
+      const uint32_t cb = (uint32_t)((bits + 7) / 8);
+      if (lane == 0) p.chunk_coded[c] = cb;
+      mine += cb;
     }
+    if (lane == 0) s_bits[wid] = mine;
     __syncthreads();
-    coded_total += p.chunk_coded[c];
   }
+  uint64_t coded_total = 0;
+  for (int w = 0; w < kHuffThreads / 32; ++w) coded_total += s_bits[w];
   const uint64_t packed_total = o1 - o0;
   const bool raw = packed_total == 0 || coded_total >= packed_total;
   if (raw) {
