@@ -936,9 +936,13 @@ __host__ __device__ inline uint32_t enc_tile_stride(uint32_t D) {
 __host__ __device__ inline uint32_t enc_stage_bytes(uint32_t D, uint32_t wb) {
   return ((32 / D) * blk_stage_stride(D, wb) + 15) & ~15u;
 }
+// The tile exists only for row-major packing.
+__host__ __device__ inline uint32_t enc_tile_bytes(const Geom &g) {
+  return g.col_major ? 0u : enc_tile_stride(g.D);
+}
 __host__ __device__ inline uint32_t enc_slot_region(const Geom &g, uint32_t window) {
   const uint32_t K = 32 / g.D;
-  return enc_stage_bytes(g.D, g.wb) + K * enc_tile_stride(g.D) + K * window;
+  return enc_stage_bytes(g.D, g.wb) + K * enc_tile_bytes(g) + K * window;
 }
 
 struct EncSlotCfg {
@@ -950,7 +954,10 @@ struct EncSlotCfg {
 
 // Encode chunk group `grp` of one stream with one warp: wsm is the warp's
 // shared region (stage, then K rings), wslots its K body slots.
-template <int W, int DT>
+// PF: prefetch the chunks' rows into L2 ahead of the reads (the batched
+// kernel, with few warps per SM, gains; the single-stream kernel, whose one
+// wave of warps covers the whole input, loses: its windows evict each other).
+template <int W, int DT, bool PF = false>
 __device__ __forceinline__ void encode_group_slots(const EncParams &p, const EncSlotCfg &cfg, uint32_t grp,
                                                    uint8_t *wsm, uint8_t *wslots) {
   const Geom &g = p.g;
@@ -964,7 +971,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
   const uint32_t G = g.G, hb = g.hb, H = g.hdr_bytes;
   (void)warp;
   uint8_t *stage = wsm;
-  const uint32_t tile_stride = enc_tile_stride(D), tile_rw = enc_tile_row(D) / 4;
+  const uint32_t tile_stride = enc_tile_bytes(g), tile_rw = enc_tile_row(D) / 4;
   const uint32_t st_stride = blk_stage_stride(D, wb), st_bytes = enc_stage_bytes(D, wb);
   uint32_t *tile = reinterpret_cast<uint32_t *>(wsm + st_bytes + kc * tile_stride);
   uint32_t *ring = reinterpret_cast<uint32_t *>(wsm + st_bytes + K * tile_stride + (uint64_t)kc * cfg.window);
@@ -1006,6 +1013,14 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
       nbw[t] = __shfl_sync(0xFFFFFFFFu, nb, k2[t] * D);
       const uint64_t c2 = (uint64_t)grp * K + k2[t];
       srcw[t] = reinterpret_cast<const unsigned long long *>(p.src + c2 * g.chunk_rows * D * wb) + wq[t];
+    }
+    const uintptr_t rows_lo = (uintptr_t)(p.src + row0 * D * wb);
+    const uintptr_t rows_hi = rows_lo + (uint64_t)nb * kBlockRows * D * wb;
+    uintptr_t pf = rows_lo;
+    if (PF && live && j == 0) {
+      const uintptr_t e2 = min(rows_hi, pf + 8192);
+      prefetch_l2_range(pf, e2, rows_lo, rows_hi);
+      pf = e2;
     }
     if (live)
       for (uint32_t t = j; t < cfg.window / 16; t += D)
@@ -1131,7 +1146,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
         }
       }
       const uint32_t total = __shfl_sync(0xFFFFFFFFu, v, last);
-      if (here && !colmaj) {
+      if (DT != 0 && here && !colmaj) {
         const uint32_t nh = n << 16;
 #pragma unroll
         for (int i = 0; i < kBlockRows; ++i) tile[i * tile_rw + j] = z[i] | nh;
@@ -1173,11 +1188,18 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
               for (int i = 0; i < kBlockRows; ++i) bs.put(z[i], n);
               bs.finish();
             }
+          } else if (DT == 0) {
+            // any column count (the batched kernel): each lane ORs its 8
+            // fields into the ring, rows size bits apart
+            if (n) {
+              const uint32_t b0 = pos * 8 + prefix;
+#pragma unroll
+              for (int i = 0; i < kBlockRows; ++i) ror(b0 + i * size, z[i], n);
+            }
           } else {
             // rows j, j + D, ...: each the concatenation of its D fields
             // (size bits per row), read from the tile 4 entries at a time and
             // appended two columns at a time
-            (void)prefix;
             for (uint32_t i = j; i < kBlockRows; i += D) {
               const uint4 *row = reinterpret_cast<const uint4 *>(tile + i * tile_rw);
               BitSink bs(ring, ring_wmask, pos * 8 + i * size);
@@ -1203,6 +1225,11 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
             }
           }
           end_record(size);
+        }
+        if (PF && j == 0 && pf < rows_hi && rows_lo + (uint64_t)(b + 1) * kBlockRows * D * wb + 4096 > pf) {
+          const uintptr_t e2 = min(rows_hi, pf + 4096);
+          prefetch_l2_range(pf, e2, rows_lo, rows_hi);
+          pf = e2;
         }
       }
       __syncwarp();
@@ -1366,9 +1393,9 @@ __global__ void __launch_bounds__(kEncLaneThreads) k_encode_batch(const EncBatch
     const EncBatchItem it = items[lo];
     const uint32_t grp = (uint32_t)(item - gprefix[lo]);
     if (it.p.g.w == 8)
-      encode_group_slots<8, 0>(it.p, it.cfg, grp, wsm, wslots);
+      encode_group_slots<8, 0, true>(it.p, it.cfg, grp, wsm, wslots);
     else
-      encode_group_slots<16, 0>(it.p, it.cfg, grp, wsm, wslots);
+      encode_group_slots<16, 0, true>(it.p, it.cfg, grp, wsm, wslots);
   }
 }
 
@@ -1900,7 +1927,7 @@ static uint32_t enc_batch_ctas_per_sm() {
   static uint32_t v = [] {
     const char *e = getenv("SPRINTZ_ENC_BATCH_CTAS_PER_SM");
     int x = e ? atoi(e) : 0;
-    return (uint32_t)(x > 0 && x <= 32 ? x : 4);
+    return (uint32_t)(x > 0 && x <= 32 ? x : 8);
   }();
   return v;
 }
