@@ -50,6 +50,7 @@ def parse():
                     choices=["sensor", "walk", "batch", "huffman", "serve", "fire_speed", "dsweep", "gsweep",
                              "quantize"])
     ap.add_argument("--streams", type=int, default=10_000, help="batch: number of streams")
+    ap.add_argument("--huff-rows", type=int, default=1 << 28, help="huffman: rows of the accel series")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     return ap.parse_args()
 

@@ -62,7 +62,11 @@ typedef struct {
   uint8_t learn_shift;  /* FIRE: alpha = accumulator >> learn_shift; 1 gives eta = 1/2 (Sec. 4.2.2) */
   uint32_t chunk_rows;  /* rows per chunk, multiple of 8; the forecaster restarts at each chunk;
                            0 = one chunk for the whole series (the paper's single stream) */
-  uint32_t huff_chunks; /* consecutive chunks sharing one Huffman table (huffman = 1), >= 1 */
+  uint32_t huff_chunks; /* consecutive chunks sharing one Huffman table (huffman = 1), >= 1.
+                           A coded chunk is a jump table of u32 offsets followed by
+                           independently decodable sub-blocks of 2048 packed bytes; with
+                           huffman = 1 a chunk body may not exceed 2^31 bytes
+                           (SPRINTZ_ERR_INVALID_ARG) */
 } sprintz_opts;
 
 /* Shape and options of a stream, as recorded in its 64-byte header. */

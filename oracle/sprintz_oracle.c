@@ -16,7 +16,9 @@
  *                      u64 body offset from data_off, u32 records, u32 packed bytes
  *   then             Huffman tables (huffman streams only), 128 bytes per segment:
  *                      256 code lengths, 4 bits each, symbol 2k in the low nibble
- *   data_off         chunk bodies, back to back
+ *   data_off         chunk bodies, back to back; a Huffman-coded body is a jump
+ *                    table of n-1 u32 sub-block offsets followed by n byte-
+ *                    aligned sub-block codes (huff_n_sub below)
  *   tail_off         the rows % 8 trailing rows, stored raw (Sec. 5.4: the
  *                    paper memcpy's trailing bytes)
  *   total_bytes      end of stream
@@ -35,6 +37,7 @@
 #define HDR_BYTES 64u
 #define CHUNK_ENTRY_BYTES 16u
 #define HUFF_TABLE_BYTES 128u
+#define HUFF_SUB_BYTES 2048u   /* packed bytes per independently decodable sub-block */
 
 /* ------------------------------------------------------------------------ */
 /* Integer helpers                                                          */
@@ -660,10 +663,10 @@ static uint64_t max_body_bytes(uint64_t n_blocks, uint32_t D, uint32_t w, uint32
 }
 
 /* A chunk body's size is stored in 32 bits and the chunk count in 32 bits. */
-static int check_layout(const layout *L, uint32_t D, uint32_t w, uint32_t G) {
+static int check_layout(const layout *L, uint32_t D, uint32_t w, uint32_t G, int huffman) {
   if (L->n_chunks > 0xFFFFFFFFull) return SPO_ERR_INVALID_ARG;
-  if (L->n_chunks && max_body_bytes(chunk_blocks(L, 0), D, w, G) > 0xFFFFFFFFull)
-    return SPO_ERR_INVALID_ARG;
+  uint64_t limit = huffman ? (1ull << 31) : 0xFFFFFFFFull; /* Huffman: jump-table offsets fit u32 */
+  if (L->n_chunks && max_body_bytes(chunk_blocks(L, 0), D, w, G) > limit) return SPO_ERR_INVALID_ARG;
   return SPO_OK;
 }
 
@@ -671,7 +674,7 @@ uint64_t spo_max_compressed_size(uint64_t rows, uint32_t D, uint32_t w, const sp
   if (check_opts(D, w, o) != SPO_OK) return 0;
   layout L;
   make_layout(rows, o, &L);
-  if (check_layout(&L, D, w, (uint32_t)o->group_blocks) != SPO_OK) return 0;
+  if (check_layout(&L, D, w, (uint32_t)o->group_blocks, o->huffman) != SPO_OK) return 0;
   uint64_t total = L.data_off;
   for (uint64_t c = 0; c < L.n_chunks; ++c)
     total += max_body_bytes(chunk_blocks(&L, c), D, w, (uint32_t)o->group_blocks);
@@ -703,6 +706,41 @@ static void write_header(uint8_t *dst, const layout *L, uint32_t D, uint32_t w,
   put_le(dst + 56, total, 8);
 }
 
+/* Sub-blocks of one chunk's code (our container; Huff0, the coder the paper
+ * uses, likewise splits a block into separately decodable streams behind a
+ * jump table of their sizes, RFC 8878 Sec. 4.2.2).  A body of `packed` bytes
+ * has n = ceil(packed / S) sub-blocks of q = ceil(packed / n) bytes each
+ * (S = HUFF_SUB_BYTES; the last one may be shorter; an empty body has one
+ * empty sub-block): sub-block k holds the packed bytes
+ * [min(packed, k*q), min(packed, (k+1)*q)).  The coded body is
+ *   n-1 u32 offsets: where sub-blocks 1..n-1 start, counted from the end of
+ *                    this table,
+ *   n codes:         each sub-block's symbols, padded to a byte. */
+static uint64_t huff_n_sub(uint64_t packed) {
+  return packed == 0 ? 1 : (packed + HUFF_SUB_BYTES - 1) / HUFF_SUB_BYTES;
+}
+
+/* Packed bytes [*i0, *i1) of sub-block k. */
+static void huff_sub_range(uint64_t packed, uint64_t k, uint64_t *i0, uint64_t *i1) {
+  uint64_t n = huff_n_sub(packed);
+  uint64_t q = (packed + n - 1) / n;
+  *i0 = k * q < packed ? k * q : packed;
+  *i1 = (k + 1) * q < packed ? (k + 1) * q : packed;
+}
+
+/* Coded bytes of one chunk body under the code lengths len. */
+static uint64_t huff_coded_bytes(const uint8_t *body, uint64_t packed, const uint8_t len[256]) {
+  uint64_t n_sub = huff_n_sub(packed);
+  uint64_t bytes = 4 * (n_sub - 1);
+  for (uint64_t k = 0; k < n_sub; ++k) {
+    uint64_t i0, i1, bits = 0;
+    huff_sub_range(packed, k, &i0, &i1);
+    for (uint64_t i = i0; i < i1; ++i) bits += len[body[i]];
+    bytes += (bits + 7) / 8;
+  }
+  return bytes;
+}
+
 /* Huffman-code one segment's packed chunk bodies.  Returns the coded bytes
  * written at out (or a negative error). */
 static int64_t huff_encode_segment(uint8_t *const *bodies, const uint64_t *packed,
@@ -717,11 +755,7 @@ static int64_t huff_encode_segment(uint8_t *const *bodies, const uint64_t *packe
   uint8_t len[256];
   spo_huff_code_lengths(freq, HUFF_MAX_LEN, len);
   uint64_t coded_total = 0;
-  for (uint32_t c = 0; c < n; ++c) {
-    uint64_t bits = 0;
-    for (uint64_t k = 0; k < packed[c]; ++k) bits += len[bodies[c][k]];
-    coded_total += (bits + 7) / 8;
-  }
+  for (uint32_t c = 0; c < n; ++c) coded_total += huff_coded_bytes(bodies[c], packed[c], len);
   int raw = (total_packed == 0) || (coded_total >= total_packed);
   if (raw) memset(len, 0, sizeof(len));
   for (uint32_t k = 0; k < 128; ++k) table_out[k] = (uint8_t)(len[2 * k] | (len[2 * k + 1] << 4));
@@ -737,12 +771,21 @@ static int64_t huff_encode_segment(uint8_t *const *bodies, const uint64_t *packe
       pos += packed[c];
       continue;
     }
-    bit_writer b = {out + pos, out_cap - pos, 0, 0};
-    for (uint64_t k = 0; k < packed[c]; ++k) huff_put(&b, code[bodies[c][k]], len[bodies[c][k]]);
-    bw_align_byte(&b);
+    uint64_t n_sub = huff_n_sub(packed[c]);
+    uint64_t jump = 4 * (n_sub - 1);
+    if (pos + jump > out_cap) return SPO_ERR_DST_TOO_SMALL;
+    bit_writer b = {out + pos + jump, out_cap - pos - jump, 0, 0};
+    for (uint64_t k = 0; k < n_sub; ++k) {
+      if (k > 0) put_le(out + pos + 4 * (k - 1), b.pos / 8, 4);
+      uint64_t i0, i1;
+      huff_sub_range(packed[c], k, &i0, &i1);
+      for (uint64_t i = i0; i < i1; ++i)
+        huff_put(&b, code[bodies[c][i]], len[bodies[c][i]]);
+      bw_align_byte(&b);
+    }
     if (b.overflow) return SPO_ERR_DST_TOO_SMALL;
-    coded_sizes[c] = b.pos / 8;
-    pos += b.pos / 8;
+    coded_sizes[c] = jump + b.pos / 8;
+    pos += coded_sizes[c];
   }
   return (int64_t)pos;
 }
@@ -754,7 +797,7 @@ int64_t spo_compress(const void *src_v, uint64_t rows, uint32_t D, uint32_t w,
   if (rc != SPO_OK) return rc;
   layout L;
   make_layout(rows, o, &L);
-  rc = check_layout(&L, D, w, (uint32_t)o->group_blocks);
+  rc = check_layout(&L, D, w, (uint32_t)o->group_blocks, o->huffman);
   if (rc != SPO_OK) return rc;
   if (dst_cap < L.data_off) return SPO_ERR_DST_TOO_SMALL;
   memset(dst, 0, L.data_off);
@@ -997,13 +1040,28 @@ int spo_decompress(const uint8_t *src, uint64_t n, void *dst_v, uint64_t dst_cap
       if (coded_bytes != packed) rc = SPO_ERR_CORRUPT;
       else memcpy(body, coded, packed);
     } else {
-      bit_reader b = {coded, coded_bytes, 0, 0};
-      for (uint64_t k = 0; k < packed && rc == SPO_OK; ++k) {
-        uint32_t sym;
-        rc = huff_get(&b, len, &sym);
-        body[k] = (uint8_t)sym;
+      /* the jump table, then every sub-block's code on its own */
+      uint64_t n_sub = huff_n_sub(packed);
+      uint64_t jump = 4 * (n_sub - 1);
+      if (jump > coded_bytes) rc = SPO_ERR_CORRUPT;
+      uint64_t span = rc == SPO_OK ? coded_bytes - jump : 0;
+      for (uint64_t k = 0; k < n_sub && rc == SPO_OK; ++k) {
+        uint64_t s0 = k == 0 ? 0 : get_le(coded + 4 * (k - 1), 4);
+        uint64_t s1 = k + 1 < n_sub ? get_le(coded + 4 * k, 4) : span;
+        if (s0 > s1 || s1 > span) {
+          rc = SPO_ERR_CORRUPT;
+          break;
+        }
+        bit_reader b = {coded + jump + s0, s1 - s0, 0, 0};
+        uint64_t i0, i1;
+        huff_sub_range(packed, k, &i0, &i1);
+        for (uint64_t i = i0; i < i1 && rc == SPO_OK; ++i) {
+          uint32_t sym;
+          rc = huff_get(&b, len, &sym);
+          body[i] = (uint8_t)sym;
+        }
+        if (rc == SPO_OK && (b.pos + 7) / 8 != s1 - s0) rc = SPO_ERR_CORRUPT;
       }
-      if (rc == SPO_OK && (b.pos + 7) / 8 != coded_bytes) rc = SPO_ERR_CORRUPT;
     }
     if (rc == SPO_OK) rc = decode_chunk(body, packed, n_records, nb, D, w, &o, chunk_dst);
     free(body);

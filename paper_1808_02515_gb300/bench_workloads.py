@@ -90,8 +90,10 @@ def run(args, metric, ClockSampler, peaks):
         single(x, spz.Opts(forecaster=0), "random_walk_u8_D1_100000rows_delta", 8)
         line["config"]["note"] = "100 KB: launch-latency bound; roofline not meaningful"
     elif args.workload == "huffman":
-        x = synth.accel_u8_torch(1 << 28, 3, seed=3, device=dev)
-        single(x, spz.Opts(forecaster=1, huffman=1, huff_chunks=64), "accel_u8_D3_2^28rows_FIRE_huffman", 8)
+        rows = args.huff_rows
+        x = synth.accel_u8_torch(rows, 3, seed=3, device=dev)
+        label = "accel_u8_D3_2^28rows_FIRE_huffman" if rows == 1 << 28 else f"accel_u8_D3_{rows}rows_FIRE_huffman"
+        single(x, spz.Opts(forecaster=1, huffman=1, huff_chunks=64), label, 8)
         line["config"]["generator"] = "accel_u8 recipe drawn on the GPU (torch)"
     elif args.workload == "batch":
         run_batch(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, synth, spz)

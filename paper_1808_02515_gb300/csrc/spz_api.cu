@@ -60,6 +60,8 @@ int make_geom(uint64_t rows, uint32_t D, uint32_t w, const sprintz_opts *o, Geom
   g->max_blocks = (uint32_t)(max_rows / kBlockRows);
   g->max_body = max_body_bytes(g->max_blocks, D, w, g->G);
   if (g->max_body > 0xFFFFFFFFull) return SPRINTZ_ERR_INVALID_ARG;
+  // Huffman sub-block offsets are u32: at most 11/8 of a body plus its table
+  if (g->huffman && g->max_body > (1ull << 31)) return SPRINTZ_ERR_INVALID_ARG;
   return SPRINTZ_OK;
 }
 

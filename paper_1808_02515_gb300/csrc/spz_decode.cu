@@ -476,7 +476,11 @@ struct LaneRing {
 };
 
 constexpr uint32_t kRingWaitLimit = 1u << 22;
-constexpr bool kDecDirect = true;
+// Where a lane's samples go.  With at most 3 columns a row is 1-6 bytes, so
+// a lane's per-row stores would each touch a sliver of a sector: those
+// specialisations stage a block's rows per warp in shared memory and write
+// them as 8-byte words.  Wider rows are stored straight from the lanes.
+__host__ __device__ constexpr bool dec_staged(int DT) { return DT >= 1 && DT <= 3; }
 
 // Decode chunk group `warp_id` (K consecutive chunks) of one stream with one
 // warp whose shared region (stage, barriers, rings) starts at wsm.
@@ -507,6 +511,7 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
   const uint32_t blk_bytes = kBlockRows * D * wb;  // one chunk's block of output
   const uint32_t stage_stride = blk_stage_stride(D, wb);
   const uint32_t gmax = g.hdr_bytes + G * D * W;   // largest header group (bytes)
+  constexpr bool kDecDirect = !dec_staged(DT);
 
   // the chunk bodies end at tail_off
   const uint64_t tail_off = le_u64(p.src + 48);
@@ -1098,7 +1103,7 @@ __global__ void k_decode_batch_tails(const DecBatchItem *items) {
   for (uint64_t k = threadIdx.x; k < tail_bytes; k += blockDim.x) d[k] = src[k];
 }
 
-static LaneRing lane_ring_plan(const Geom &g, const LaunchCfg &cfg, uint32_t nseg_want) {
+static LaneRing lane_ring_plan(const Geom &g, const LaunchCfg &cfg, uint32_t nseg_want, bool staged) {
   LaneRing r{};
   const uint32_t K = 32 / g.D;
   const uint32_t gmax = g.hdr_bytes + g.G * g.D * g.w;
@@ -1111,7 +1116,7 @@ static LaneRing lane_ring_plan(const Geom &g, const LaunchCfg &cfg, uint32_t nse
   }
   r.nseg = nseg_want;
   auto layout = [&](LaneRing &x) {
-    x.bars_off = kDecDirect ? 0u : (K * blk_stage_stride(g.D, g.wb) + 15) & ~15u;
+    x.bars_off = staged ? (K * blk_stage_stride(g.D, g.wb) + 15) & ~15u : 0u;
     x.rings_off = x.bars_off + ((K * x.nseg * 8 + 15) & ~15u);
     x.per_warp = x.rings_off + K * (x.nseg * x.seg + x.mirror);
   };
@@ -1229,7 +1234,7 @@ int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchC
       any_ranged = true;
     }
     if (g.n_chunks) {
-      d.rg = lane_ring_plan(g, cfg, 2);
+      d.rg = lane_ring_plan(g, cfg, 2, false);  // the batch kernel stores directly
       if (!d.rg.per_warp) return SPRINTZ_ERR_UNSUPPORTED;
       region = std::max(region, d.rg.per_warp);
     }
@@ -1304,7 +1309,7 @@ int launch_decode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint6
   k_decode_header_tail<<<1, 128, 0, stream>>>(p);
   LaneRing rg{};
   if (g.n_chunks > 0 && g.D <= 32 && ((uintptr_t)dst & 7) == 0 && g.max_body < (1ull << 28))
-    rg = lane_ring_plan(g, cfg, dec_ring_segments());
+    rg = lane_ring_plan(g, cfg, dec_ring_segments(), dec_staged((int)g.D));
   if (rg.per_warp) {
     const uint64_t K = 32 / g.D;
     const uint64_t warps = (g.n_chunks + K - 1) / K;

@@ -43,7 +43,7 @@ __device__ __forceinline__ void put_le(uint8_t *p, uint64_t v, int n) {
 
 // Shared state of the length computation of one segment.
 struct HuffSmem {
-  uint32_t hist[256];
+  uint64_t hist[256];
   uint32_t sorted_sym[256];  // used symbols by (frequency, symbol)
   uint64_t w[2][kMaxItems + 1];
   uint64_t wl[256];  // leaf weights in (frequency, symbol) order
@@ -62,7 +62,7 @@ __device__ void huff_lengths(HuffSmem &sm) {
   const uint32_t t = threadIdx.x;
   if (t == 0) sm.n_used = 0;
   __syncthreads();
-  const uint32_t f = sm.hist[t];
+  const uint64_t f = sm.hist[t];
   if (f) atomicAdd(&sm.n_used, 1u);
   sm.len[t] = 0;
   __syncthreads();
@@ -71,7 +71,7 @@ __device__ void huff_lengths(HuffSmem &sm) {
   if (f) {
     uint32_t r = 0;
     for (uint32_t u = 0; u < 256; ++u) {
-      const uint32_t fu = sm.hist[u];
+      const uint64_t fu = sm.hist[u];
       r += fu && (fu < f || (fu == f && u < t));
     }
     sm.sorted_sym[r] = t;
@@ -179,91 +179,53 @@ __device__ void huff_codes(HuffSmem &sm) {
 
 __device__ __forceinline__ uint32_t bitrev(uint32_t c, uint32_t l) { return l ? __brev(c) >> (32 - l) : 0u; }
 
+
 // ---------------------------------------------------------------------------
-// Encode
+// Sub-blocks
+//
+// A chunk body of `packed` bytes is coded as n = ceil(packed / kHuffSub)
+// sub-blocks of q = ceil(packed / n) packed bytes (the last one may be
+// shorter; an empty body has one empty sub-block).  Each is padded to a
+// byte and decodes on its own; n - 1 u32 offsets in front of them say where
+// sub-blocks 1..n-1 start, counted from the end of that jump table.  Huff0,
+// the coder the paper uses, splits its blocks into separately decodable
+// streams behind a table of their sizes in the same way (RFC 8878 Sec.
+// 4.2.2).  One warp encodes, and one thread decodes, one sub-block, so the
+// parallelism no longer depends on how wide a chunk's rows are.
 // ---------------------------------------------------------------------------
 
-struct HuffEncParams {
-  const uint8_t *P;      // Huffman-free stream (regular encoder output)
-  uint8_t *dst;
-  uint64_t dst_cap;
-  uint64_t *out_size;
-  const uint8_t *src;    // raw samples (for the tail)
-  int *status;
-  Geom g;                // the Huffman stream's geometry
-  uint64_t p_data_off;   // data offset of P
-  uint32_t *chunk_coded; // [n_chunks] coded bytes of each chunk
-  uint64_t *seg_total;   // [n_segments] coded bytes of each segment
-  uint64_t *seg_prefix;  // [n_segments + 1]
-  uint32_t *gbuf;        // per-segment code buffers in global memory when a chunk's code
-  uint64_t gbuf_words;   // does not fit shared memory (else null)
-};
+constexpr uint32_t kHuffSub = 2048;
+__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+constexpr uint32_t kHuffSubWords = (kHuffSub * kHuffMaxLen / 8 + 4) / 4 + 2;  // one sub-block's code
+constexpr uint32_t kHuffBufWords = kHuffSubWords + kHuffSubWords / 16 + 2;      // the same, skewed
+constexpr uint32_t kHuffInWords = (kHuffSub + 6) / 4 + (kHuffSub + 6) / 64 + 4;   // one sub-block, skewed
+constexpr int kHuffWarps = 8;                                                 // warps per CTA
+constexpr int kHuffEncWarps = 4;  // k_huff_encode: 5.7 KB of shared memory per warp
+constexpr uint32_t kLutSize = 1u << kHuffMaxLen;
+constexpr uint32_t kHuffDecThreads = 128;
 
-// Chunk c of P: body offset (from P's data), records, packed bytes.
-__device__ __forceinline__ void p_entry(const HuffEncParams &p, uint32_t c, uint64_t *off, uint32_t *nrec,
-                                        uint32_t *packed) {
-  const uint8_t *e = p.P + kHdrBytes + (uint64_t)c * kEntryBytes;
-  *off = le64(e);
-  *nrec = le32(e + 8);
-  *packed = le32(e + 12);
+__host__ __device__ __forceinline__ uint32_t huff_n_sub(uint32_t packed) {
+  return packed == 0 ? 1u : (uint32_t)(((uint64_t)packed + kHuffSub - 1) / kHuffSub);
 }
 
-__global__ void __launch_bounds__(kHuffThreads) k_huff_build(HuffEncParams p) {
-  __shared__ HuffSmem sm;
-  __shared__ uint64_t s_bits[kHuffThreads / 32];
-  const Geom &g = p.g;
-  const uint32_t s = blockIdx.x;
-  const uint32_t c0 = s * g.huff_chunks;
-  const uint32_t c1 = min(g.n_chunks, c0 + g.huff_chunks);
-  const uint32_t t = threadIdx.x;
-  // histogram of the segment's packed bytes (its bodies are contiguous in P)
-  uint64_t o0, o1;
-  uint32_t nr, pk;
-  p_entry(p, c0, &o0, &nr, &pk);
-  p_entry(p, c1 - 1, &o1, &nr, &pk);
-  o1 += pk;
-  sm.hist[t] = 0;
-  __syncthreads();
-  const uint8_t *bytes = p.P + p.p_data_off;
-  for (uint64_t k = o0 + t; k < o1; k += blockDim.x) atomicAdd(&sm.hist[bytes[k]], 1u);
-  __syncthreads();
-  huff_lengths(sm);
-  // coded size of every chunk of the segment: one warp per chunk
-  {
-    const uint32_t lane = t & 31, wid = t >> 5;
-    uint64_t mine = 0;
-    for (uint32_t c = c0 + wid; c < c1; c += kHuffThreads / 32) {
-      uint64_t off;
-      uint32_t nrec, packed;
-      p_entry(p, c, &off, &nrec, &packed);
-      uint64_t bits = 0;
-      for (uint64_t k = off + lane; k < off + packed; k += 32) bits += sm.len[bytes[k]];
-      for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xFFFFFFFFu, bits, o);
-      const uint32_t cb = (uint32_t)((bits + 7) / 8);
-      if (lane == 0) p.chunk_coded[c] = cb;
-      mine += cb;
-    }
-    if (lane == 0) s_bits[wid] = mine;
-    __syncthreads();
-  }
-  uint64_t coded_total = 0;
-  for (int w = 0; w < kHuffThreads / 32; ++w) coded_total += s_bits[w];
-  const uint64_t packed_total = o1 - o0;
-  const bool raw = packed_total == 0 || coded_total >= packed_total;
-  if (raw) {
-    sm.len[t] = 0;
-    __syncthreads();
-    for (uint32_t c = c0 + t; c < c1; c += blockDim.x) {
-      uint64_t off;
-      uint32_t nrec, packed;
-      p_entry(p, c, &off, &nrec, &packed);
-      p.chunk_coded[c] = packed;
-    }
-  }
-  // the segment's table: 256 lengths, 4 bits each, symbol 2k in the low nibble
-  uint8_t *tab = p.dst + kHdrBytes + (uint64_t)kEntryBytes * g.n_chunks + (uint64_t)kHuffTableBytes * s;
-  if (t < 128) tab[t] = (uint8_t)(sm.len[2 * t] | (sm.len[2 * t + 1] << 4));
-  if (t == 0) p.seg_total[s] = raw ? packed_total : coded_total;
+// Packed bytes [i0, i0 + n) of sub-block k of a body of `packed` bytes.
+__device__ __forceinline__ void huff_sub_range(uint32_t packed, uint32_t k, uint64_t *i0, uint32_t *n) {
+  const uint64_t ns = huff_n_sub(packed);
+  const uint64_t q = (packed + ns - 1) / ns;
+  const uint64_t a = umin64(packed, k * q), b = umin64(packed, (k + 1) * q);
+  *i0 = a;
+  *n = (uint32_t)(b - a);
+}
+
+// Chunks [c0, c1) of segment s.
+__device__ __forceinline__ void seg_chunks(const Geom &g, uint32_t s, uint32_t *c0, uint32_t *c1) {
+  const uint64_t a = (uint64_t)s * g.huff_chunks;
+  *c0 = (uint32_t)a;
+  *c1 = (uint32_t)umin64(g.n_chunks, a + g.huff_chunks);
+}
+
+__device__ __forceinline__ uint8_t *huff_table(uint8_t *base, const Geom &g, uint32_t s) {
+  return base + kHdrBytes + (uint64_t)kEntryBytes * g.n_chunks + (uint64_t)kHuffTableBytes * s;
 }
 
 // Exclusive prefix of the segment totals (one CTA).
@@ -300,106 +262,350 @@ __global__ void __launch_bounds__(1024) k_huff_scan(const uint64_t *in, uint64_t
   if (t == 0) out[n] = s_carry;
 }
 
-__global__ void __launch_bounds__(kHuffThreads) k_huff_encode(HuffEncParams p) {
-  __shared__ HuffSmem sm;
-  __shared__ uint32_t s_bits[kHuffThreads];
-  extern __shared__ __align__(16) uint32_t obuf[];  // one chunk's code, bit-packed
-  const Geom &g = p.g;
-  const uint32_t s = blockIdx.x;
-  const uint32_t c0 = s * g.huff_chunks;
-  const uint32_t c1 = min(g.n_chunks, c0 + g.huff_chunks);
-  const uint32_t t = threadIdx.x;
-  // the table this segment was given
-  const uint8_t *tab = p.dst + kHdrBytes + (uint64_t)kEntryBytes * g.n_chunks + (uint64_t)kHuffTableBytes * s;
-  sm.len[t] = (tab[t >> 1] >> ((t & 1) * 4)) & 15u;
-  __syncthreads();
-  huff_codes(sm);
-  // codes bit-reversed once: the stream is least significant bit first
-  sm.code[t] = bitrev(sm.code[t], sm.len[t]);
-  const bool raw = __syncthreads_or(sm.len[t] != 0) == 0;
-  const uint8_t *bytes = p.P + p.p_data_off;
-  uint64_t pos = p.seg_prefix[s];
-  for (uint32_t c = c0; c < c1; ++c) {
-    uint64_t off;
-    uint32_t nrec, packed;
-    p_entry(p, c, &off, &nrec, &packed);
-    const uint32_t coded = p.chunk_coded[c];
-    uint8_t *d = p.dst + g.data_off + pos;
-    if (t == 0) {
-      uint8_t *e = p.dst + kHdrBytes + (uint64_t)c * kEntryBytes;
-      put_le(e, pos, 8);
-      put_le(e + 8, nrec, 4);
-      put_le(e + 12, packed, 4);
-    }
-    if (raw) {
-      for (uint32_t k = t; k < packed; k += blockDim.x) d[k] = bytes[off + k];
-    } else {
-      // each thread codes a contiguous run of the chunk's bytes; a block scan
-      // of the runs' bit counts places them
-      const uint32_t per = (packed + blockDim.x - 1) / blockDim.x;
-      const uint32_t k0 = min(packed, t * per), k1 = min(packed, k0 + per);
-      uint32_t nb = 0;
-      for (uint32_t k = k0; k < k1; ++k) nb += sm.len[bytes[off + k]];
-      s_bits[t] = nb;
-      const uint32_t words = (coded + 3) / 4;
-      uint32_t *ob32 = p.gbuf ? p.gbuf + (uint64_t)s * p.gbuf_words : obuf;
-      for (uint32_t k = t; k < words; k += blockDim.x) ob32[k] = 0;
-      __syncthreads();
-      // exclusive scan of s_bits (Hillis-Steele in place)
-      for (uint32_t o = 1; o < blockDim.x; o <<= 1) {
-        const uint32_t v = t >= o ? s_bits[t - o] : 0;
-        __syncthreads();
-        s_bits[t] += v;
-        __syncthreads();
-      }
-      uint32_t bit = s_bits[t] - nb;
-      for (uint32_t k = k0; k < k1; ++k) {
-        const uint32_t sym = bytes[off + k];
-        const uint32_t l = sm.len[sym];
-        const uint32_t v = sm.code[sym];
-        const uint32_t wi = bit >> 5, sh = bit & 31;
-        atomicOr(&ob32[wi], v << sh);
-        if (sh + l > 32) atomicOr(&ob32[wi + 1], v >> (32 - sh));
-        bit += l;
-      }
-      __syncthreads();
-      const uint8_t *ob = reinterpret_cast<const uint8_t *>(ob32);
-      for (uint32_t k = t; k < coded; k += blockDim.x) d[k] = ob[k];
-    }
-    __syncthreads();
-    pos += coded;
+// Block-wide exclusive scan of one value per thread (256 threads); returns
+// the thread's exclusive prefix plus *carry, and advances *carry by the sum.
+__device__ __forceinline__ uint64_t block_scan256(uint64_t v, uint64_t *s_w, uint64_t *carry) {
+  const uint32_t t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  uint64_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
   }
-  if (s == g.n_segments - 1 && t == 0) {
-    const uint64_t tail_off = g.data_off + p.seg_prefix[g.n_segments];
-    const uint64_t tail_bytes = g.tail_rows * g.D * g.wb;
-    const uint64_t total = tail_off + tail_bytes;
-    if (total <= p.dst_cap) {
-      for (uint64_t k = 0; k < tail_bytes; ++k) p.dst[tail_off + k] = p.src[g.full_rows * g.D * g.wb + k];
-      uint8_t *h = p.dst;
-      for (int k = 0; k < 64; ++k) h[k] = 0;
-      h[0] = 'S';
-      h[1] = 'P';
-      h[2] = 'Z';
-      h[3] = '1';
-      h[4] = 1;
-      h[5] = (uint8_t)g.w;
-      h[6] = (uint8_t)g.forecaster;
-      h[7] = 1;
-      put_le(h + 8, g.D, 2);
-      h[10] = (uint8_t)g.G;
-      h[11] = (uint8_t)g.learn_shift;
-      put_le(h + 12, g.chunk_rows_opt, 4);
-      put_le(h + 16, g.huff_chunks, 4);
-      put_le(h + 20, g.n_chunks, 4);
-      put_le(h + 24, g.rows, 8);
-      put_le(h + 32, g.tail_rows, 4);
-      put_le(h + 40, g.data_off, 8);
-      put_le(h + 48, tail_off, 8);
-      put_le(h + 56, total, 8);
-      *p.out_size = total;
-    } else {
-      set_status(p.status, SPRINTZ_ERR_DST_TOO_SMALL);
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t z = lane < 8 ? s_w[lane] : 0;
+    for (int o = 1; o < 8; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, z, o);
+      if (lane >= o) z += y;
     }
+    if (lane < 8) s_w[lane] = z;
+  }
+  __syncthreads();
+  const uint64_t excl = x - v + (warp ? s_w[warp - 1] : 0) + *carry;
+  __syncthreads();
+  if (t == 255) *carry = excl + v;
+  __syncthreads();
+  return excl;
+}
+
+// ---------------------------------------------------------------------------
+// Encode
+// ---------------------------------------------------------------------------
+
+struct HuffEncParams {
+  const uint8_t *P;               // Huffman-free stream (regular encoder output)
+  uint8_t *dst;
+  uint64_t dst_cap;
+  uint64_t *out_size;
+  const uint8_t *src;             // raw samples (for the tail)
+  int *status;
+  Geom g;                         // the Huffman stream's geometry
+  uint64_t p_data_off;            // data offset of P
+  uint64_t p_body_cap;            // bytes of P after p_data_off
+  uint32_t slots;                 // sub-block slots per chunk (sub-blocks of the largest body)
+  uint32_t slices;                // histogram CTAs per segment
+  uint64_t slice_bytes;           // packed bytes per histogram CTA
+  unsigned long long *hist;       // [n_segments][256] byte counts
+  uint32_t *codes;                // [n_segments][256] bit-reversed code | length << 16
+  unsigned long long *seg_coded;  // [n_segments] coded bytes of the segment's chunks
+  uint32_t *seg_raw;              // [n_segments] 1 = stored raw
+  uint64_t *seg_total;            // [n_segments] bytes the segment takes in the stream
+  uint64_t *seg_prefix;           // [n_segments + 1]
+  uint64_t *chunk_coded;          // [n_chunks] coded bytes of each chunk
+  uint64_t *chunk_pos;            // [n_chunks] offset of each chunk inside its segment
+  uint32_t *sub_off;              // [n_chunks][slots] start of each sub-block inside its chunk
+};
+
+// Chunk c of P: body offset (from P's data), records, packed bytes.  The
+// regular encoder wrote these; they are clamped to P and to the largest
+// body all the same, so that a failed encode cannot send a read astray.
+__device__ __forceinline__ void p_entry(const HuffEncParams &p, uint32_t c, uint64_t *off, uint32_t *nrec,
+                                        uint32_t *packed) {
+  const uint8_t *e = p.P + kHdrBytes + (uint64_t)c * kEntryBytes;
+  const uint64_t o = min(le64(e), p.p_body_cap);
+  *off = o;
+  *nrec = le32(e + 8);
+  *packed = (uint32_t)min(min((uint64_t)le32(e + 12), p.p_body_cap - o), p.g.max_body);
+}
+
+// Byte histogram of one slice of a segment's packed bytes (the segment's
+// bodies are contiguous in P): per-warp counters, then global atomics.
+__global__ void __launch_bounds__(kHuffWarps * 32) k_huff_hist(HuffEncParams p) {
+  __shared__ uint32_t h[kHuffWarps][256];
+  const Geom &g = p.g;
+  const uint32_t s = blockIdx.x / p.slices, part = blockIdx.x % p.slices;
+  uint32_t c0, c1;
+  seg_chunks(g, s, &c0, &c1);
+  uint64_t o0, o1;
+  uint32_t nr, pk;
+  p_entry(p, c0, &o0, &nr, &pk);
+  p_entry(p, c1 - 1, &o1, &nr, &pk);
+  o1 += pk;
+  const uint64_t a = o0 + (uint64_t)part * p.slice_bytes;
+  if (a >= o1) return;
+  const uint64_t b = min(o1, a + p.slice_bytes);
+  const uint32_t t = threadIdx.x, warp = t >> 5;
+  for (uint32_t k = t; k < kHuffWarps * 256; k += blockDim.x) (&h[0][0])[k] = 0;
+  __syncthreads();
+  // aligned 32-bit words covering [a, b); P has slack after its last byte
+  const uintptr_t base = (uintptr_t)(p.P + p.p_data_off);
+  const uintptr_t A = base + a, B = base + b;
+  for (uintptr_t q = (A & ~(uintptr_t)3) + 4 * (uintptr_t)t; q < B; q += 4 * (uintptr_t)blockDim.x) {
+    const uint32_t v = *reinterpret_cast<const uint32_t *>(q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (q + i >= A && q + i < B) atomicAdd(&h[warp][(v >> (8 * i)) & 255u], 1u);
+  }
+  __syncthreads();
+  uint32_t sum = 0;
+  for (int w = 0; w < kHuffWarps; ++w) sum += h[w][t];
+  if (sum) atomicAdd(&p.hist[(uint64_t)s * 256 + t], (unsigned long long)sum);
+}
+
+// Code lengths, the table and the codes of one segment (one CTA).
+__global__ void __launch_bounds__(kHuffThreads) k_huff_lengths(HuffEncParams p) {
+  __shared__ HuffSmem sm;
+  const uint32_t s = blockIdx.x, t = threadIdx.x;
+  sm.hist[t] = p.hist[(uint64_t)s * 256 + t];
+  __syncthreads();
+  huff_lengths(sm);
+  huff_codes(sm);
+  const uint32_t l = sm.len[t];
+  p.codes[(uint64_t)s * 256 + t] = bitrev(sm.code[t], l) | (l << 16);
+  uint8_t *tab = huff_table(p.dst, p.g, s);
+  if (t < 128) tab[t] = (uint8_t)(sm.len[2 * t] | (sm.len[2 * t + 1] << 4));
+  if (t == 0) p.seg_coded[s] = 0;
+}
+
+// Coded size of every sub-block of a chunk (one warp per chunk).
+__global__ void __launch_bounds__(kHuffWarps * 32) k_huff_sizes(HuffEncParams p) {
+  __shared__ uint8_t s_len[kHuffWarps][256];
+  const Geom &g = p.g;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t c64 = (uint64_t)blockIdx.x * kHuffWarps + warp;
+  if (c64 >= g.n_chunks) return;
+  const uint32_t c = (uint32_t)c64;
+  const uint32_t s = c / g.huff_chunks;
+  const uint32_t *cs = p.codes + (uint64_t)s * 256;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s_len[warp][lane + 32 * i] = (uint8_t)(cs[lane + 32 * i] >> 16);
+  __syncwarp();
+  uint64_t off;
+  uint32_t nrec, packed;
+  p_entry(p, c, &off, &nrec, &packed);
+  const uint8_t *body = p.P + p.p_data_off + off;
+  const uint32_t n_sub = huff_n_sub(packed);
+  uint64_t run = 4ull * (n_sub - 1);
+  for (uint32_t k = 0; k < n_sub; ++k) {
+    uint64_t i0;
+    uint32_t len;
+    huff_sub_range(packed, k, &i0, &len);
+    uint32_t bits = 0;
+    for (uint64_t i = i0 + lane; i < i0 + len; i += 32) bits += s_len[warp][body[i]];
+    for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xFFFFFFFFu, bits, o);
+    if (lane == 0) p.sub_off[(uint64_t)c * p.slots + k] = (uint32_t)run;
+    run += (bits + 7) / 8;
+  }
+  if (lane == 0) {
+    p.chunk_coded[c] = run;
+    atomicAdd(&p.seg_coded[s], (unsigned long long)run);
+  }
+}
+
+// Raw or coded, and every chunk's place inside its segment (one CTA per
+// segment): a segment whose coded bytes are not fewer than its packed bytes
+// keeps an all-zero table and raw bodies.
+__global__ void __launch_bounds__(256) k_huff_decide(HuffEncParams p) {
+  __shared__ uint64_t s_w[8];
+  __shared__ uint64_t s_carry;
+  __shared__ uint32_t s_raw;
+  const Geom &g = p.g;
+  const uint32_t s = blockIdx.x, t = threadIdx.x;
+  uint32_t c0, c1;
+  seg_chunks(g, s, &c0, &c1);
+  if (t == 0) {
+    uint64_t o0, o1;
+    uint32_t nr, pk;
+    p_entry(p, c0, &o0, &nr, &pk);
+    p_entry(p, c1 - 1, &o1, &nr, &pk);
+    const uint64_t packed_total = o1 + pk - o0;
+    const uint32_t raw = packed_total == 0 || p.seg_coded[s] >= packed_total;
+    s_raw = raw;
+    p.seg_raw[s] = raw;
+    s_carry = 0;
+  }
+  __syncthreads();
+  const bool raw = s_raw != 0;
+  if (raw && t < 128) huff_table(p.dst, g, s)[t] = 0;
+  for (uint64_t base = c0; base < c1; base += 256) {
+    const uint64_t c = base + t;
+    uint64_t v = 0;
+    if (c < c1) {
+      uint64_t off;
+      uint32_t nrec, packed;
+      p_entry(p, (uint32_t)c, &off, &nrec, &packed);
+      v = raw ? packed : p.chunk_coded[c];
+    }
+    const uint64_t excl = block_scan256(v, s_w, &s_carry);
+    if (c < c1) p.chunk_pos[c] = excl;
+  }
+  if (t == 0) p.seg_total[s] = s_carry;
+}
+
+// One warp per sub-block: its packed bytes are copied to shared memory with
+// coalesced word loads; lanes code contiguous runs of them, a warp scan of
+// their bit counts places them in a shared buffer (whole words stored, the
+// words two lanes share OR-ed), and the coded bytes go to the stream in
+// 4-byte stores.  Both shared buffers have a pad word after every 16, so
+// that lanes working about 16 words apart hit different banks.  The first
+// warp of a chunk writes its table entry, the others their jump-table
+// offsets.
+__global__ void __launch_bounds__(kHuffEncWarps * 32) k_huff_encode(HuffEncParams p) {
+  __shared__ uint16_t s_code[kHuffEncWarps][256];  // reversed code | length << 11
+  __shared__ uint32_t s_in[kHuffEncWarps][kHuffInWords];
+  __shared__ uint32_t s_buf[kHuffEncWarps][kHuffBufWords];
+  const Geom &g = p.g;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t slot = (uint64_t)blockIdx.x * kHuffEncWarps + warp;
+  const uint64_t c64 = slot / p.slots;
+  if (c64 >= g.n_chunks) return;
+  const uint32_t c = (uint32_t)c64, k = (uint32_t)(slot % p.slots);
+  uint64_t off;
+  uint32_t nrec, packed;
+  p_entry(p, c, &off, &nrec, &packed);
+  const uint32_t n_sub = huff_n_sub(packed);
+  if (k >= n_sub) return;
+  const uint32_t s = c / g.huff_chunks;
+  const bool raw = p.seg_raw[s] != 0;
+  const uint64_t cpos = p.seg_prefix[s] + p.chunk_pos[c];  // from data_off
+  const uint64_t ctotal = raw ? packed : p.chunk_coded[c];
+  if (g.data_off + cpos + ctotal > p.dst_cap) {
+    if (lane == 0) set_status(p.status, SPRINTZ_ERR_DST_TOO_SMALL);
+    return;
+  }
+  uint8_t *d = p.dst + g.data_off + cpos;
+  if (k == 0 && lane == 0) {
+    uint8_t *e = p.dst + kHdrBytes + (uint64_t)c * kEntryBytes;
+    put_le(e, cpos, 8);
+    put_le(e + 8, nrec, 4);
+    put_le(e + 12, packed, 4);
+  }
+  uint64_t i0;
+  uint32_t n;
+  huff_sub_range(packed, k, &i0, &n);
+  const uint8_t *in = p.P + p.p_data_off + off + i0;
+  if (raw) {
+    for (uint32_t i = lane; i < n; i += 32) d[i0 + i] = in[i];
+    return;
+  }
+  const uint32_t jump = 4 * (n_sub - 1);
+  const uint32_t start = p.sub_off[(uint64_t)c * p.slots + k];
+  if (k > 0 && lane < 4) d[4 * (k - 1) + lane] = (uint8_t)((start - jump) >> (8 * lane));
+  const uint32_t *cs = p.codes + (uint64_t)s * 256;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t e = cs[lane + 32 * i];
+    s_code[warp][lane + 32 * i] = (uint16_t)((e & 0x7FFu) | ((e >> 16) << 11));
+  }
+  // the sub-block's bytes: aligned words from up to 3 bytes before it to up
+  // to 3 bytes after it (P has slack after its last byte)
+  const uint32_t lead = (uint32_t)((uintptr_t)in & 3);
+  const uint32_t *w32 = reinterpret_cast<const uint32_t *>((uintptr_t)in - lead);
+  const uint32_t nw = (n + lead + 3) / 4;
+  uint32_t *sin = s_in[warp];
+  for (uint32_t q = lane; q < nw; q += 32) sin[q + (q >> 4)] = w32[q];
+  __syncwarp();
+  auto byte_at = [&](uint32_t j) {
+    const uint32_t x = j + lead, q = x >> 2;
+    return (sin[q + (q >> 4)] >> (8 * (x & 3))) & 255u;
+  };
+  const uint32_t per = (n + 31) / 32;
+  const uint32_t a = min(n, lane * per), b = min(n, a + per);
+  uint32_t nb = 0;
+  for (uint32_t i = a; i < b; ++i) nb += s_code[warp][byte_at(i)] >> 11;
+  uint32_t incl = nb;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  uint32_t *buf = s_buf[warp];
+  auto pad = [](uint32_t w) { return w + (w >> 4); };
+  for (uint32_t i = lane; i <= pad(total / 32 + 1); i += 32) buf[i] = 0;
+  __syncwarp();
+  // the lane's bits [bit0, bit0 + nb): whole words stored, its first word
+  // (shared with the lane before) and last word (with the lane after) OR-ed
+  const uint32_t bit0 = incl - nb;
+  uint32_t wi = bit0 >> 5, nacc = bit0 & 31;
+  bool first_shared = nacc != 0;
+  uint64_t acc = 0;
+  for (uint32_t i = a; i < b; ++i) {
+    const uint32_t e = s_code[warp][byte_at(i)];
+    acc |= (uint64_t)(e & 0x7FFu) << nacc;
+    nacc += e >> 11;
+    if (nacc >= 32) {
+      if (first_shared) atomicOr(&buf[pad(wi)], (uint32_t)acc);
+      else buf[pad(wi)] = (uint32_t)acc;
+      first_shared = false;
+      acc >>= 32;
+      nacc -= 32;
+      ++wi;
+    }
+  }
+  if (b > a && nacc > 0) atomicOr(&buf[pad(wi)], (uint32_t)acc);
+  __syncwarp();
+  // the coded bytes: a few head bytes until the destination is 4-byte
+  // aligned, whole words (two buffer words funnel-shifted), tail bytes
+  const uint32_t nbytes = (total + 7) / 8;
+  uint8_t *dd = d + start;
+  auto byte_of = [&](uint32_t i) { return (uint8_t)(buf[pad(i >> 2)] >> (8 * (i & 3))); };
+  const uint32_t hb = min(nbytes, (uint32_t)((4 - ((uintptr_t)dd & 3)) & 3));
+  if (lane < hb) dd[lane] = byte_of(lane);
+  const uint32_t nout = (nbytes - hb) / 4, sh = 8 * (hb & 3);
+  uint32_t *dw = reinterpret_cast<uint32_t *>(dd + hb);
+  for (uint32_t m = lane; m < nout; m += 32) {
+    const uint32_t w = (hb + 4 * m) >> 2;
+    dw[m] = __funnelshift_r(buf[pad(w)], buf[pad(w + 1)], sh);
+  }
+  for (uint32_t i = hb + 4 * nout + lane; i < nbytes; i += 32) dd[i] = byte_of(i);
+}
+
+// Header and raw tail of the Huffman stream.
+__global__ void k_huff_enc_finish(HuffEncParams p) {
+  const Geom &g = p.g;
+  const uint64_t tail_off = g.data_off + p.seg_prefix[g.n_segments];
+  const uint64_t tail_bytes = g.tail_rows * g.D * g.wb;
+  const uint64_t total = tail_off + tail_bytes;
+  if (total > p.dst_cap) {
+    if (threadIdx.x == 0) set_status(p.status, SPRINTZ_ERR_DST_TOO_SMALL);
+    return;
+  }
+  for (uint64_t k = threadIdx.x; k < tail_bytes; k += blockDim.x)
+    p.dst[tail_off + k] = p.src[g.full_rows * g.D * g.wb + k];
+  if (threadIdx.x == 0) {
+    uint8_t *h = p.dst;
+    for (int k = 0; k < 64; ++k) h[k] = 0;
+    h[0] = 'S';
+    h[1] = 'P';
+    h[2] = 'Z';
+    h[3] = '1';
+    h[4] = 1;
+    h[5] = (uint8_t)g.w;
+    h[6] = (uint8_t)g.forecaster;
+    h[7] = 1;
+    put_le(h + 8, g.D, 2);
+    h[10] = (uint8_t)g.G;
+    h[11] = (uint8_t)g.learn_shift;
+    put_le(h + 12, g.chunk_rows_opt, 4);
+    put_le(h + 16, g.huff_chunks, 4);
+    put_le(h + 20, g.n_chunks, 4);
+    put_le(h + 24, g.rows, 8);
+    put_le(h + 32, g.tail_rows, 4);
+    put_le(h + 40, g.data_off, 8);
+    put_le(h + 48, tail_off, 8);
+    put_le(h + 56, total, 8);
+    *p.out_size = total;
   }
 }
 
@@ -415,174 +621,222 @@ struct HuffDecParams {
   int *status;
   Geom g;                // the Huffman stream's geometry
   uint64_t p_data_off;
+  uint32_t slots;        // sub-block slots per chunk
+  uint32_t parts;        // k_huff_decode CTAs per segment
+  uint16_t *lut;         // [n_segments][2^11] symbol | length << 8 (0: no code)
+  uint32_t *seg_flags;   // [n_segments] bit 0 raw, bit 1 invalid table
   uint64_t *seg_packed;  // [n_segments] packed bytes per segment, then its prefix
   uint64_t *seg_prefix;  // [n_segments + 1]
+  uint64_t *chunk_poff;  // [n_chunks] packed offset of each chunk inside its segment
+  uint64_t *chunk_sub0;  // [n_chunks] index of each chunk's first sub-block inside its segment
+  uint64_t *seg_nsub;    // [n_segments] sub-blocks of each segment
 };
 
-// Packed bytes of every segment (one thread per segment).
-__global__ void k_huff_seg_packed(HuffDecParams p) {
-  const Geom &g = p.g;
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= g.n_segments) return;
-  const uint32_t c0 = s * g.huff_chunks, c1 = min(g.n_chunks, c0 + g.huff_chunks);
-  uint64_t sum = 0;
-  for (uint32_t c = c0; c < c1; ++c) sum += le32(p.src + kHdrBytes + (uint64_t)c * kEntryBytes + 12);
-  p.seg_packed[s] = sum;
-}
-
-// One CTA per segment, one thread per chunk: decode each chunk's bitstream
-// into the Huffman-free stream P (its body and its chunk-table entry).
-__global__ void __launch_bounds__(64) k_huff_decode(HuffDecParams p) {
+// Per segment: check its table (lengths <= 11, Kraft), build its 11-bit
+// lookup table, and place its chunks' packed bodies.
+__global__ void __launch_bounds__(256) k_huff_dec_prep(HuffDecParams p) {
   __shared__ uint8_t s_len[256];
-  __shared__ uint32_t s_code[256];
   __shared__ uint32_t s_cnt[16];
-  __shared__ uint16_t lut[1u << kHuffMaxLen];  // symbol | length << 8
-  __shared__ uint32_t s_packed[64];
+  __shared__ uint16_t s_lut[kLutSize];
+  __shared__ uint64_t s_w[8];
+  __shared__ uint64_t s_carry, s_carry2;
   __shared__ uint32_t s_ok;
   const Geom &g = p.g;
-  const uint32_t s = blockIdx.x;
-  const uint32_t t = threadIdx.x;
-  const uint8_t *tab = p.src + kHdrBytes + (uint64_t)kEntryBytes * g.n_chunks + (uint64_t)kHuffTableBytes * s;
-  for (uint32_t k = t; k < 256; k += blockDim.x) s_len[k] = (tab[k >> 1] >> ((k & 1) * 4)) & 15u;
+  const uint32_t s = blockIdx.x, t = threadIdx.x;
+  const uint8_t *tab = huff_table(const_cast<uint8_t *>(p.src), g, s);
+  s_len[t] = (tab[t >> 1] >> ((t & 1) * 4)) & 15u;
   if (t < 16) s_cnt[t] = 0;
-  if (t == 0) s_ok = 1;
+  if (t == 0) {
+    s_ok = 1;
+    s_carry = 0;
+    s_carry2 = 0;
+  }
+  for (uint32_t k = t; k < kLutSize; k += blockDim.x) s_lut[k] = 0;
   __syncthreads();
-  for (uint32_t k = t; k < 256; k += blockDim.x)
-    if (s_len[k]) atomicAdd(&s_cnt[s_len[k]], 1u);
+  if (s_len[t]) atomicAdd(&s_cnt[s_len[t]], 1u);
   __syncthreads();
-  // lengths above 11 are invalid; the code must not be over-subscribed (Kraft)
   if (t == 0) {
     for (uint32_t l = kHuffMaxLen + 1; l < 16; ++l)
       if (s_cnt[l]) s_ok = 0;
     uint64_t kraft = 0;
     for (uint32_t l = 1; l <= kHuffMaxLen; ++l) kraft += (uint64_t)s_cnt[l] << (kHuffMaxLen - l);
     if (kraft > (1ull << kHuffMaxLen)) s_ok = 0;
-    uint32_t code = 0;
-    uint32_t prev = 0;
+    uint32_t code = 0, prev = 0;
     for (uint32_t bits = 1; bits <= kHuffMaxLen; ++bits) {
       code = (code + prev) << 1;
       prev = s_cnt[bits];
       s_cnt[bits] = code;  // first code of this length
     }
   }
-  const bool raw = __syncthreads_or((t < 128 && tab[t] != 0) || (t + 64 < 128 && tab[t + 64] != 0)) == 0;
-  for (uint32_t k = t; k < 256; k += blockDim.x) {
-    const uint32_t l = s_len[k];
+  const bool raw = __syncthreads_or(t < 128 && tab[t] != 0) == 0;
+  const bool ok = s_ok != 0;
+  const uint32_t l = s_len[t];
+  if (!raw && ok && l) {
     uint32_t r = 0;
-    if (l)
-      for (uint32_t u = 0; u < k; ++u) r += s_len[u] == l;
-    s_code[k] = l ? s_cnt[l] + r : 0;
+    for (uint32_t u = 0; u < t; ++u) r += s_len[u] == l;
+    const uint32_t rc = bitrev(s_cnt[l] + r, l);
+    for (uint32_t fill = 0; fill < (1u << (kHuffMaxLen - l)); ++fill)
+      s_lut[rc | (fill << l)] = (uint16_t)(t | (l << 8));
   }
-  for (uint32_t k = t; k < (1u << kHuffMaxLen); k += blockDim.x) lut[k] = 0;
   __syncthreads();
-  if (!raw && s_ok) {
-    for (uint32_t k = t; k < 256; k += blockDim.x) {
-      const uint32_t l = s_len[k];
-      if (!l) continue;
-      const uint32_t rc = bitrev(s_code[k], l);
-      for (uint32_t fill = 0; fill < (1u << (kHuffMaxLen - l)); ++fill)
-        lut[rc | (fill << l)] = (uint16_t)(k | (l << 8));
+  if (!raw && ok) {
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(p.lut + (uint64_t)s * kLutSize);
+    const uint32_t *l32 = reinterpret_cast<const uint32_t *>(s_lut);
+    for (uint32_t k = t; k < kLutSize / 2; k += blockDim.x) d32[k] = l32[k];
+  }
+  if (t == 0) {
+    p.seg_flags[s] = (raw ? 1u : 0u) | (ok ? 0u : 2u);
+    if (!ok) set_status(p.status, SPRINTZ_ERR_CORRUPT);
+  }
+  uint32_t c0, c1;
+  seg_chunks(g, s, &c0, &c1);
+  for (uint64_t base = c0; base < c1; base += 256) {
+    const uint64_t c = base + t;
+    const uint32_t v = c < c1 ? le32(p.src + kHdrBytes + c * kEntryBytes + 12) : 0;
+    const uint64_t excl = block_scan256(v, s_w, &s_carry);
+    const uint64_t sub0 = block_scan256(c < c1 ? huff_n_sub(v) : 0, s_w, &s_carry2);
+    if (c < c1) {
+      p.chunk_poff[c] = excl;
+      p.chunk_sub0[c] = sub0;
     }
   }
-  __syncthreads();
-  if (!s_ok) {
-    if (t == 0) set_status(p.status, SPRINTZ_ERR_CORRUPT);
-    return;
+  if (t == 0) {
+    p.seg_packed[s] = s_carry;
+    p.seg_nsub[s] = s_carry2;
   }
-  const uint32_t c0 = s * g.huff_chunks, c1 = min(g.n_chunks, c0 + g.huff_chunks);
+}
+
+// Decode `n` symbols of one sub-block's code [in, in + bytes) into out with
+// the 11-bit table.  The bit buffer (least significant bit first) holds at
+// least 32 bits before every pair of symbols: it is refilled from aligned
+// 32-bit words, the next one already loaded (zeros past the code's words,
+// bytes only past the end of the stream buffer).  Symbols leave in 8-byte
+// stores once out is aligned.  True when every symbol has a code and the
+// symbols use exactly the code's bytes.
+__device__ __forceinline__ bool huff_decode_sub(const uint8_t *in, uint64_t bytes, uint32_t n, uint8_t *out,
+                                                const uint16_t *lut, uintptr_t buf_end) {
+  const uintptr_t ia = (uintptr_t)in;
+  const uint32_t *w32 = reinterpret_cast<const uint32_t *>(ia & ~(uintptr_t)3);
+  const uint32_t lead = (uint32_t)(ia & 3);  // bytes of the first word before the code
+  const uint64_t words = (bytes + lead + 3) / 4;
+  auto load = [&](uint64_t i) -> uint32_t {
+    if (i >= words) return 0u;
+    const uintptr_t a = (uintptr_t)(w32 + i);
+    if (a + 4 <= buf_end) return __ldg(w32 + i);
+    uint32_t v = 0;
+    for (uint32_t q = 0; q < 4; ++q)
+      if (a + q < buf_end) v |= (uint32_t)*reinterpret_cast<const uint8_t *>(a + q) << (8 * q);
+    return v;
+  };
+  uint64_t buf = ((uint64_t)load(0) | ((uint64_t)load(1) << 32)) >> (8 * lead);
+  uint32_t have = 64 - 8 * lead;
+  uint32_t nxt = load(2);
+  uint64_t wi = 3;  // words loaded (nxt is the last, not yet in buf)
+  bool bad = false;
+  auto refill = [&]() {
+    if (have < 32) {
+      buf |= (uint64_t)nxt << have;
+      have += 32;
+      nxt = load(wi);
+      ++wi;
+    }
+  };
+  auto dec1 = [&]() -> uint32_t {
+    const uint32_t ent = lut[buf & (kLutSize - 1)];
+    const uint32_t l = ent >> 8;
+    bad |= l == 0;
+    buf >>= l;
+    have -= l;
+    return ent & 0xFFu;
+  };
+  const uint32_t head = min((uint32_t)((8 - ((uintptr_t)out & 7)) & 7), n);
+  uint32_t k = 0;
+  for (; k < head; ++k) {
+    refill();
+    out[k] = (uint8_t)dec1();
+  }
+  for (; k + 8 <= n; k += 8) {
+    uint64_t o = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < 8; q += 2) {
+      refill();
+      o |= (uint64_t)dec1() << (8 * q);
+      o |= (uint64_t)dec1() << (8 * q + 8);
+    }
+    *reinterpret_cast<uint64_t *>(out + k) = o;
+  }
+  for (; k < n; ++k) {
+    refill();
+    out[k] = (uint8_t)dec1();
+  }
+  const uint64_t used = 32ull * (wi - 1) - 8ull * lead - have;  // bits taken from the code
+  return !bad && (used + 7) / 8 == bytes;
+}
+
+// One thread per sub-block: CTA (segment, part) covers sub-blocks
+// [part * blockDim, (part + 1) * blockDim) of its segment; a binary search
+// over the chunks' first sub-block indices finds the thread's chunk.  Every
+// sub-block decodes into the Huffman-free stream P; the thread of sub-block
+// 0 writes the chunk's entry of P's table.
+__global__ void __launch_bounds__(kHuffDecThreads, 10) k_huff_decode(HuffDecParams p) {
+  __shared__ __align__(16) uint16_t lut[kLutSize];
+  const Geom &g = p.g;
+  const uint32_t s = blockIdx.x / p.parts, part = blockIdx.x % p.parts, t = threadIdx.x;
+  const uint32_t flags = p.seg_flags[s];
+  if (flags & 2u) return;
+  const bool raw = (flags & 1u) != 0;
+  if (!raw) {
+    const uint32_t *l32 = reinterpret_cast<const uint32_t *>(p.lut + (uint64_t)s * kLutSize);
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(lut);
+    for (uint32_t k = t; k < kLutSize / 2; k += blockDim.x) d32[k] = l32[k];
+  }
+  __syncthreads();
+  uint32_t c0, c1;
+  seg_chunks(g, s, &c0, &c1);
+  const uint64_t j = (uint64_t)part * blockDim.x + t;
+  if (j >= p.seg_nsub[s]) return;
+  uint32_t lo = c0, hi = c1 - 1;  // the last chunk whose first sub-block is <= j
+  while (lo < hi) {
+    const uint32_t mid = lo + (hi - lo + 1) / 2;
+    if (p.chunk_sub0[mid] <= j) lo = mid;
+    else hi = mid - 1;
+  }
+  const uint32_t c = lo, k = (uint32_t)(j - p.chunk_sub0[c]);
+  const uint8_t *e = p.src + kHdrBytes + (uint64_t)c * kEntryBytes;
+  const uint64_t off = le64(e);
+  const uint32_t nrec = le32(e + 8), packed = le32(e + 12);
+  const uint32_t n_sub = huff_n_sub(packed);
   const uint64_t tail_off = le64(p.src + 48);
   const uint64_t data_bytes = tail_off >= g.data_off && tail_off <= p.src_size ? tail_off - g.data_off : 0;
-  for (uint32_t cb = c0; cb < c1; cb += 64) {
-    const uint32_t c = cb + t;
-    const bool mine = c < c1;
-    uint32_t packed = 0;
-    if (mine) packed = le32(p.src + kHdrBytes + (uint64_t)c * kEntryBytes + 12);
-    s_packed[t] = packed;
-    __syncthreads();
-    uint64_t poff = p.seg_prefix[s];
-    for (uint32_t k = c0; k < c; ++k)
-      poff += k < cb ? le32(p.src + kHdrBytes + (uint64_t)k * kEntryBytes + 12) : s_packed[k - cb];
-    __syncthreads();
-    if (!mine) continue;
-    const uint8_t *e = p.src + kHdrBytes + (uint64_t)c * kEntryBytes;
-    const uint64_t off = le64(e);
-    const uint32_t nrec = le32(e + 8);
-    const uint64_t end = c + 1 < g.n_chunks ? le64(e + kEntryBytes) : data_bytes;
-    uint8_t *out = p.P + p.p_data_off + poff;
-    bool bad = off > end || end > data_bytes || p.p_data_off + poff + packed > p.p_cap;
-    const uint64_t coded = bad ? 0 : end - off;
-    const uint8_t *in = p.src + g.data_off + off;
-    if (!bad && raw) {
-      bad = coded != packed;
-      if (!bad)
-        for (uint32_t k = 0; k < packed; ++k) out[k] = in[k];
-    } else if (!bad) {
-      // bit buffer, least significant bit first, refilled with aligned
-      // 32-bit loads (bytes only past the end of the buffer); symbols leave
-      // in 8-byte stores once the output is aligned
-      const uintptr_t ia = (uintptr_t)in;
-      const uint32_t *w32 = reinterpret_cast<const uint32_t *>(ia & ~(uintptr_t)3);
-      const uint32_t lead = (uint32_t)(ia & 3);  // bytes of the first word before the chunk
-      const uint64_t words = (coded + lead + 3) / 4;
-      const uintptr_t buf_end = (uintptr_t)p.src + p.src_size;
-      uint64_t buf = 0;
-      uint32_t have = 0;
-      uint64_t wi = 0;
-      uint64_t used = 0;  // bits consumed
-      auto refill = [&]() {
-        while (have <= 32 && wi < words) {
-          const uintptr_t a = (uintptr_t)(w32 + wi);
-          uint32_t v = 0;
-          if (a + 4 <= buf_end) {
-            v = __ldg(w32 + wi);
-          } else {
-            for (uint32_t q = 0; q < 4; ++q)
-              if (a + q < buf_end) v |= (uint32_t)*reinterpret_cast<const uint8_t *>(a + q) << (8 * q);
-          }
-          buf |= (uint64_t)v << have;
-          have += 32;
-          ++wi;
-        }
-      };
-      refill();
-      buf >>= 8 * lead;
-      have -= 8 * lead;
-      auto next = [&](uint32_t *sym) -> bool {
-        refill();
-        const uint32_t ent = lut[buf & ((1u << kHuffMaxLen) - 1)];
-        const uint32_t l = ent >> 8;
-        if (l == 0 || l > have) return false;
-        *sym = ent & 0xFFu;
-        buf >>= l;
-        have -= l;
-        used += l;
-        return true;
-      };
-      const uint32_t head = min((uint32_t)((8 - ((uintptr_t)out & 7)) & 7), packed);
-      uint32_t k = 0, sym = 0;
-      for (; k < head && !bad; ++k) {
-        if (!next(&sym)) bad = true;
-        else out[k] = (uint8_t)sym;
-      }
-      for (; k + 8 <= packed && !bad; k += 8) {
-        uint64_t o = 0;
-#pragma unroll
-        for (uint32_t q = 0; q < 8; ++q) {
-          if (!next(&sym)) bad = true;
-          o |= (uint64_t)sym << (8 * q);
-        }
-        if (!bad) *reinterpret_cast<uint64_t *>(out + k) = o;
-      }
-      for (; k < packed && !bad; ++k) {
-        if (!next(&sym)) bad = true;
-        else out[k] = (uint8_t)sym;
-      }
-      if (!bad && (used + 7) / 8 != coded) bad = true;
+  const uint64_t end = c + 1 < g.n_chunks ? le64(e + kEntryBytes) : data_bytes;
+  const uint64_t poff = p.seg_prefix[s] + p.chunk_poff[c];
+  bool bad = off > end || end > data_bytes || p.p_data_off + poff + packed > p.p_cap || n_sub > p.slots;
+  const uint64_t coded = bad ? 0 : end - off;
+  const uint8_t *in = p.src + g.data_off + off;
+  uint64_t i0;
+  uint32_t n;
+  huff_sub_range(packed, k, &i0, &n);
+  uint8_t *out = p.P + p.p_data_off + poff + i0;
+  if (!bad && raw) {
+    bad = coded != packed;
+    if (!bad)
+      for (uint32_t i = 0; i < n; ++i) out[i] = in[i0 + i];
+  } else if (!bad) {
+    const uint64_t jump = 4ull * (n_sub - 1);
+    bad = jump > coded;
+    if (!bad) {
+      const uint64_t span = coded - jump;
+      const uint64_t s0 = k ? le32(in + 4ull * (k - 1)) : 0;
+      const uint64_t s1 = k + 1 < n_sub ? le32(in + 4ull * k) : span;
+      bad = s0 > s1 || s1 > span;
+      if (!bad) bad = !huff_decode_sub(in + jump + s0, s1 - s0, n, out, lut, (uintptr_t)p.src + p.src_size);
     }
-    if (bad) {
-      set_status(p.status, SPRINTZ_ERR_CORRUPT);
-      continue;
-    }
+  }
+  if (bad) {
+    set_status(p.status, SPRINTZ_ERR_CORRUPT);
+    return;
+  }
+  if (k == 0) {
     uint8_t *pe = p.P + kHdrBytes + (uint64_t)c * kEntryBytes;
     put_le(pe, poff, 8);
     put_le(pe + 8, nrec, 4);
@@ -640,34 +894,39 @@ static uint64_t plain_cap(const Geom &g) {
   return total + g.tail_rows * g.D * g.wb;
 }
 
-struct HuffEncLayout {
-  uint64_t P, P_cap, size_word, coded, seg_total, seg_prefix, gbuf, gbuf_bytes, inner, inner_bytes, total;
-  uint64_t obytes;  // one chunk's code buffer
-  bool global_buf;  // the buffer lives in the workspace (too large for shared memory)
-};
-
-// Static shared memory of the Huffman encoder (its per-chunk code buffer is
-// dynamic shared memory on top of it).
-static uint64_t huff_encode_static_smem() {
-  cudaFuncAttributes a{};
-  if (cudaFuncGetAttributes(&a, k_huff_encode) != cudaSuccess) return 64 * 1024;
-  return a.sharedSizeBytes;
+// Sub-block slots per chunk: the sub-blocks of the largest possible body.
+static uint32_t huff_slots(const Geom &g) {
+  return (uint32_t)std::max<uint64_t>(1, (g.max_body + kHuffSub - 1) / kHuffSub);
 }
+
+constexpr uint64_t kHistSlice = 64 * 1024;  // packed bytes per histogram CTA
+
+struct HuffEncLayout {
+  uint64_t P, P_cap, size_word, hist, codes, seg_coded, seg_raw, seg_total, seg_prefix, chunk_coded, chunk_pos,
+      sub_off, inner, inner_bytes, total;
+  uint32_t slots, slices;
+};
 
 static HuffEncLayout huff_enc_layout(const Geom &g, const LaunchCfg &cfg) {
   HuffEncLayout L{};
   const Geom gp = plain_geom(g);
+  const uint64_t ns = g.n_segments, nc = g.n_chunks;
+  L.slots = huff_slots(g);
+  const uint64_t seg_chunks_max = std::min<uint64_t>(g.huff_chunks ? g.huff_chunks : 1, std::max<uint64_t>(nc, 1));
+  L.slices = (uint32_t)std::max<uint64_t>(1, (seg_chunks_max * g.max_body + kHistSlice - 1) / kHistSlice);
   L.P = 0;
   L.P_cap = plain_cap(gp);
-  L.size_word = a256(L.P_cap + 16);
-  L.coded = L.size_word + 256;
-  L.seg_total = a256(L.coded + 4ull * g.n_chunks);
-  L.seg_prefix = a256(L.seg_total + 8ull * g.n_segments);
-  L.obytes = ((g.max_body * kHuffMaxLen / 8 + 16) + 15) & ~15ull;
-  L.global_buf = L.obytes + huff_encode_static_smem() > (uint64_t)cfg.max_smem_optin;
-  L.gbuf = a256(L.seg_prefix + 8ull * (g.n_segments + 1));
-  L.gbuf_bytes = L.global_buf ? (uint64_t)g.n_segments * L.obytes : 0;
-  L.inner = a256(L.gbuf + L.gbuf_bytes);
+  L.size_word = a256(L.P_cap + 16);  // P keeps 16 bytes of slack for word reads past its end
+  L.hist = L.size_word + 256;
+  L.codes = a256(L.hist + 8 * 256 * ns);
+  L.seg_coded = a256(L.codes + 4 * 256 * ns);
+  L.seg_raw = a256(L.seg_coded + 8 * ns);
+  L.seg_total = a256(L.seg_raw + 4 * ns);
+  L.seg_prefix = a256(L.seg_total + 8 * ns);
+  L.chunk_coded = a256(L.seg_prefix + 8 * (ns + 1));
+  L.chunk_pos = a256(L.chunk_coded + 8 * nc);
+  L.sub_off = a256(L.chunk_pos + 8 * nc);
+  L.inner = a256(L.sub_off + 4 * nc * L.slots);
   L.inner_bytes = encode_workspace_bytes(gp, cfg);
   L.total = L.inner + L.inner_bytes;
   return L;
@@ -684,6 +943,9 @@ int launch_encode_huffman(const Geom &g, const LaunchCfg &cfg, const uint8_t *sr
   if (g.n_chunks == 0) return launch_encode(g, cfg, src, dst, dst_cap, d_out_size, ws, ws_bytes, d_status, stream);
   const HuffEncLayout L = huff_enc_layout(g, cfg);
   if (ws_bytes < L.total) return SPRINTZ_ERR_WS_TOO_SMALL;
+  const uint64_t hist_grid = (uint64_t)g.n_segments * L.slices;
+  const uint64_t enc_grid = ((uint64_t)g.n_chunks * L.slots + kHuffEncWarps - 1) / kHuffEncWarps;
+  if (hist_grid > 0x7FFFFFFFull || enc_grid > 0x7FFFFFFFull) return SPRINTZ_ERR_UNSUPPORTED;
   const Geom gp = plain_geom(g);
   uint8_t *P = ws + L.P;
   int rc = launch_encode_fast(gp, cfg, src, P, L.P_cap, reinterpret_cast<uint64_t *>(ws + L.size_word),
@@ -698,36 +960,55 @@ int launch_encode_huffman(const Geom &g, const LaunchCfg &cfg, const uint8_t *sr
   hp.status = d_status;
   hp.g = g;
   hp.p_data_off = gp.data_off;
-  hp.chunk_coded = reinterpret_cast<uint32_t *>(ws + L.coded);
+  hp.p_body_cap = L.P_cap - gp.data_off;
+  hp.slots = L.slots;
+  hp.slices = L.slices;
+  hp.slice_bytes = kHistSlice;
+  hp.hist = reinterpret_cast<unsigned long long *>(ws + L.hist);
+  hp.codes = reinterpret_cast<uint32_t *>(ws + L.codes);
+  hp.seg_coded = reinterpret_cast<unsigned long long *>(ws + L.seg_coded);
+  hp.seg_raw = reinterpret_cast<uint32_t *>(ws + L.seg_raw);
   hp.seg_total = reinterpret_cast<uint64_t *>(ws + L.seg_total);
   hp.seg_prefix = reinterpret_cast<uint64_t *>(ws + L.seg_prefix);
-  k_huff_build<<<g.n_segments, kHuffThreads, 0, stream>>>(hp);
+  hp.chunk_coded = reinterpret_cast<uint64_t *>(ws + L.chunk_coded);
+  hp.chunk_pos = reinterpret_cast<uint64_t *>(ws + L.chunk_pos);
+  hp.sub_off = reinterpret_cast<uint32_t *>(ws + L.sub_off);
+  if (cudaMemsetAsync(hp.hist, 0, 8ull * 256 * g.n_segments, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  k_huff_hist<<<(uint32_t)hist_grid, kHuffWarps * 32, 0, stream>>>(hp);
+  k_huff_lengths<<<g.n_segments, kHuffThreads, 0, stream>>>(hp);
+  k_huff_sizes<<<(g.n_chunks + kHuffWarps - 1) / kHuffWarps, kHuffWarps * 32, 0, stream>>>(hp);
+  k_huff_decide<<<g.n_segments, 256, 0, stream>>>(hp);
   k_huff_scan<<<1, 1024, 0, stream>>>(hp.seg_total, hp.seg_prefix, g.n_segments);
-  uint64_t obytes = L.obytes;
-  if (L.global_buf) {
-    hp.gbuf = reinterpret_cast<uint32_t *>(ws + L.gbuf);
-    hp.gbuf_words = L.obytes / 4;
-    obytes = 0;
-  } else if (cudaFuncSetAttribute(k_huff_encode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)obytes) !=
-             cudaSuccess) {
-    return SPRINTZ_ERR_CUDA;
-  }
-  k_huff_encode<<<g.n_segments, kHuffThreads, obytes, stream>>>(hp);
+  k_huff_encode<<<(uint32_t)enc_grid, kHuffEncWarps * 32, 0, stream>>>(hp);
+  k_huff_enc_finish<<<1, 256, 0, stream>>>(hp);
   return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
 }
 
 struct HuffDecLayout {
-  uint64_t P, P_cap, seg_packed, seg_prefix, inner, inner_bytes, total;
+  uint64_t P, P_cap, lut, seg_flags, seg_packed, seg_prefix, chunk_poff, chunk_sub0, seg_nsub, inner, inner_bytes,
+      total;
+  uint32_t slots, threads, parts;
 };
 
 static HuffDecLayout huff_dec_layout(const Geom &g, const LaunchCfg &cfg) {
   HuffDecLayout L{};
   const Geom gp = plain_geom(g);
+  const uint64_t ns = g.n_segments, nc = g.n_chunks;
+  L.slots = huff_slots(g);
+  const uint64_t seg_slots =
+      std::min<uint64_t>(g.huff_chunks ? g.huff_chunks : 1, std::max<uint64_t>(nc, 1)) * L.slots;
+  L.threads = (uint32_t)std::min<uint64_t>(kHuffDecThreads, (seg_slots + 31) & ~31ull);
+  L.parts = (uint32_t)((seg_slots + L.threads - 1) / L.threads);
   L.P = 0;
   L.P_cap = plain_cap(gp);
-  L.seg_packed = a256(L.P_cap + 16);
-  L.seg_prefix = a256(L.seg_packed + 8ull * g.n_segments);
-  L.inner = a256(L.seg_prefix + 8ull * (g.n_segments + 1));
+  L.lut = a256(L.P_cap + 16);
+  L.seg_flags = a256(L.lut + 2ull * kLutSize * ns);
+  L.seg_packed = a256(L.seg_flags + 4 * ns);
+  L.seg_prefix = a256(L.seg_packed + 8 * ns);
+  L.chunk_poff = a256(L.seg_prefix + 8 * (ns + 1));
+  L.chunk_sub0 = a256(L.chunk_poff + 8 * nc);
+  L.seg_nsub = a256(L.chunk_sub0 + 8 * nc);
+  L.inner = a256(L.seg_nsub + 8 * ns);
   L.inner_bytes = decode_workspace_bytes(gp, cfg);
   L.total = L.inner + L.inner_bytes;
   return L;
@@ -742,6 +1023,8 @@ int launch_decode_huffman(const Geom &g, const LaunchCfg &cfg, const uint8_t *sr
                           cudaStream_t stream) {
   const HuffDecLayout L = huff_dec_layout(g, cfg);
   if (ws_bytes < L.total) return SPRINTZ_ERR_WS_TOO_SMALL;
+  const uint64_t dec_grid = (uint64_t)g.n_segments * L.parts;
+  if (dec_grid > 0x7FFFFFFFull) return SPRINTZ_ERR_UNSUPPORTED;
   const Geom gp = plain_geom(g);
   HuffDecParams hp{};
   hp.src = src;
@@ -751,12 +1034,19 @@ int launch_decode_huffman(const Geom &g, const LaunchCfg &cfg, const uint8_t *sr
   hp.status = d_status;
   hp.g = g;
   hp.p_data_off = gp.data_off;
+  hp.slots = L.slots;
+  hp.parts = L.parts;
+  hp.lut = reinterpret_cast<uint16_t *>(ws + L.lut);
+  hp.seg_flags = reinterpret_cast<uint32_t *>(ws + L.seg_flags);
   hp.seg_packed = reinterpret_cast<uint64_t *>(ws + L.seg_packed);
   hp.seg_prefix = reinterpret_cast<uint64_t *>(ws + L.seg_prefix);
+  hp.chunk_poff = reinterpret_cast<uint64_t *>(ws + L.chunk_poff);
+  hp.chunk_sub0 = reinterpret_cast<uint64_t *>(ws + L.chunk_sub0);
+  hp.seg_nsub = reinterpret_cast<uint64_t *>(ws + L.seg_nsub);
   if (g.n_chunks) {
-    k_huff_seg_packed<<<(g.n_segments + 127) / 128, 128, 0, stream>>>(hp);
+    k_huff_dec_prep<<<g.n_segments, 256, 0, stream>>>(hp);
     k_huff_scan<<<1, 1024, 0, stream>>>(hp.seg_packed, hp.seg_prefix, g.n_segments);
-    k_huff_decode<<<g.n_segments, 64, 0, stream>>>(hp);
+    k_huff_decode<<<(uint32_t)dec_grid, L.threads, 0, stream>>>(hp);
   } else {
     cudaMemsetAsync(hp.seg_prefix, 0, 8, stream);
   }

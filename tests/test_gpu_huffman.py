@@ -63,8 +63,8 @@ def test_huffman_u16_and_wide(codec, oracle_mod):
 
 @pytest.mark.parametrize("w,D", [(8, 24), (8, 32), (16, 40), (16, 80), (16, 200)])
 def test_huffman_large_chunk_bodies(codec, oracle_mod, w, D):
-    """Chunk bodies whose code buffer needs more than 48 KB of shared memory,
-    or more than a CTA can have (then the buffer is in the workspace)."""
+    """Wide rows: a chunk body of up to 400 KB is coded as up to 200
+    sub-blocks of 2048 packed bytes behind its jump table."""
     from paper_1808_02515_gb300 import synth
     x = synth.uniform(2048 + 3, D, w, seed=D)
     _rt(codec, oracle_mod, x, huff_chunks=1)

@@ -5,6 +5,10 @@ Code lengths: Kraft inequality, the length limit, optimality against brute
 force over all length vectors on tiny alphabets, and equality with the cost
 of an unrestricted Huffman code (heapq construction) when the limit does not
 bind. Canonical codes: the worked example of RFC 1951 Sec. 3.2.2.
+Container: each chunk's code is split into n = ceil(packed / 2048) sub-blocks
+of ceil(packed / n) packed bytes behind a jump table of u32 offsets; a
+sub-block decoded on its own, with a bit-by-bit canonical decoder written
+here, must give its slice of the packed body and use exactly its bytes.
 """
 import heapq
 import itertools
@@ -16,6 +20,25 @@ import numpy as np
 import pytest
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "streams.json")
+SUB = 2048  # packed bytes per Huffman sub-block
+
+
+def _n_sub(packed):
+    return max(1, -(-packed // SUB))
+
+
+def _sub_slices(body):
+    """The n = ceil(len / 2048) equal slices (the last may be shorter)."""
+    n = _n_sub(len(body))
+    q = -(-len(body) // n)
+    return [body[min(len(body), k * q):min(len(body), (k + 1) * q)] for k in range(n)]
+
+
+def _chunk_coded(body, lengths):
+    """Coded bytes of one chunk: the jump table plus each sub-block's bits
+    rounded up to a byte."""
+    subs = _sub_slices(body)
+    return 4 * (len(subs) - 1) + sum(-(-sum(int(lengths[v]) for v in sb) // 8) for sb in subs)
 
 
 def test_rfc1951_canonical_example(oracle_mod):
@@ -180,7 +203,8 @@ def test_huffman_raw_segments(oracle_mod):
                                         ("walk", 16, 2)])
 def test_huffman_container_size_model(oracle_mod, kind, cr, hc):
     """From the Huffman-free stream: each segment's histogram -> code lengths
-    -> coded bytes = sum over chunks of ceil(bits / 8); the segment is stored
+    -> coded bytes = sum over chunks of the jump table plus ceil(bits / 8) per
+    sub-block; the segment is stored
     raw (all-zero table) iff that is not smaller than its packed bytes. The
     Huffman stream's size and tables must follow."""
     from paper_1808_02515_gb300 import synth
@@ -206,7 +230,7 @@ def test_huffman_container_size_model(oracle_mod, kind, cr, hc):
             for v in b:
                 freq[v] += 1
         lengths = oracle_mod.huff_code_lengths(freq, 11)
-        coded_bytes = sum(-(-sum(int(lengths[v]) for v in b) // 8) for b in seg)
+        coded_bytes = sum(_chunk_coded(b, lengths) for b in seg)
         packed = sum(len(b) for b in seg)
         raw = packed == 0 or coded_bytes >= packed
         want = bytes(128) if raw else bytes(int(lengths[2 * i]) | (int(lengths[2 * i + 1]) << 4)
@@ -214,3 +238,66 @@ def test_huffman_container_size_model(oracle_mod, kind, cr, hc):
         assert t == want, k
         expect_data += packed if raw else coded_bytes
     assert coded.size == plain.size + 128 * len(tables) + expect_data - sum(len(b) for b in bodies)
+
+
+def _canonical_decoder(lengths, codes):
+    """(length, code) -> symbol, for a decoder that reads one bit at a time,
+    each code's most significant bit first."""
+    return {(int(lengths[v]), int(codes[v])): v for v in range(256) if lengths[v]}
+
+
+def _decode_sub(data, n_sym, table):
+    out, bit, cur, ln = [], 0, 0, 0
+    while len(out) < n_sym:
+        assert bit < 8 * len(data), "sub-block code ran out"
+        cur = (cur << 1) | ((data[bit >> 3] >> (bit & 7)) & 1)
+        ln += 1
+        bit += 1
+        if (ln, cur) in table:
+            out.append(table[(ln, cur)])
+            cur = ln = 0
+        assert ln <= 11
+    return bytes(out), bit
+
+
+@pytest.mark.parametrize("cols,hc", [(4, 2), (7, 3)])
+def test_huffman_sub_blocks(oracle_mod, cols, hc):
+    """Chunks of 1024 u16 rows pack to several 2048-byte sub-blocks: parse
+    every coded body (jump table, then codes) and decode each sub-block alone."""
+    from paper_1808_02515_gb300 import synth
+    x = synth.sensor_u16(4096, cols, seed=5)
+    plain = oracle_mod.compress(x, forecaster=1, huffman=0)
+    coded = oracle_mod.compress(x, forecaster=1, huffman=1, huff_chunks=hc)
+    assert np.array_equal(oracle_mod.decompress(coded), x)
+    bodies = _bodies(plain)
+    tables = _tables(coded)
+    n_chunks = len(bodies)
+    data_off, tail_off = struct.unpack_from("<QQ", coded, 40)
+    multi = 0
+    for c, body in enumerate(bodies):
+        off = struct.unpack_from("<Q", coded, 64 + 16 * c)[0]
+        end = struct.unpack_from("<Q", coded, 64 + 16 * (c + 1))[0] if c + 1 < n_chunks else tail_off - data_off
+        chunk = bytes(coded[data_off + off: data_off + end])
+        t = tables[c // hc]
+        if not any(t):
+            assert chunk == body
+            continue
+        lengths = np.zeros(256, np.uint8)
+        for i in range(128):
+            lengths[2 * i], lengths[2 * i + 1] = t[i] & 15, t[i] >> 4
+        dec = _canonical_decoder(lengths, oracle_mod.huff_canonical(lengths))
+        subs = _sub_slices(body)
+        n = len(subs)
+        assert max(len(sb) for sb in subs) - min(len(sb) for sb in subs) < n
+        multi += n > 1
+        starts = [0] + [struct.unpack_from("<I", chunk, 4 * k)[0] for k in range(n - 1)]
+        span = len(chunk) - 4 * (n - 1)
+        bounds = starts + [span]
+        assert all(a <= b for a, b in zip(bounds, bounds[1:]))
+        for k in range(n):
+            sub = chunk[4 * (n - 1) + bounds[k]: 4 * (n - 1) + bounds[k + 1]]
+            want = subs[k]
+            got, bits = _decode_sub(sub, len(want), dec)
+            assert got == want, (c, k)
+            assert -(-bits // 8) == len(sub), (c, k)
+    assert multi > 0
