@@ -471,15 +471,23 @@ __global__ void __launch_bounds__(kHuffEncWarps * 32) k_huff_encode(HuffEncParam
   const uint64_t c64 = slot / p.slots;
   if (c64 >= g.n_chunks) return;
   const uint32_t c = (uint32_t)c64, k = (uint32_t)(slot % p.slots);
+  const uint32_t s = c / g.huff_chunks;
+  // every per-slot load issued at once (all in bounds for any slot); the
+  // segment's code table follows into shared memory
   uint64_t off;
   uint32_t nrec, packed;
   p_entry(p, c, &off, &nrec, &packed);
+  const bool raw = p.seg_raw[s] != 0;
+  const uint64_t seg_base = p.seg_prefix[s], chunk_base = p.chunk_pos[c], coded = p.chunk_coded[c];
+  const uint32_t start = p.sub_off[(uint64_t)c * p.slots + k];
+  const uint32_t *cs = p.codes + (uint64_t)s * 256;
+  uint32_t ce[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) ce[i] = cs[lane + 32 * i];
   const uint32_t n_sub = huff_n_sub(packed);
   if (k >= n_sub) return;
-  const uint32_t s = c / g.huff_chunks;
-  const bool raw = p.seg_raw[s] != 0;
-  const uint64_t cpos = p.seg_prefix[s] + p.chunk_pos[c];  // from data_off
-  const uint64_t ctotal = raw ? packed : p.chunk_coded[c];
+  const uint64_t cpos = seg_base + chunk_base;  // from data_off
+  const uint64_t ctotal = raw ? packed : coded;
   if (g.data_off + cpos + ctotal > p.dst_cap) {
     if (lane == 0) set_status(p.status, SPRINTZ_ERR_DST_TOO_SMALL);
     return;
@@ -500,14 +508,9 @@ __global__ void __launch_bounds__(kHuffEncWarps * 32) k_huff_encode(HuffEncParam
     return;
   }
   const uint32_t jump = 4 * (n_sub - 1);
-  const uint32_t start = p.sub_off[(uint64_t)c * p.slots + k];
   if (k > 0 && lane < 4) d[4 * (k - 1) + lane] = (uint8_t)((start - jump) >> (8 * lane));
-  const uint32_t *cs = p.codes + (uint64_t)s * 256;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const uint32_t e = cs[lane + 32 * i];
-    s_code[warp][lane + 32 * i] = (uint16_t)((e & 0x7FFu) | ((e >> 16) << 11));
-  }
+  for (int i = 0; i < 8; ++i) s_code[warp][lane + 32 * i] = (uint16_t)((ce[i] & 0x7FFu) | ((ce[i] >> 16) << 11));
   // the sub-block's bytes: aligned words from up to 3 bytes before it to up
   // to 3 bytes after it (P has slack after its last byte)
   const uint32_t lead = (uint32_t)((uintptr_t)in & 3);
@@ -630,6 +633,8 @@ struct HuffDecParams {
   uint64_t *chunk_poff;  // [n_chunks] packed offset of each chunk inside its segment
   uint64_t *chunk_sub0;  // [n_chunks] index of each chunk's first sub-block inside its segment
   uint64_t *seg_nsub;    // [n_segments] sub-blocks of each segment
+  uint64_t seg_slots;    // sub-block entries per segment in sub_map: huff_chunks * slots
+  uint64_t *sub_map;     // [n_segments][seg_slots] chunk << 32 | k of each sub-block
 };
 
 // Per segment: check its table (lengths <= 11, Kraft), build its 11-bit
@@ -694,10 +699,15 @@ __global__ void __launch_bounds__(256) k_huff_dec_prep(HuffDecParams p) {
     const uint64_t c = base + t;
     const uint32_t v = c < c1 ? le32(p.src + kHdrBytes + c * kEntryBytes + 12) : 0;
     const uint64_t excl = block_scan256(v, s_w, &s_carry);
-    const uint64_t sub0 = block_scan256(c < c1 ? huff_n_sub(v) : 0, s_w, &s_carry2);
+    const uint32_t ns = c < c1 ? huff_n_sub(v) : 0;
+    const uint64_t sub0 = block_scan256(ns, s_w, &s_carry2);
     if (c < c1) {
       p.chunk_poff[c] = excl;
       p.chunk_sub0[c] = sub0;
+      // a body larger than any valid one: its sub-blocks have no slots
+      if (ns > p.slots) set_status(p.status, SPRINTZ_ERR_CORRUPT);
+      uint64_t *m = p.sub_map + (uint64_t)s * p.seg_slots;
+      for (uint32_t k = 0; k < ns && sub0 + k < p.seg_slots; ++k) m[sub0 + k] = (c << 32) | k;
     }
   }
   if (t == 0) {
@@ -774,10 +784,10 @@ __device__ __forceinline__ bool huff_decode_sub(const uint8_t *in, uint64_t byte
 }
 
 // One thread per sub-block: CTA (segment, part) covers sub-blocks
-// [part * blockDim, (part + 1) * blockDim) of its segment; a binary search
-// over the chunks' first sub-block indices finds the thread's chunk.  Every
-// sub-block decodes into the Huffman-free stream P; the thread of sub-block
-// 0 writes the chunk's entry of P's table.
+// [part * blockDim, (part + 1) * blockDim) of its segment; the map built by
+// k_huff_dec_prep gives each its chunk and index.  Every sub-block decodes
+// into the Huffman-free stream P; the thread of sub-block 0 writes the
+// chunk's entry of P's table.
 __global__ void __launch_bounds__(kHuffDecThreads, 10) k_huff_decode(HuffDecParams p) {
   __shared__ __align__(16) uint16_t lut[kLutSize];
   const Geom &g = p.g;
@@ -791,21 +801,22 @@ __global__ void __launch_bounds__(kHuffDecThreads, 10) k_huff_decode(HuffDecPara
     for (uint32_t k = t; k < kLutSize / 2; k += blockDim.x) d32[k] = l32[k];
   }
   __syncthreads();
-  uint32_t c0, c1;
-  seg_chunks(g, s, &c0, &c1);
   const uint64_t j = (uint64_t)part * blockDim.x + t;
-  if (j >= p.seg_nsub[s]) return;
-  uint32_t lo = c0, hi = c1 - 1;  // the last chunk whose first sub-block is <= j
-  while (lo < hi) {
-    const uint32_t mid = lo + (hi - lo + 1) / 2;
-    if (p.chunk_sub0[mid] <= j) lo = mid;
-    else hi = mid - 1;
+  if (j >= p.seg_nsub[s] || j >= p.seg_slots) return;
+  const uint64_t m = p.sub_map[(uint64_t)s * p.seg_slots + j];
+  const uint32_t c = (uint32_t)(m >> 32), k = (uint32_t)m;
+  if (c >= g.n_chunks) {  // an entry a corrupt segment left unset
+    set_status(p.status, SPRINTZ_ERR_CORRUPT);
+    return;
   }
-  const uint32_t c = lo, k = (uint32_t)(j - p.chunk_sub0[c]);
   const uint8_t *e = p.src + kHdrBytes + (uint64_t)c * kEntryBytes;
   const uint64_t off = le64(e);
   const uint32_t nrec = le32(e + 8), packed = le32(e + 12);
   const uint32_t n_sub = huff_n_sub(packed);
+  if (k >= n_sub) {
+    set_status(p.status, SPRINTZ_ERR_CORRUPT);
+    return;
+  }
   const uint64_t tail_off = le64(p.src + 48);
   const uint64_t data_bytes = tail_off >= g.data_off && tail_off <= p.src_size ? tail_off - g.data_off : 0;
   const uint64_t end = c + 1 < g.n_chunks ? le64(e + kEntryBytes) : data_bytes;
@@ -985,8 +996,8 @@ int launch_encode_huffman(const Geom &g, const LaunchCfg &cfg, const uint8_t *sr
 }
 
 struct HuffDecLayout {
-  uint64_t P, P_cap, lut, seg_flags, seg_packed, seg_prefix, chunk_poff, chunk_sub0, seg_nsub, inner, inner_bytes,
-      total;
+  uint64_t P, P_cap, lut, seg_flags, seg_packed, seg_prefix, chunk_poff, chunk_sub0, seg_nsub, sub_map, inner,
+      inner_bytes, total, seg_slots;
   uint32_t slots, threads, parts;
 };
 
@@ -997,6 +1008,7 @@ static HuffDecLayout huff_dec_layout(const Geom &g, const LaunchCfg &cfg) {
   L.slots = huff_slots(g);
   const uint64_t seg_slots =
       std::min<uint64_t>(g.huff_chunks ? g.huff_chunks : 1, std::max<uint64_t>(nc, 1)) * L.slots;
+  L.seg_slots = seg_slots;
   L.threads = (uint32_t)std::min<uint64_t>(kHuffDecThreads, (seg_slots + 31) & ~31ull);
   L.parts = (uint32_t)((seg_slots + L.threads - 1) / L.threads);
   L.P = 0;
@@ -1008,7 +1020,8 @@ static HuffDecLayout huff_dec_layout(const Geom &g, const LaunchCfg &cfg) {
   L.chunk_poff = a256(L.seg_prefix + 8 * (ns + 1));
   L.chunk_sub0 = a256(L.chunk_poff + 8 * nc);
   L.seg_nsub = a256(L.chunk_sub0 + 8 * nc);
-  L.inner = a256(L.seg_nsub + 8 * ns);
+  L.sub_map = a256(L.seg_nsub + 8 * ns);
+  L.inner = a256(L.sub_map + 8 * ns * seg_slots);
   L.inner_bytes = decode_workspace_bytes(gp, cfg);
   L.total = L.inner + L.inner_bytes;
   return L;
@@ -1043,6 +1056,8 @@ int launch_decode_huffman(const Geom &g, const LaunchCfg &cfg, const uint8_t *sr
   hp.chunk_poff = reinterpret_cast<uint64_t *>(ws + L.chunk_poff);
   hp.chunk_sub0 = reinterpret_cast<uint64_t *>(ws + L.chunk_sub0);
   hp.seg_nsub = reinterpret_cast<uint64_t *>(ws + L.seg_nsub);
+  hp.seg_slots = L.seg_slots;
+  hp.sub_map = reinterpret_cast<uint64_t *>(ws + L.sub_map);
   if (g.n_chunks) {
     k_huff_dec_prep<<<g.n_segments, 256, 0, stream>>>(hp);
     k_huff_scan<<<1, 1024, 0, stream>>>(hp.seg_packed, hp.seg_prefix, g.n_segments);
