@@ -54,6 +54,18 @@ def test_max_size_matches_oracle(spz, oracle_mod, rows, D, w, opts):
         oracle_mod.max_compressed_size(rows, D, w, **full)
 
 
+def test_huffman_body_limit(spz, oracle_mod):
+    """With Huffman a chunk body may not exceed 2^31 bytes (its sub-block
+    offsets are u32): one chunk of 2^23 rows x 128 u16 columns (a 2 GiB body)
+    is valid plain and rejected with Huffman, by both sides alike."""
+    rows, D, w = 1 << 23, 128, 16
+    for huff in (0, 1):
+        o = dict(forecaster=1, huffman=huff, group_blocks=2, learn_shift=1, chunk_rows=0, huff_chunks=1)
+        ours = spz.max_compressed_size(rows, D, w, spz.Opts(**o))
+        assert ours == oracle_mod.max_compressed_size(rows, D, w, **o)
+        assert (ours == 0) == (huff == 1)
+
+
 def test_invalid_options_rejected(spz):
     bad = [dict(group_blocks=0), dict(group_blocks=9), dict(chunk_rows=12), dict(learn_shift=16),
            dict(forecaster=4), dict(huffman=1, huff_chunks=0)]
