@@ -51,6 +51,7 @@ def parse():
                              "quantize"])
     ap.add_argument("--streams", type=int, default=10_000, help="batch: number of streams")
     ap.add_argument("--huff-rows", type=int, default=1 << 28, help="huffman: rows of the accel series")
+    ap.add_argument("--e2e-lanes", type=int, default=4, help="end to end: steps in flight (streams)")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     return ap.parse_args()
 
@@ -289,11 +290,12 @@ def main():
         # End to end through the C ABI with pinned host buffers: every step
         # copies its input samples in, compresses, copies the stream out and
         # back in (a store/load round trip through the host), decompresses and
-        # copies the samples out.  Two lanes (each its own CUDA stream and
+        # copies the samples out.  Several lanes (each its own CUDA stream and
         # buffers) take steps in turn, so one step's copies overlap the
-        # other's kernels and the two copy directions overlap each other.
+        # others' kernels and the two copy directions overlap each other.
+        nl = max(1, args.e2e_lanes)
         lanes = []
-        for _ in range(2):
+        for _ in range(nl):
             lanes.append({
                 "s": torch.cuda.Stream(dev),
                 "xh": torch.from_numpy(x.view(np.int16)).pin_memory(),
@@ -316,28 +318,30 @@ def main():
                 codec.decompress_into(L["dst"], C, info, L["out"], L["wsd"], stream=L["s"])
                 L["yh"].copy_(L["out"], non_blocking=True)
 
-        for k in range(4):
-            e2e_step(lanes[k % 2])
+        for k in range(2 * nl):
+            e2e_step(lanes[k % nl])
         torch.cuda.synchronize()
         codec.check()
         if not torch.equal(lanes[0]["yh"], lanes[0]["xh"]):
             raise SystemExit("end-to-end round trip mismatch")
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        n_e2e = max(4, min(40, args.steps // 10)) // 2 * 2
+        n_e2e = max(2 * nl, min(40, args.steps // 10)) // nl * nl
         a.record(lanes[0]["s"])
-        lanes[1]["s"].wait_event(a)
+        for L in lanes[1:]:
+            L["s"].wait_event(a)
         for k in range(n_e2e):
-            e2e_step(lanes[k % 2])
-        done = torch.cuda.Event()
-        done.record(lanes[1]["s"])
-        lanes[0]["s"].wait_event(done)
+            e2e_step(lanes[k % nl])
+        for L in lanes[1:]:
+            done = torch.cuda.Event()
+            done.record(L["s"])
+            lanes[0]["s"].wait_event(done)
         b.record(lanes[0]["s"])
         torch.cuda.synchronize()
         e2e_ms = a.elapsed_time(b) / n_e2e
         e2e = {"value": world * U / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": U + C, "d2h_bytes_per_step": C + U,
                "ms_per_step": e2e_ms, "steps": n_e2e,
-               "pipelining": "two lanes (streams) take steps in turn"}
+               "pipelining": f"{nl} lanes (streams) take steps in turn"}
 
     if rank != 0:
         return
