@@ -153,6 +153,26 @@ def traffic_bytes(kernel: str):
     return None if k is None else k.get("dram_bytes_per_launch")
 
 
+def slowest_rank_ms(ms, dist, device):
+    """The job's time: the largest of the ranks' times (all ranks get it)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbs(bytes_per_rank, world, ms):
+    """Whole-job throughput: every rank's units over the slowest rank's time
+    (weak scaling: each rank encodes and decodes its own series)."""
+    return world * bytes_per_rank / (ms * 1e-3) / 1e9
+
+
+def rank_seed(rank):
+    """Each rank draws its own series (no data crosses ranks)."""
+    return SEED + rank
+
+
 def run_reference(args, rank, world):
     """The oracle timed on the host cores on a bounded sample of the workload."""
     if rank != 0:
@@ -215,7 +235,7 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
-    x = synth.sensor_u16(args.rows, COLS, seed=SEED + rank)
+    x = synth.sensor_u16(args.rows, COLS, seed=rank_seed(rank))
     U = x.nbytes
     xd = torch.from_numpy(x.view(np.int16)).to(dev)
     codec = spz.Codec(local)
@@ -275,13 +295,9 @@ def main():
         clk.mark(h0, time.monotonic())
     if dist:
         dist.barrier()
-    total_ms = t_start.elapsed_time(t_end)
     enc_ms = [e[0].elapsed_time(e[1]) for e in evs]
     dec_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    t = torch.tensor([total_ms], device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = slowest_rank_ms(t_start.elapsed_time(t_end), dist, dev)
     ms_step = total_ms / args.steps
 
     # end to end through the C ABI with host buffers (pinned), copies timed
@@ -338,7 +354,8 @@ def main():
         b.record(lanes[0]["s"])
         torch.cuda.synchronize()
         e2e_ms = a.elapsed_time(b) / n_e2e
-        e2e = {"value": world * U / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+        e2e_ms = slowest_rank_ms(e2e_ms, dist, dev)
+        e2e = {"value": job_gbs(U, world, e2e_ms), "unit": "GB/s",
                "h2d_bytes_per_step": U + C, "d2h_bytes_per_step": C + U,
                "ms_per_step": e2e_ms, "steps": n_e2e,
                "pipelining": f"{nl} lanes (streams) take steps in turn"}
@@ -355,7 +372,7 @@ def main():
     dom_bytes = dec_bytes if dom == "decode" else enc_bytes
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     line = {
-        "metric": METRIC, "value": world * U / (ms_step * 1e-3) / 1e9, "unit": "GB/s",
+        "metric": METRIC, "value": job_gbs(U, world, ms_step), "unit": "GB/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
         "data": "synthetic",
