@@ -1,24 +1,31 @@
 """Benchmark of the CUDA Sprintz codec on its headline workload.
 
-Workload (default): uint16, D = 8 columns, 2^24 rows (256 MiB) of the seeded
-sensor-like generator (two sinusoids + Gaussian noise + 5 % flat stretches),
-FIRE forecaster, bit packing + zero-block runs, chunk_rows 1024, G = 2.
-One step = one compress and one decompress of the whole series (the hot path
-in both directions), inputs resident in HBM. `value` is uncompressed GB/s of
-the round trip; per-direction GB/s and the dominant kernel's HBM roofline
-are reported beside it.
+Workload (default): the batch of 10,000 independent streams, rows
+log-uniform in [1e3, 1e6], D uniform in 1..16, even streams uint8 random
+walks and odd streams uint16 sensor-like series (about 18 GB), FIRE
+forecaster, bit packing + zero-block runs, chunk_rows 1024, G = 2.  One step
+= one batched compress and one batched decompress of every stream (the hot
+path in both directions, each one persistent launch with the schedule the
+library's autotuner picked during warm-up), inputs resident in HBM.
+`value` is uncompressed GB/s of the round trip over all ranks; per-direction
+GB/s, the delta forecaster, per-stream launches of the same work, the HBM
+roofline of both batched kernels, an end-to-end figure through host buffers
+and the CPU oracle on the host's cores are reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload batch|sensor|walk|huffman|serve|...]
 
-N > 1 runs under torchrun, one rank per GPU, each rank on its own copy of
-the workload (independent streams: weak scaling, no collective on the data
-path); the barrier-bracketed time is the max over ranks.
-`--impl reference` times the CPU oracle (the plain scalar C codec) on a
-bounded sample of the same workload.
+--gpus N > 1 starts N ranks (one per GPU) through torch.distributed.run
+unless it already runs under it; the 10,000 streams are split into N
+contiguous ranges of about equal bytes (no collective on the data path; the
+total work is fixed: strong scaling), and the barrier-bracketed time is the
+slowest rank's.  `--impl reference` times the CPU oracle (the plain scalar C
+codec) on all host cores, on a bounded sample of the same streams.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -33,27 +40,34 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "decompress and compress GB/s (uncompressed bytes) at 1 GB300 and % HBM roofline"
-WORKLOAD = "sensor_u16_D8_2^24rows_FIRE"
+N_STREAMS = 10_000
+WORKLOAD = "batch_10000_streams_rows_logU_1e3_1e6_D1-16_u8u16_FIRE"
+SENSOR_WORKLOAD = "sensor_u16_D8_2^24rows_FIRE"
 ROWS, COLS, SEED = 1 << 24, 8, 1
+NOMINAL_HBM_GBS = 8000.0
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--rows", type=int, default=ROWS)
+    ap.add_argument("--rows", type=int, default=ROWS, help="sensor: rows of the series")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="sensor",
-                    choices=["sensor", "walk", "batch", "huffman", "serve", "fire_speed", "dsweep", "gsweep",
+    ap.add_argument("--no-tune", action="store_true", help="batch: default schedules, no autotuner")
+    ap.add_argument("--no-per-stream", action="store_true", help="batch: skip the per-stream launches")
+    ap.add_argument("--no-delta", action="store_true", help="batch: skip the delta forecaster")
+    ap.add_argument("--workload", default="batch",
+                    choices=["batch", "sensor", "walk", "huffman", "serve", "fire_speed", "dsweep", "gsweep",
                              "quantize"])
-    ap.add_argument("--streams", type=int, default=10_000, help="batch: number of streams")
+    ap.add_argument("--streams", type=int, default=N_STREAMS, help="batch: number of streams")
     ap.add_argument("--huff-rows", type=int, default=1 << 28, help="huffman: rows of the accel series")
-    ap.add_argument("--e2e-lanes", type=int, default=4, help="end to end: steps in flight (streams)")
+    ap.add_argument("--e2e-lanes", type=int, default=4, help="end to end: CUDA streams taking slices in turn")
+    ap.add_argument("--e2e-slices", type=int, default=16, help="end to end: slices of the batch per step")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def opts_dict():
@@ -134,14 +148,13 @@ def traffic_bytes(kernel: str):
     (profiles/traffic.json), or None when the kernel sources changed since
     the counters were taken."""
     import hashlib
-    root = os.path.dirname(os.path.abspath(__file__))
-    path = os.path.join(root, "profiles", "traffic.json")
+    path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
     except Exception:
         return None
-    csrc = os.path.join(root, "paper_1808_02515_gb300", "csrc")
+    csrc = os.path.join(ROOT, "paper_1808_02515_gb300", "csrc")
     h = hashlib.sha256()
     for name in sorted(os.listdir(csrc)):
         if name.endswith((".cu", ".cuh")):
@@ -163,67 +176,209 @@ def slowest_rank_ms(ms, dist, device):
 
 
 def job_gbs(bytes_per_rank, world, ms):
-    """Whole-job throughput: every rank's units over the slowest rank's time
-    (weak scaling: each rank encodes and decodes its own series)."""
+    """Whole-job throughput when every rank moves the same bytes."""
     return world * bytes_per_rank / (ms * 1e-3) / 1e9
 
 
+def total_gbs(total_bytes, ms):
+    """Whole-job throughput: all ranks' bytes over the slowest rank's time."""
+    return total_bytes / (ms * 1e-3) / 1e9
+
+
 def rank_seed(rank):
-    """Each rank draws its own series (no data crosses ranks)."""
+    """Single-stream workload: each rank draws its own series."""
     return SEED + rank
 
 
+def rank_streams(rank, world, n_streams=N_STREAMS):
+    """This rank's contiguous range of the batch's stream ids (byte-balanced)."""
+    from paper_1808_02515_gb300 import shard, synth
+    shapes = [synth.batch_stream_shape(i) for i in range(n_streams)]
+    nbytes = [r * d * (w // 8) for r, d, w in shapes]
+    lo, hi = shard.partition_streams(nbytes, world)[rank]
+    return list(range(lo, hi)), shapes, nbytes
+
+
+def launch_ranks(args) -> bool:
+    """--gpus N > 1 outside torch.distributed.run: start N ranks through it
+    (this process waits and returns its exit code). False when nothing was
+    started (one GPU, or already a rank)."""
+    if args.gpus <= 1 or "RANK" in os.environ:
+        return False
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *sys.argv[1:]]
+    raise SystemExit(subprocess.call(cmd))
+
+
+class Cudart:
+    """cudaMemcpyAsync from the CUDA runtime torch loaded (one call per
+    compressed stream in the end-to-end figure: torch's per-call overhead
+    would dominate 20,000 small copies a step)."""
+
+    H2D, D2H = 1, 2
+
+    def __init__(self):
+        import torch  # noqa: F401  (loads the runtime)
+        lib = None
+        for name in ("libcudart.so.13", "libcudart.so", "/usr/local/cuda/lib64/libcudart.so"):
+            try:
+                lib = ctypes.CDLL(name)
+                break
+            except OSError:
+                continue
+        if lib is None:
+            raise RuntimeError("CUDA runtime library not found")
+        lib.cudaMemcpyAsync.restype = ctypes.c_int
+        lib.cudaMemcpyAsync.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                        ctypes.c_void_p]
+        self.lib = lib
+
+    def copy(self, dst: int, src: int, n: int, kind: int, stream) -> None:
+        rc = self.lib.cudaMemcpyAsync(dst, src, n, kind, stream)
+        if rc != 0:
+            raise RuntimeError(f"cudaMemcpyAsync failed ({rc})")
+
+
+def oracle_sample(ids, every):
+    """Every `every`-th of the given stream ids (at least one)."""
+    s = ids[::max(1, every)]
+    return s if s else ids[:1]
+
+
 def run_reference(args, rank, world):
-    """The oracle timed on the host cores on a bounded sample of the workload."""
+    """The oracle, timed on the host cores (all of them, one stream per
+    thread) on a bounded sample of the workload's streams: each step
+    compresses and decompresses every sampled stream (FIRE)."""
     if rank != 0:
         return
     import oracle
     from paper_1808_02515_gb300 import synth
     oracle.build()
-    sample_rows = 1 << 20
-    x = synth.sensor_u16(sample_rows, COLS, seed=SEED)
+    every = getattr(args, "ref_every", 200)
+    ids = oracle_sample(list(range(N_STREAMS)), every)
+    xs = oracle.map_streams(synth.batch_stream, ids)
+    U = sum(x.nbytes for x in xs)
     o = opts_dict()
+    cores = oracle.host_cores()
+
+    def step():
+        oracle.decompress_many(oracle.compress_many(xs, o, cores), cores)
+
     for _ in range(max(0, min(args.warmup, 1))):
-        oracle.decompress(oracle.compress(x, **o))
+        step()
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        s = oracle.compress(x, **o)
-        oracle.decompress(s)
+        step()
         times.append(time.perf_counter() - t0)
     t = sum(times) / len(times)
-    val = x.nbytes / t / 1e9
+    val = U / t / 1e9
+    sample = (f"{len(ids)} of the {N_STREAMS} streams (every {every}th, {U / 1e6:.0f} MB), "
+              f"compress + decompress per step, one stream per thread")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u16", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "step": "compress+decompress round trip",
-                       "sample_rows": sample_rows},
-            "cpu_baseline": {"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {sample_rows} rows of the workload, single thread"},
-            "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "u8/u16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": "compress + decompress round trip (FIRE)",
+                       "sample_streams": len(ids), "sample_bytes": U},
+            "cpu_baseline": {"value": val, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def main():
-    args = parse()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        run_reference(args, rank, world)
-        return
-    if args.workload != "sensor":
-        from paper_1808_02515_gb300 import bench_workloads
-        bench_workloads.run(args, METRIC, ClockSampler, peaks)
-        return
+def cpu_baseline(xs_host, every_one=10):
+    """The oracle on the host cores: all cores over the given streams, one
+    core over every `every_one`-th of them (compress + decompress, FIRE)."""
+    import oracle
+    oracle.build()
+    o = opts_dict()
+    cores = oracle.host_cores()
+    res = {}
+    for label, xs, threads in (("all", xs_host, cores), ("one", oracle_sample(xs_host, every_one), 1)):
+        U = sum(x.nbytes for x in xs)
+        t0 = time.perf_counter()
+        oracle.decompress_many(oracle.compress_many(xs, o, threads), threads)
+        t = time.perf_counter() - t0
+        res[label] = (U / t / 1e9, len(xs), U, threads)
+    v, n, U, c = res["all"]
+    v1, n1, U1, _ = res["one"]
+    return {"value": v, "unit": "GB/s", "cores": c, "kind": "oracle",
+            "sample": f"{n} of the streams ({U / 1e6:.0f} MB), one compress + decompress each, "
+                      "one stream per thread",
+            "single_core": {"value": v1, "unit": "GB/s", "cores": 1,
+                            "sample": f"{n1} streams ({U1 / 1e6:.0f} MB)"}}
 
+
+def _aligned_offsets(sizes, align=256):
+    offs, o = [], 0
+    for n in sizes:
+        offs.append(o)
+        o += (int(n) + align - 1) // align * align
+    return offs, max(o, align)
+
+
+class BatchWorkload:
+    """This rank's streams on the device, laid out in `n_slices` contiguous
+    slices (each slice one buffer: inputs, outputs and stream buffers alike),
+    so that a slice moves to or from the host in one copy."""
+
+    def __init__(self, ids, shapes, nbytes, n_slices, dev, spz, synth, torch):
+        from paper_1808_02515_gb300 import shard
+        self.ids = ids
+        self.dev = dev
+        n = len(ids)
+        self.slices = [s for s in shard.partition_streams([nbytes[i] for i in ids], max(1, min(n_slices, n)))
+                       if s[1] > s[0]]
+        o = spz.Opts(**opts_dict())
+        self.xs, self.outs, self.bufs = [None] * n, [None] * n, [None] * n
+        self.in_bufs, self.out_bufs, self.st_bufs = [], [], []
+        self.view = []  # per slice: (byte offsets in the sample buffers, in the stream buffer)
+        t0 = time.perf_counter()
+        for a, b in self.slices:
+            sz = [nbytes[ids[k]] for k in range(a, b)]
+            offs, tot = _aligned_offsets(sz)
+            caps = [spz.max_compressed_size(*shapes[ids[k]], o) for k in range(a, b)]
+            coffs, ctot = _aligned_offsets(caps)
+            xin = torch.zeros(tot, dtype=torch.uint8, device=dev)
+            xout = torch.zeros(tot, dtype=torch.uint8, device=dev)
+            st = torch.empty(ctot, dtype=torch.uint8, device=dev)
+            for k in range(a, b):
+                rows, D, w = shapes[ids[k]]
+                dt = torch.uint8 if w == 8 else torch.int16
+                lo, nb = offs[k - a], sz[k - a]
+                v = xin[lo:lo + nb].view(dt).view(rows, D)
+                v.copy_(synth.batch_stream_torch(ids[k], device=dev))
+                self.xs[k] = v
+                self.outs[k] = xout[lo:lo + nb].view(dt).view(rows, D)
+                self.bufs[k] = st[coffs[k - a]:coffs[k - a] + caps[k - a]]
+            self.in_bufs.append(xin)
+            self.out_bufs.append(xout)
+            self.st_bufs.append(st)
+            self.view.append((offs, coffs))
+        torch.cuda.synchronize()
+        self.gen_s = time.perf_counter() - t0
+        self.U = sum(nbytes[i] for i in ids)
+        self.chunks = sum(-(-(shapes[i][0] - shapes[i][0] % 8) // 1024) if shapes[i][0] >= 8 else 0 for i in ids)
+
+    def outputs_equal_inputs(self, torch):
+        return all(torch.equal(a, b) for a, b in zip(self.in_bufs, self.out_bufs))
+
+
+def _headers(bufs, torch):
+    """Host copies of every stream's 64-byte header (one gather, one copy)."""
+    return torch.stack([b[:64] for b in bufs]).cpu().numpy()
+
+
+def run_batch(args, rank, world, local):
     import torch
     import paper_1808_02515_gb300.sprintz as spz
     from paper_1808_02515_gb300 import _build, synth
 
-    if rank == 0 or world == 1:
+    if rank == 0:
         _build.build()
     dist = None
     if world > 1:
@@ -234,181 +389,305 @@ def main():
         _build.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-
-    x = synth.sensor_u16(args.rows, COLS, seed=rank_seed(rank))
-    U = x.nbytes
-    xd = torch.from_numpy(x.view(np.int16)).to(dev)
-    codec = spz.Codec(local)
-    o = spz.Opts(**opts_dict())
-    rows, D, w = args.rows, COLS, 16
-    cap = spz.max_compressed_size(rows, D, w, o)
-    dst = torch.empty(cap, dtype=torch.uint8, device=dev)
-    size = torch.zeros(1, dtype=torch.int64, device=dev)
-    wsc = spz.compress_workspace_size(rows, D, w, o)
-    ws_c = torch.empty(max(wsc, 1), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    # one call to learn the stream's header and size
-    codec.compress_into(xd, rows, D, w, o, dst, size, ws_c)
-    torch.cuda.synchronize()
-    codec.check()
-    C = int(size.item())
-    info = spz.query(dst[:64].cpu().numpy().tobytes())
-    wsd = spz.decompress_workspace_size(info)
-    ws_d = torch.empty(max(wsd, 1), dtype=torch.uint8, device=dev)
-    out = torch.empty((rows, D), dtype=torch.int16, device=dev)
+    ids, shapes, nbytes = rank_streams(rank, world, args.streams)
+    wl = BatchWorkload(ids, shapes, nbytes, args.e2e_slices, dev, spz, synth, torch)
+    U_total = sum(nbytes[:args.streams])
+    tune = not args.no_tune
 
-    def step(ev=None):
-        if ev is not None:
-            ev[0].record(stream)
-        codec.compress_into(xd, rows, D, w, o, dst, size, ws_c)
-        if ev is not None:
-            ev[1].record(stream)
-        codec.decompress_into(dst, C, info, out, ws_d)
-        if ev is not None:
-            ev[2].record(stream)
-
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        for _ in range(args.warmup):
-            step()
+    def plans(fc, label):
+        o = spz.Opts(**{**opts_dict(), "forecaster": fc})
+        cc, cd = spz.Codec(local), spz.Codec(local)
+        sizes = torch.zeros(len(ids), dtype=torch.int64, device=dev)
+        _, _, ws_c = cc.compress_batch(wl.xs, o, autotune=tune, bufs=wl.bufs, sizes=sizes)
+        tc = cc.last_tune if tune else (cc.batch_schedule(), None)
         torch.cuda.synchronize()
-        # keep the GPU busy until the clock sampler delivers (at most 2 s)
+        cc.check()
+        sz = [int(v) for v in sizes.cpu().numpy()]
+        infos = [spz.query(h.tobytes()) for h in _headers(wl.bufs, torch)]
+        _, ws_d = cd.decompress_batch(wl.bufs, infos, sz, autotune=tune, outs=wl.outs)
+        td = cd.last_tune if tune else (cd.batch_schedule(), None)
+        torch.cuda.synchronize()
+        cd.check()
+        if not wl.outputs_equal_inputs(torch):
+            raise SystemExit(f"batched round trip mismatch ({label})")
+        sched = {"compress": {**vars(tc[0]), "tune_ms": tc[1]}, "decompress": {**vars(td[0]), "tune_ms": td[1]}}
+        return dict(o=o, cc=cc, cd=cd, ws_c=ws_c, ws_d=ws_d, sizes=sizes, sz=sz, infos=infos, sched=sched,
+                    C=sum(sz))
+
+    def timed(P, steps, evs=None):
+        """Mean compress and decompress ms per step over `steps` steps."""
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        for k in range(steps):
+            ev[k][0].record(stream)
+            P["cc"].batch_run(P["ws_c"])
+            ev[k][1].record(stream)
+            P["cd"].batch_run(P["ws_d"])
+            ev[k][2].record(stream)
+        torch.cuda.synchronize()
+        return (statistics.mean(e[0].elapsed_time(e[1]) for e in ev),
+                statistics.mean(e[1].elapsed_time(e[2]) for e in ev))
+
+    F = plans(1, "FIRE")
+    with ClockSampler(local) as clk:
+        timed(F, max(1, args.warmup))
         t_w = time.monotonic()
         while not clk.lines and time.monotonic() - t_w < 2.0:
-            step()
-            torch.cuda.synchronize()
-        codec.check()
-        if not torch.equal(out, xd):
-            raise SystemExit("round trip mismatch")
+            timed(F, 1)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         h0 = time.monotonic()
-        t_start.record(stream)
-        for k in range(args.steps):
-            step(evs[k])
-        t_end.record(stream)
+        a.record(stream)
+        enc_ms, dec_ms = timed(F, args.steps)
+        b.record(stream)
         torch.cuda.synchronize()
         clk.mark(h0, time.monotonic())
     if dist:
         dist.barrier()
-    enc_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    dec_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    total_ms = slowest_rank_ms(t_start.elapsed_time(t_end), dist, dev)
+    total_ms = slowest_rank_ms(a.elapsed_time(b), dist, dev)
     ms_step = total_ms / args.steps
+    F["cc"].check()
+    F["cd"].check()
+    if not wl.outputs_equal_inputs(torch):
+        raise SystemExit("batched round trip mismatch after the timed steps")
+    res = {"enc_ms": enc_ms, "dec_ms": dec_ms}
 
-    # end to end through the C ABI with host buffers (pinned), copies timed
-    e2e = None
-    if not args.no_e2e:
-        # End to end through the C ABI with pinned host buffers: every step
-        # copies its input samples in, compresses, copies the stream out and
-        # back in (a store/load round trip through the host), decompresses and
-        # copies the samples out.  Several lanes (each its own CUDA stream and
-        # buffers) take steps in turn, so one step's copies overlap the
-        # others' kernels and the two copy directions overlap each other.
-        nl = max(1, args.e2e_lanes)
-        lanes = []
-        for _ in range(nl):
-            lanes.append({
-                "s": torch.cuda.Stream(dev),
-                "xh": torch.from_numpy(x.view(np.int16)).pin_memory(),
-                "sh": torch.empty(cap, dtype=torch.uint8).pin_memory(),
-                "yh": torch.empty((rows, D), dtype=torch.int16).pin_memory(),
-                "xin": torch.empty_like(xd),
-                "dst": torch.empty(cap, dtype=torch.uint8, device=dev),
-                "size": torch.zeros(1, dtype=torch.int64, device=dev),
-                "wsc": torch.empty(max(wsc, 1), dtype=torch.uint8, device=dev),
-                "wsd": torch.empty(max(wsd, 1), dtype=torch.uint8, device=dev),
-                "out": torch.empty((rows, D), dtype=torch.int16, device=dev),
-            })
+    # per-stream launches of the same work (one context, one shared workspace)
+    per_stream = None
+    if not args.no_per_stream:
+        o = F["o"]
+        codec = spz.Codec(local)
+        shp = [shapes[i] for i in ids]
+        ws_e = torch.empty(max(max(spz.compress_workspace_size(r, d, w, o) for r, d, w in shp), 1),
+                           dtype=torch.uint8, device=dev)
+        ws_dd = torch.empty(max(max(spz.decompress_workspace_size(i) for i in F["infos"]), 1),
+                            dtype=torch.uint8, device=dev)
 
-        def e2e_step(L):
-            with torch.cuda.stream(L["s"]):
-                L["xin"].copy_(L["xh"], non_blocking=True)
-                codec.compress_into(L["xin"], rows, D, w, o, L["dst"], L["size"], L["wsc"], stream=L["s"])
-                L["sh"][:C].copy_(L["dst"][:C], non_blocking=True)
-                L["dst"][:C].copy_(L["sh"][:C], non_blocking=True)
-                codec.decompress_into(L["dst"], C, info, L["out"], L["wsd"], stream=L["s"])
-                L["yh"].copy_(L["out"], non_blocking=True)
+        def per_enc():
+            for k, x in enumerate(wl.xs):
+                r, d, w = shp[k]
+                codec.compress_into(x, r, d, w, o, wl.bufs[k], F["sizes"][k:k + 1], ws_e)
 
-        for k in range(2 * nl):
-            e2e_step(lanes[k % nl])
+        def per_dec():
+            for k in range(len(ids)):
+                codec.decompress_into(wl.bufs[k], F["sz"][k], F["infos"][k], wl.outs[k], ws_dd)
+
+        per_enc()
+        per_dec()
         torch.cuda.synchronize()
         codec.check()
-        if not torch.equal(lanes[0]["yh"], lanes[0]["xh"]):
-            raise SystemExit("end-to-end round trip mismatch")
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        n_e2e = max(2 * nl, min(40, args.steps // 10)) // nl * nl
-        a.record(lanes[0]["s"])
-        for L in lanes[1:]:
-            L["s"].wait_event(a)
-        for k in range(n_e2e):
-            e2e_step(lanes[k % nl])
-        for L in lanes[1:]:
-            done = torch.cuda.Event()
-            done.record(L["s"])
-            lanes[0]["s"].wait_event(done)
-        b.record(lanes[0]["s"])
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        per_enc()
+        ev[1].record(stream)
+        per_dec()
+        ev[2].record(stream)
         torch.cuda.synchronize()
-        e2e_ms = a.elapsed_time(b) / n_e2e
-        e2e_ms = slowest_rank_ms(e2e_ms, dist, dev)
-        e2e = {"value": job_gbs(U, world, e2e_ms), "unit": "GB/s",
-               "h2d_bytes_per_step": U + C, "d2h_bytes_per_step": C + U,
-               "ms_per_step": e2e_ms, "steps": n_e2e,
-               "pipelining": f"{nl} lanes (streams) take steps in turn"}
+        codec.check()
+        if not wl.outputs_equal_inputs(torch):
+            raise SystemExit("per-stream round trip mismatch")
+        pe, pd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        per_stream = {"compress_gbs": wl.U / (pe * 1e-3) / 1e9, "decompress_gbs": wl.U / (pd * 1e-3) / 1e9,
+                      "compress_ms": pe, "decompress_ms": pd,
+                      "launches": "one sprintz_compress / sprintz_decompress call per stream, one CUDA stream"}
+        codec.close()
 
+    # end to end through the public API with host buffers: every step copies
+    # each slice's samples in (one copy), compresses it, copies every stream's
+    # compressed bytes out and back in (one copy per stream), decompresses
+    # and copies the samples out (one copy) into the same pinned host buffer
+    # they came from (the round trip is lossless, so every step's input is
+    # again the workload).  Slices take CUDA streams in turn, so one slice's
+    # copies overlap another's kernels and the two directions overlap.
+    e2e = None
+    if not args.no_e2e:
+        cr = Cudart()
+        lib = cr.lib
+        lib.cudaHostRegister.restype = ctypes.c_int
+        lib.cudaHostRegister.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint]
+        lib.cudaHostUnregister.restype = ctypes.c_int
+        lib.cudaHostUnregister.argtypes = [ctypes.c_void_p]
+        in_sizes = [t.numel() for t in wl.in_bufs]
+        h_off, h_tot = _aligned_offsets(in_sizes, 4096)
+        c_off, c_tot = _aligned_offsets(F["sz"], 256)
+        hin = np.empty(h_tot, dtype=np.uint8)
+        hc = np.empty(c_tot, dtype=np.uint8)
+        for arr in (hin, hc):
+            if lib.cudaHostRegister(arr.ctypes.data, arr.nbytes, 0) != 0:
+                raise SystemExit("cudaHostRegister failed")
+        try:
+            for s_i, t in enumerate(wl.in_bufs):
+                cr.copy(hin.ctypes.data + h_off[s_i], t.data_ptr(), t.numel(), Cudart.D2H,
+                        stream.cuda_stream)
+            torch.cuda.synchronize()
+            nl = max(1, args.e2e_lanes)
+            lanes = [torch.cuda.Stream(dev) for _ in range(nl)]
+            sc = spz.Schedule(**{k: v for k, v in F["sched"]["compress"].items() if k != "tune_ms"})
+            sd = spz.Schedule(**{k: v for k, v in F["sched"]["decompress"].items() if k != "tune_ms"})
+            sl = []
+            for s_i, (lo, hi) in enumerate(wl.slices):
+                ls = lanes[s_i % nl]
+                cc, cd = spz.Codec(local), spz.Codec(local)
+                sizes = F["sizes"][lo:hi]
+                _, _, wsc = cc.compress_batch(wl.xs[lo:hi], F["o"], stream=ls, schedule=sc, bufs=wl.bufs[lo:hi],
+                                              sizes=sizes)
+                _, wsd = cd.decompress_batch(wl.bufs[lo:hi], F["infos"][lo:hi], F["sz"][lo:hi], stream=ls,
+                                             schedule=sd, outs=wl.outs[lo:hi])
+                sl.append((ls, cc, cd, wsc, wsd, lo, hi))
+            torch.cuda.synchronize()
+
+            def e2e_step():
+                for s_i, (ls, cc, cd, wsc, wsd, lo, hi) in enumerate(sl):
+                    sp = ls.cuda_stream
+                    cr.copy(wl.in_bufs[s_i].data_ptr(), hin.ctypes.data + h_off[s_i], in_sizes[s_i], Cudart.H2D, sp)
+                    cc.batch_run(wsc, stream=ls)
+                    for k in range(lo, hi):
+                        cr.copy(hc.ctypes.data + c_off[k], wl.bufs[k].data_ptr(), F["sz"][k], Cudart.D2H, sp)
+                    for k in range(lo, hi):
+                        cr.copy(wl.bufs[k].data_ptr(), hc.ctypes.data + c_off[k], F["sz"][k], Cudart.H2D, sp)
+                    cd.batch_run(wsd, stream=ls)
+                    cr.copy(hin.ctypes.data + h_off[s_i], wl.out_bufs[s_i].data_ptr(), in_sizes[s_i], Cudart.D2H, sp)
+
+            e2e_step()
+            torch.cuda.synchronize()
+            a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            n_e2e = 3
+            a2.record(lanes[0])
+            for ls in lanes[1:]:
+                ls.wait_event(a2)
+            for _ in range(n_e2e):
+                e2e_step()
+            for ls in lanes[1:]:
+                done = torch.cuda.Event()
+                done.record(ls)
+                lanes[0].wait_event(done)
+            b2.record(lanes[0])
+            torch.cuda.synchronize()
+            for _, cc, cd, *_ in sl:
+                cc.check()
+                cd.check()
+            ok = all(torch.equal(torch.from_numpy(hin[h_off[s_i]:h_off[s_i] + in_sizes[s_i]]).to(dev), t)
+                     for s_i, t in enumerate(wl.in_bufs))
+            if not ok:
+                raise SystemExit("end-to-end round trip mismatch")
+            e2e_ms = slowest_rank_ms(a2.elapsed_time(b2) / n_e2e, dist, dev)
+            e2e = {"value": total_gbs(U_total, e2e_ms), "unit": "GB/s",
+                   "h2d_bytes_per_step": sum(in_sizes) + F["C"], "d2h_bytes_per_step": F["C"] + sum(in_sizes),
+                   "ms_per_step": e2e_ms, "steps": n_e2e,
+                   "pipelining": f"{len(sl)} slices on {nl} CUDA streams; pinned host buffers; "
+                                 "one copy per slice for samples, one per stream for compressed bytes"}
+            for _, cc, cd, *_ in sl:
+                cc.close()
+                cd.close()
+        finally:
+            lib.cudaHostUnregister(hin.ctypes.data)
+            lib.cudaHostUnregister(hc.ctypes.data)
+
+    # the delta forecaster (its own autotuned plans; overwrites the stream buffers)
+    delta = None
+    if not args.no_delta:
+        Dl = plans(0, "delta")
+        de, dd = timed(Dl, max(1, min(args.steps, 10)))
+        delta = {"compress_gbs": wl.U / (de * 1e-3) / 1e9, "decompress_gbs": wl.U / (dd * 1e-3) / 1e9,
+                 "compress_ms": de, "decompress_ms": dd, "compressed_bytes": Dl["C"], "ratio": wl.U / Dl["C"],
+                 "schedules": Dl["sched"]}
+        Dl["cc"].close()
+        Dl["cd"].close()
+
+    C_total = F["C"]
+    chunks_total = wl.chunks
+    if dist:
+        t = torch.tensor([F["C"], wl.chunks], dtype=torch.int64, device=dev)
+        dist.all_reduce(t)
+        C_total, chunks_total = int(t[0].item()), int(t[1].item())
+    enc_max = slowest_rank_ms(enc_ms, dist, dev)
+    dec_max = slowest_rank_ms(dec_ms, dist, dev)
     if rank != 0:
+        F["cc"].close()
+        F["cd"].close()
         return
-    enc_avg, dec_avg = statistics.mean(enc_ms), statistics.mean(dec_ms)
     peak, peak_kind = peaks()
-    table = 16 * info.n_chunks
-    enc_bytes, dec_bytes = U + C + table, C + U
-    dom = "decode" if dec_avg >= enc_avg else "encode"
-    dom_kernel = "k_decode_lanes" if dom == "decode" else "k_encode_slots"
-    dom_ms = dec_avg if dom == "decode" else enc_avg
-    dom_bytes = dec_bytes if dom == "decode" else enc_bytes
-    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    enc_bytes = U_total + C_total + 16 * chunks_total
+    dec_bytes = U_total + C_total
+    enc_ach = enc_bytes / (enc_max * 1e-3) / 1e9
+    dec_ach = dec_bytes / (dec_max * 1e-3) / 1e9
+    dom = "encode" if enc_max >= dec_max else "decode"
+    kern = "k_encode_batch" if dom == "encode" else "k_decode_batch"
+    ach = enc_ach if dom == "encode" else dec_ach
     line = {
-        "metric": METRIC, "value": job_gbs(U, world, ms_step), "unit": "GB/s",
+        "metric": METRIC, "value": total_gbs(U_total, ms_step), "unit": "GB/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u8/u16",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "rows": rows, "D": D, "w": w, **opts_dict(),
-                   "step": "compress+decompress round trip", "uncompressed_bytes": U,
-                   "compressed_bytes": C, "ratio": U / C,
-                   "l2": "inputs (256 MiB raw, compressed stream) larger than the 129 MB L2",
-                   "parallelism": f"{world} independent streams (one per GPU)"},
-        "decompress_gbs": U / (dec_avg * 1e-3) / 1e9,
-        "compress_gbs": U / (enc_avg * 1e-3) / 1e9,
-        "decompress_ms": dec_avg, "compress_ms": enc_avg,
-        "roofline": {"bound": "hbm", "kernel": dom_kernel,
-                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic_bytes(dom_kernel),
-                     "algorithmic_bytes_per_launch": dom_bytes,
-                     "decode_frac": dec_bytes / (dec_avg * 1e-3) / 1e9 / peak,
-                     "encode_frac": enc_bytes / (enc_avg * 1e-3) / 1e9 / peak},
-        "gpu_launches": 3 * args.steps,
+        "config": {"workload": WORKLOAD, "streams": args.streams, **opts_dict(),
+                   "step": "batched compress + batched decompress of every stream (FIRE)",
+                   "uncompressed_bytes": U_total, "compressed_bytes": C_total, "ratio": U_total / C_total,
+                   "chunks": chunks_total, "generator": "batch_stream recipe drawn on the GPU (torch)",
+                   "generator_s": wl.gen_s,
+                   "l2": "inputs (18 GB) and streams far larger than the 129 MB L2",
+                   "parallelism": f"{world} rank(s), each a contiguous byte-balanced range of the streams",
+                   "schedules": F["sched"]},
+        "compress_gbs": total_gbs(U_total, enc_max), "decompress_gbs": total_gbs(U_total, dec_max),
+        "compress_ms": enc_max, "decompress_ms": dec_max,
+        "roofline": {"bound": "hbm", "kernel": kern, "achieved": ach, "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": ach / peak, "frac_of_nominal_8tbs": ach / NOMINAL_HBM_GBS,
+                     "traffic": traffic_bytes(kern),
+                     "algorithmic_bytes_per_launch": enc_bytes if dom == "encode" else dec_bytes,
+                     "timing": "CUDA events around each sprintz_batch_run (its memset, the header/tail "
+                               "kernel and the batched kernel)",
+                     "encode": {"kernel": "k_encode_batch", "achieved": enc_ach, "frac": enc_ach / peak,
+                                "frac_of_nominal_8tbs": enc_ach / NOMINAL_HBM_GBS,
+                                "algorithmic_bytes_per_launch": enc_bytes,
+                                "traffic": traffic_bytes("k_encode_batch")},
+                     "decode": {"kernel": "k_decode_batch", "achieved": dec_ach, "frac": dec_ach / peak,
+                                "frac_of_nominal_8tbs": dec_ach / NOMINAL_HBM_GBS,
+                                "algorithmic_bytes_per_launch": dec_bytes,
+                                "traffic": traffic_bytes("k_decode_batch")},
+                     "encode_frac": enc_ach / peak, "decode_frac": dec_ach / peak},
+        "gpu_launches": 4 * args.steps,
         "clocks": clk.summary(),
     }
+    if per_stream:
+        line["per_stream_launches"] = per_stream
+    if delta:
+        line["delta"] = delta
     if e2e:
         line["e2e"] = e2e
     if not args.no_cpu_baseline and world == 1:
-        import oracle
-        oracle.build()
-        n_s = 1 << 22
-        xs = x[:n_s]
-        t0 = time.perf_counter()
-        s = oracle.compress(xs, **opts_dict())
-        oracle.decompress(s)
-        tc = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": xs.nbytes / tc / 1e9, "unit": "GB/s", "cores": 1,
-                                "kind": "oracle",
-                                "sample": f"first {n_s} of {rows} rows, one compress+decompress, "
-                                          "single thread"}
+        sample = oracle_sample(list(range(len(ids))), 50)
+        xs_host = []
+        for k in sample:
+            h = wl.xs[k].cpu().numpy()
+            xs_host.append(h.view(np.uint16) if h.dtype == np.int16 else h)
+        line["cpu_baseline"] = cpu_baseline(xs_host)
     print(json.dumps(line), flush=True)
+    F["cc"].close()
+    F["cd"].close()
+
+
+def main():
+    args = parse()
+    if launch_ranks(args):
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus and args.impl == "ours":
+        raise SystemExit(f"--gpus {args.gpus} but {world} rank(s) were started")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if args.workload == "batch":
+        run_batch(args, rank, world, local)
+        return
+    from paper_1808_02515_gb300 import bench_workloads
+    if args.workload == "sensor":
+        bench_workloads.run_sensor(args, sys.modules[__name__], rank, world, local)
+        return
+    bench_workloads.run(args, METRIC, ClockSampler, peaks)
 
 
 if __name__ == "__main__":

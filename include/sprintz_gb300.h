@@ -55,8 +55,8 @@ extern "C" {
 typedef struct {
   uint8_t forecaster;   /* 0 = delta coding (Sec. 4.2.1); 1 = FIRE as used in practice, alpha
                            per block and one averaged update (Sec. 4.2.2); 2 = double delta,
-                           the a = 2, b = -1 model of Sec. 4.2.2; 3 = FIRE exactly as
-                           Algorithm 3 prints it, alpha and an update at every sample */
+                           the a = 2, b = -1 model of Sec. 4.2.2; 3 = FIRE in its
+                           per-sample form (Algorithm 3), alpha and a step at every sample */
   uint8_t huffman;      /* 1 = Huffman-code the bit-packed bytes (Sec. 4.4) */
   uint8_t group_blocks; /* G, 1..8: record headers stored together (Sec. 4.3); the paper uses 2 */
   uint8_t learn_shift;  /* FIRE: alpha = accumulator >> learn_shift; 1 gives eta = 1/2 (Sec. 4.2.2) */
@@ -122,6 +122,43 @@ int sprintz_decompress(sprintz_ctx *ctx, const void *src, uint64_t src_size,
                        const sprintz_info *info, void *dst, uint64_t dst_cap, void *workspace,
                        uint64_t ws_bytes, void *stream);
 
+/* Decompress rows [row_begin, row_end) of a stream into dst
+ * ((row_end - row_begin) x D samples, capacity dst_cap bytes, any alignment):
+ * Algorithm 2 over only the chunks that cover those rows -- every chunk
+ * decodes on its own, since the forecaster restarts at each one -- and the
+ * raw tail rows when the range reaches them.  The covering chunks are decoded
+ * into the workspace (sprintz_decompress_rows_workspace_size() bytes) and
+ * the rows copied out.  Streams with Huffman coding, or whose chunks no range
+ * decoder takes, are decoded whole into the workspace first (a larger
+ * workspace, same result).  row_end <= row_begin does nothing;
+ * row_end > rows is SPRINTZ_ERR_INVALID_ARG.  `info` as for
+ * sprintz_decompress(); the device checks the header and flags
+ * SPRINTZ_ERR_CORRUPT. */
+uint64_t sprintz_decompress_rows_workspace_size(const sprintz_info *info, uint64_t row_begin, uint64_t row_end);
+int sprintz_decompress_rows(sprintz_ctx *ctx, const void *src, uint64_t src_size, const sprintz_info *info,
+                            uint64_t row_begin, uint64_t row_end, void *dst, uint64_t dst_cap, void *workspace,
+                            uint64_t ws_bytes, void *stream);
+
+/* Append n_rows rows (rows x D samples at `rows`, the stream's w and D) to a
+ * compressed stream: dst receives the stream of the old series followed by
+ * the new rows, byte for byte what sprintz_compress() of the whole series
+ * writes, and *d_out_size its size.  Chunks restart the forecaster, so the
+ * old stream's complete chunks are copied as they are; its last chunk if it
+ * is partial and its raw tail rows are decoded (Algorithm 2) and encoded
+ * again with the new rows (Algorithm 1) in the workspace
+ * (sprintz_append_workspace_size() bytes), and one kernel joins the two.
+ *   - `info` is the old stream's header as parsed by sprintz_query() (a host
+ *     copy); the device checks it against the stream (SPRINTZ_ERR_CORRUPT).
+ *   - dst_cap >= sprintz_max_compressed_size(info->rows + n_rows, ...);
+ *     dst must not overlap src or rows (the old stream is not grown in
+ *     place: its chunk table precedes its bodies).
+ *   - Huffman-coded streams, and streams with chunk_rows = 0 whose one chunk
+ *     no range decoder takes, are SPRINTZ_ERR_UNSUPPORTED. */
+uint64_t sprintz_append_workspace_size(const sprintz_info *info, uint64_t n_rows);
+int sprintz_append(sprintz_ctx *ctx, const void *src, uint64_t src_size, const sprintz_info *info,
+                   const void *rows, uint64_t n_rows, void *dst, uint64_t dst_cap, uint64_t *d_out_size,
+                   void *workspace, uint64_t ws_bytes, void *stream);
+
 /* ---- Batches of independent streams --------------------------------------
  * Many streams of uneven length, width and D encoded or decoded by one
  * persistent kernel launch over the chunk groups of all of them.  The paper
@@ -151,12 +188,50 @@ typedef struct {
   uint64_t row_end;    /*   dst then receives exactly those rows; 0, 0 = the whole stream */
 } sprintz_batch_item;
 
-/* Workspace bytes for a batch (compress = 1 or 0); 0 if an item is invalid. */
+/* Launch schedule of a batched launch: the knobs that change its speed but
+ * never its bytes.  0 in a field means the library's default.
+ *   ctas_per_sm     persistent CTAs of 4 warps per SM (clamped to what fits).
+ *   ring_segments   decompress: TMA ring segments per chunk, 2 or 4.
+ *   prefetch_bytes  L2 bulk prefetch this many bytes ahead of each chunk's
+ *                   reads (rounded down to 16); 1 = no prefetch.
+ *   order           work order inside each (w, D) class of streams (the
+ *                   classes come one after another, heaviest chunk groups
+ *                   first): 1 = stream order, 2 = longest stream first,
+ *                   3 = round robin over the class's streams. */
+typedef struct {
+  uint32_t ctas_per_sm;
+  uint32_t ring_segments;
+  uint32_t prefetch_bytes;
+  uint32_t order;
+} sprintz_schedule;
+
+/* Workspace bytes for a batch (compress = 1 or 0) under any schedule; 0 if
+ * an item is invalid. */
 uint64_t sprintz_batch_workspace_size(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n,
                                       int compress);
+/* Plan with the schedule the context's autotuner chose for a batch of this
+ * kind (device, direction, forecasters, mix of widths and column counts,
+ * size), else the defaults. */
 int sprintz_batch_plan(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n, int compress,
                        void *workspace, uint64_t ws_bytes, void *stream);
+/* Plan with an explicit schedule (NULL = the defaults). */
+int sprintz_batch_plan_schedule(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n, int compress,
+                                const sprintz_schedule *schedule, void *workspace, uint64_t ws_bytes,
+                                void *stream);
 int sprintz_batch_run(sprintz_ctx *ctx, void *workspace, uint64_t ws_bytes, void *stream);
+/* The resolved schedule of the context's current plan. */
+int sprintz_batch_schedule(sprintz_ctx *ctx, sprintz_schedule *out);
+
+/* Autotuner: plan the batch under a set of candidate schedules, run each
+ * (the outputs are written, identically, every time) and time it with CUDA
+ * events on `stream` (synchronous), searching one knob at a time from the
+ * defaults.  The fastest schedule is remembered in the context for batches
+ * of the same kind (and in the text file named by SPRINTZ_SCHEDULE_CACHE, if
+ * set, which later contexts read), and the batch is left planned with it.
+ * *chosen and *ms (either may be NULL) receive it and its time. */
+int sprintz_batch_autotune(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n, int compress,
+                           void *workspace, uint64_t ws_bytes, void *stream, sprintz_schedule *chosen,
+                           float *ms);
 
 /* Compression for callers that cannot allocate device memory.  (The paper has
  * no counterpart: this is a deployment variant of sprintz_compress.)
@@ -176,7 +251,9 @@ int sprintz_batch_run(sprintz_ctx *ctx, void *workspace, uint64_t ws_bytes, void
  *     returns SPRINTZ_ERR_UNSUPPORTED.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept for the life of the
+ *     process: after cudaDeviceReset() on that device it is stale, so this
+ *     entry point must not be used on a device once it has been reset.
  *   - Every call shares the one array and each call clears what must start at
  *     zero; two calls whose work overlaps on the GPU (different streams, or
  *     different host threads) race and corrupt each other's output.
@@ -232,6 +309,21 @@ int sprintz_quant_nmse(sprintz_ctx *ctx, const float *src, const void *codes, ui
 
 /* Parse a HOST copy of a stream's first n >= 64 bytes. */
 int sprintz_query(const void *host_header, uint64_t n, sprintz_info *out);
+
+/* Failure detection, for tests of the error path (both 0 = normal use):
+ *   wait_limit        polls the single-stream encoder's look-back (the wait
+ *                     for an earlier chunk group's offset) makes before it
+ *                     gives up with SPRINTZ_ERR_TIMEOUT (0 = about 4 million,
+ *                     a few seconds at most);
+ *   skip_first_group  1 = the next single-stream compressions on this
+ *                     context never take their first chunk group, so the
+ *                     later groups wait for a predecessor that never
+ *                     publishes its offset: every such wait runs out, the
+ *                     kernel still returns, and sprintz_get_status() reports
+ *                     SPRINTZ_ERR_TIMEOUT (the bytes written are not a valid
+ *                     stream).
+ * Nothing faults or hangs: the waits are bounded and the kernels exit. */
+int sprintz_ctx_set_failure_test(sprintz_ctx *ctx, uint32_t wait_limit, uint32_t skip_first_group);
 
 /* Wait for `stream`, return the first data-dependent error recorded since
  * the last call (SPRINTZ_OK if none) and clear it. */

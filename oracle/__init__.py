@@ -318,3 +318,39 @@ def huff_canonical(lengths) -> np.ndarray:
     if rc != OK:
         raise OracleError(rc, "huff_canonical")
     return out
+
+
+# ---------------------------------------------------------------------------
+# Many independent streams on all host cores.  Streams share nothing, so the
+# plain per-stream oracle runs on a pool of host threads, one stream per task
+# (ctypes releases the GIL for the duration of each C call).  This is the
+# oracle as it stands, spread over cores; nothing in it is tuned.
+# ---------------------------------------------------------------------------
+
+def host_cores() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover - non-Linux
+        return os.cpu_count() or 1
+
+
+def map_streams(fn, items, threads: int | None = None) -> list:
+    """fn(item) for every item on `threads` host threads (all cores by
+    default), results in item order."""
+    from concurrent.futures import ThreadPoolExecutor
+    n = threads or host_cores()
+    if n <= 1:
+        return [fn(it) for it in items]
+    with ThreadPoolExecutor(n) as ex:
+        return list(ex.map(fn, items))
+
+
+def compress_many(xs, opts, threads: int | None = None) -> list:
+    """compress() of every array in xs (opts: one dict, or one per array)."""
+    ol = list(opts) if isinstance(opts, (list, tuple)) else [opts] * len(xs)
+    return map_streams(lambda a: compress(a[0], **a[1]), list(zip(xs, ol)), threads)
+
+
+def decompress_many(streams, threads: int | None = None) -> list:
+    return map_streams(decompress, list(streams), threads)

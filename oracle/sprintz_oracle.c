@@ -189,7 +189,8 @@ static uint32_t code_to_width(uint32_t c, uint32_t w) { return c == w - 1 ? w : 
  * one averaged update per block from every other sample (Sec. 4.2.2, last
  * paragraph); 2 double-delta coding, the a = 2, b = -1 case of the
  * autoregressive model of Sec. 4.2.2 (predict x_{i-1} + delta_{i-1}); 3 FIRE
- * exactly as Algorithm 3 prints it: alpha and an update at every sample. */
+ * in its per-sample form (Algorithm 3 without the practical changes of
+ * Sec. 4.2.2): a fresh alpha and an accumulator step at every sample. */
 enum { FC_DELTA = 0, FC_FIRE = 1, FC_DDELTA = 2, FC_FIRE_SAMPLE = 3 };
 enum { FIRE_NORMAL = 0, FIRE_NO_LEARNING = 1, FIRE_PINNED_ALPHA = 2 };
 
@@ -200,12 +201,12 @@ typedef struct {
   int64_t pinned_alpha;
   int64_t prev[MAX_D];   /* x_{i-1}: the previous sample, zeros initially (Sec. 4.2.1) */
   int64_t deltas[MAX_D]; /* FIRE / double delta: x_{i-1} - x_{i-2}, signed w-bit */
-  int64_t acc[MAX_D];    /* FIRE self.accumulators: signed 2w-bit */
+  int64_t acc[MAX_D];    /* FIRE accumulator A_j: signed 2w-bit */
   int64_t alpha[MAX_D];  /* FIRE alpha of the current block */
   int64_t grad[MAX_D];   /* FIRE sum of the block's sampled gradients */
 } forecaster;
 
-/* Algorithm 3 Init: accumulators and deltas start at zero. */
+/* Initial state (Sec. 4.2.2): A_j = 0 and delta_{-1} = 0 for every column. */
 static void fc_init(forecaster *f, int32_t kind, uint32_t D, uint32_t w,
                     uint32_t learn_shift, int32_t test_mode, int64_t pinned_alpha) {
   memset(f, 0, sizeof(*f));
@@ -218,7 +219,7 @@ static void fc_init(forecaster *f, int32_t kind, uint32_t D, uint32_t w,
 }
 
 /* FIRE in practice (last paragraph of Sec. 4.2.2): alpha is computed once at
- * the start of each block, alpha = accumulator >> learnShift. */
+ * the start of each block as alpha_j = A_j >> s (s = learn_shift, floor). */
 static void fc_block_begin(forecaster *f) {
   if (f->kind != FC_FIRE) return;
   for (uint32_t j = 0; j < f->D; ++j) {
@@ -231,30 +232,32 @@ static void fc_block_begin(forecaster *f) {
 }
 
 /* Predict column j of sample i from x_{i-1}.
- * Delta: the previous sample.  FIRE (Algorithm 3 Predict): the predicted
- * delta is (alpha * delta_{i-1}) >> w, the product taken in 2w bits. */
+ * Delta: the previous sample.  FIRE (Sec. 4.2.2): x_{i-1} plus the scaled
+ * previous delta floor(alpha * delta_{i-1} / 2^w), the product taken in 2w
+ * bits. */
 static int64_t fc_predict(const forecaster *f, uint32_t j) {
   if (f->kind == FC_DELTA) return f->prev[j];
   /* double delta: linear extrapolation from the last two samples */
   if (f->kind == FC_DDELTA) return wrap_unsigned(f->prev[j] + f->deltas[j], f->w);
-  /* Algorithm 3 Predict at every sample: alphas = accumulators >> learnShift */
+  /* per-sample form: alpha_j = A_j >> s taken afresh for every sample */
   int64_t alpha = f->kind == FC_FIRE_SAMPLE ? shift_right_floor(f->acc[j], f->learn_shift) : f->alpha[j];
   int64_t product = wrap_signed(alpha * f->deltas[j], 2 * f->w);
   int64_t predicted_delta = shift_right_floor(product, f->w);
   return wrap_unsigned(f->prev[j] + predicted_delta, f->w);
 }
 
-/* Algorithm 3 Train for column j of sample i (0-based row within the block).
- * The gradient of the L1 loss is -sign(err) * delta_{i-1}; the accumulator
- * moves against it.  In practice a gradient is taken only on every other
- * sample (rows 0, 2, 4, 6) and summed for one update per block. */
+/* Learning step (Sec. 4.2.2) for column j of sample i (0-based row within
+ * the block).  The L1 loss |e_i| has gradient -sign(e_i) * delta_{i-1} with
+ * respect to alpha, and A_j takes a step against it.  In practice a gradient
+ * is taken only on every other sample (rows 0, 2, 4, 6) and summed for one
+ * update per block. */
 static void fc_train(forecaster *f, uint32_t j, uint32_t i, int64_t x_i, int64_t err) {
   if (f->kind == FC_FIRE) {
     if (i % 2 == 0) f->grad[j] += sign_of(err) * f->deltas[j];
     f->deltas[j] = wrap_signed(x_i - f->prev[j], f->w);
   } else if (f->kind == FC_FIRE_SAMPLE) {
-    /* Algorithm 3 Train: gradients = -sign(err) * deltas; accumulators -=
-     * gradients (2w-bit wrap); deltas = x_i - x_{i-1} */
+    /* per-sample step: A_j += sign(e_i) * delta_{i-1} (2w-bit wrap), then
+     * delta_i = x_i - x_{i-1} */
     f->acc[j] = wrap_signed(f->acc[j] + sign_of(err) * f->deltas[j], 2 * f->w);
     f->deltas[j] = wrap_signed(x_i - f->prev[j], f->w);
   } else if (f->kind == FC_DDELTA) {

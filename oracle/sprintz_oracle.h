@@ -32,7 +32,7 @@ extern "C" {
 typedef struct {
   int32_t forecaster;   /* 0 = delta coding (Sec. 4.2.1), 1 = FIRE in its block form
                            (Sec. 4.2.2), 2 = double delta (Sec. 4.2.2, a = 2, b = -1),
-                           3 = FIRE per sample (Algorithm 3 as printed) */
+                           3 = FIRE per sample (Algorithm 3's per-sample form) */
   int32_t huffman;      /* 1 = Huffman-code the bit-packed bytes (Sec. 4.4) */
   int32_t group_blocks; /* G: records whose headers are stored together (Sec. 4.3) */
   int32_t learn_shift;  /* FIRE: alpha = accumulator >> learn_shift (eta = 2^-shift) */

@@ -14,7 +14,8 @@ import tempfile
 PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libsprintz_gb300.so")
-SOURCES = ["spz_api.cu", "spz_encode.cu", "spz_decode.cu", "spz_huff.cu", "spz_forecast.cu", "spz_quant.cu"]
+SOURCES = ["spz_api.cu", "spz_encode.cu", "spz_decode.cu", "spz_huff.cu", "spz_forecast.cu", "spz_quant.cu",
+           "spz_append.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

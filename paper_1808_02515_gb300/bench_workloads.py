@@ -119,19 +119,24 @@ def run_batch(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, syn
     gen_s = time.perf_counter() - t0
     U = sum(x.numel() * x.element_size() for x in xs)
     res = {}
+    sched = {}
     for fc_name, fc in (("delta", 0), ("fire", 1)):
         opts = spz.Opts(forecaster=fc)
-        bufs, sizes, ws_c = codec.compress_batch(xs, opts)
+        bufs, sizes, ws_c = codec.compress_batch(xs, opts, autotune=True)
+        enc_sched = codec.last_tune
         torch.cuda.synchronize()
         codec.check()
         sz = [int(v) for v in sizes.cpu().numpy()]
         C = sum(sz)
         infos = [spz.query(b[:64].cpu().numpy().tobytes()) for b in bufs]
-        outs, ws_d = codec.decompress_batch(bufs, infos, sz)
+        outs, ws_d = codec.decompress_batch(bufs, infos, sz, autotune=True)
+        dec_sched = codec.last_tune
         torch.cuda.synchronize()
         codec.check()
         for x, y in zip(xs, outs):
             assert torch.equal(x, y), "batched round trip mismatch"
+        sched[fc_name] = {"compress": vars(enc_sched[0]) | {"tune_ms": enc_sched[1]},
+                          "decompress": vars(dec_sched[0]) | {"tune_ms": dec_sched[1]}}
         # the batched form: one plan, then batch_run per step
         dec_b = _time(lambda: codec.batch_run(ws_d), args.steps, stream)
         _, _, ws_c = codec.compress_batch(xs, opts)
@@ -176,6 +181,7 @@ def run_batch(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, syn
         "per_stream_launches": {k: {"compress_gbs": U / (v["enc_s"] * 1e-3) / 1e9,
                                     "decompress_gbs": U / (v["dec_s"] * 1e-3) / 1e9}
                                 for k, v in res.items()},
+        "schedules": sched,
         "roofline": {"bound": "hbm", "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "traffic": None}})
 
 
@@ -402,3 +408,200 @@ def run_quantize(args, codec, dev, stream, line, peak, peak_kind, ClockSampler, 
                               "bytes_per_launch": "float reads (twice: extremes, codes) + code writes",
                               "traffic": None},
                  "table": table, "clocks": clk.summary()})
+
+
+def run_sensor(args, B, rank, world, local):
+    """The single-stream workload: uint16, D = 8, 2^24 rows (256 MiB) of the
+    sensor recipe, FIRE, chunk_rows 1024; one step = one compress and one
+    decompress of the whole series. N > 1: each rank its own series."""
+    import torch
+    import paper_1808_02515_gb300.sprintz as spz
+    from paper_1808_02515_gb300 import _build, synth
+
+    if rank == 0 or world == 1:
+        _build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        dist.barrier()
+        _build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    x = synth.sensor_u16(args.rows, B.COLS, seed=B.rank_seed(rank))
+    U = x.nbytes
+    xd = torch.from_numpy(x.view(np.int16)).to(dev)
+    codec = spz.Codec(local)
+    o = spz.Opts(**B.opts_dict())
+    rows, D, w = args.rows, B.COLS, 16
+    cap = spz.max_compressed_size(rows, D, w, o)
+    dst = torch.empty(cap, dtype=torch.uint8, device=dev)
+    size = torch.zeros(1, dtype=torch.int64, device=dev)
+    wsc = spz.compress_workspace_size(rows, D, w, o)
+    ws_c = torch.empty(max(wsc, 1), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # one call to learn the stream's header and size
+    codec.compress_into(xd, rows, D, w, o, dst, size, ws_c)
+    torch.cuda.synchronize()
+    codec.check()
+    C = int(size.item())
+    info = spz.query(dst[:64].cpu().numpy().tobytes())
+    wsd = spz.decompress_workspace_size(info)
+    ws_d = torch.empty(max(wsd, 1), dtype=torch.uint8, device=dev)
+    out = torch.empty((rows, D), dtype=torch.int16, device=dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        codec.compress_into(xd, rows, D, w, o, dst, size, ws_c)
+        if ev is not None:
+            ev[1].record(stream)
+        codec.decompress_into(dst, C, info, out, ws_d)
+        if ev is not None:
+            ev[2].record(stream)
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with B.ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        # keep the GPU busy until the clock sampler delivers (at most 2 s)
+        t_w = time.monotonic()
+        while not clk.lines and time.monotonic() - t_w < 2.0:
+            step()
+            torch.cuda.synchronize()
+        codec.check()
+        if not torch.equal(out, xd):
+            raise SystemExit("round trip mismatch")
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        h0 = time.monotonic()
+        t_start.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        clk.mark(h0, time.monotonic())
+    if dist:
+        dist.barrier()
+    enc_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    dec_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    total_ms = B.slowest_rank_ms(t_start.elapsed_time(t_end), dist, dev)
+    ms_step = total_ms / args.steps
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        # End to end through the C ABI with pinned host buffers: every step
+        # copies its input samples in, compresses, copies the stream out and
+        # back in (a store/load round trip through the host), decompresses and
+        # copies the samples out.  Several lanes (each its own CUDA stream and
+        # buffers) take steps in turn, so one step's copies overlap the
+        # others' kernels and the two copy directions overlap each other.
+        nl = max(1, args.e2e_lanes)
+        lanes = []
+        for _ in range(nl):
+            lanes.append({
+                "s": torch.cuda.Stream(dev),
+                "xh": torch.from_numpy(x.view(np.int16)).pin_memory(),
+                "sh": torch.empty(cap, dtype=torch.uint8).pin_memory(),
+                "yh": torch.empty((rows, D), dtype=torch.int16).pin_memory(),
+                "xin": torch.empty_like(xd),
+                "dst": torch.empty(cap, dtype=torch.uint8, device=dev),
+                "size": torch.zeros(1, dtype=torch.int64, device=dev),
+                "wsc": torch.empty(max(wsc, 1), dtype=torch.uint8, device=dev),
+                "wsd": torch.empty(max(wsd, 1), dtype=torch.uint8, device=dev),
+                "out": torch.empty((rows, D), dtype=torch.int16, device=dev),
+            })
+
+        def e2e_step(L):
+            with torch.cuda.stream(L["s"]):
+                L["xin"].copy_(L["xh"], non_blocking=True)
+                codec.compress_into(L["xin"], rows, D, w, o, L["dst"], L["size"], L["wsc"], stream=L["s"])
+                L["sh"][:C].copy_(L["dst"][:C], non_blocking=True)
+                L["dst"][:C].copy_(L["sh"][:C], non_blocking=True)
+                codec.decompress_into(L["dst"], C, info, L["out"], L["wsd"], stream=L["s"])
+                L["yh"].copy_(L["out"], non_blocking=True)
+
+        for k in range(2 * nl):
+            e2e_step(lanes[k % nl])
+        torch.cuda.synchronize()
+        codec.check()
+        if not torch.equal(lanes[0]["yh"], lanes[0]["xh"]):
+            raise SystemExit("end-to-end round trip mismatch")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_e2e = max(2 * nl, min(40, args.steps // 10)) // nl * nl
+        a.record(lanes[0]["s"])
+        for L in lanes[1:]:
+            L["s"].wait_event(a)
+        for k in range(n_e2e):
+            e2e_step(lanes[k % nl])
+        for L in lanes[1:]:
+            done = torch.cuda.Event()
+            done.record(L["s"])
+            lanes[0]["s"].wait_event(done)
+        b.record(lanes[0]["s"])
+        torch.cuda.synchronize()
+        e2e_ms = a.elapsed_time(b) / n_e2e
+        e2e_ms = B.slowest_rank_ms(e2e_ms, dist, dev)
+        e2e = {"value": B.job_gbs(U, world, e2e_ms), "unit": "GB/s",
+               "h2d_bytes_per_step": U + C, "d2h_bytes_per_step": C + U,
+               "ms_per_step": e2e_ms, "steps": n_e2e,
+               "pipelining": f"{nl} lanes (streams) take steps in turn"}
+
+    if rank != 0:
+        return
+    enc_avg, dec_avg = statistics.mean(enc_ms), statistics.mean(dec_ms)
+    peak, peak_kind = B.peaks()
+    table = 16 * info.n_chunks
+    enc_bytes, dec_bytes = U + C + table, C + U
+    dom = "decode" if dec_avg >= enc_avg else "encode"
+    dom_kernel = "k_decode_lanes" if dom == "decode" else "k_encode_slots"
+    dom_ms = dec_avg if dom == "decode" else enc_avg
+    dom_bytes = dec_bytes if dom == "decode" else enc_bytes
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    line = {
+        "metric": B.METRIC, "value": B.job_gbs(U, world, ms_step), "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+        "data": "synthetic",
+        "config": {"workload": B.SENSOR_WORKLOAD, "rows": rows, "D": D, "w": w, **B.opts_dict(),
+                   "step": "compress+decompress round trip", "uncompressed_bytes": U,
+                   "compressed_bytes": C, "ratio": U / C,
+                   "l2": "inputs (256 MiB raw, compressed stream) larger than the 129 MB L2",
+                   "parallelism": f"{world} independent streams (one per GPU)"},
+        "decompress_gbs": U / (dec_avg * 1e-3) / 1e9,
+        "compress_gbs": U / (enc_avg * 1e-3) / 1e9,
+        "decompress_ms": dec_avg, "compress_ms": enc_avg,
+        "roofline": {"bound": "hbm", "kernel": dom_kernel,
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": B.traffic_bytes(dom_kernel),
+                     "algorithmic_bytes_per_launch": dom_bytes,
+                     "decode_frac": dec_bytes / (dec_avg * 1e-3) / 1e9 / peak,
+                     "encode_frac": enc_bytes / (enc_avg * 1e-3) / 1e9 / peak},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+        oracle.build()
+        n_s = 1 << 22
+        xs = x[:n_s]
+        t0 = time.perf_counter()
+        s = oracle.compress(xs, **B.opts_dict())
+        oracle.decompress(s)
+        tc = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": xs.nbytes / tc / 1e9, "unit": "GB/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"first {n_s} of {rows} rows, one compress+decompress, "
+                                          "single thread"}
+    print(json.dumps(line), flush=True)
+

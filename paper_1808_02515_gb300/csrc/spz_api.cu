@@ -2,7 +2,13 @@
 // header parsing and the device status word.  Every compute step runs in the
 // kernels of spz_encode.cu and spz_decode.cu; there is no CPU fallback.
 #include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
+
+#include <map>
+#include <string>
 
 #include "spz_common.cuh"
 
@@ -11,11 +17,14 @@ struct sprintz_ctx {
   int *d_status;
   int *h_status;  // pinned
   spz::LaunchCfg cfg;
+  std::string dev_name;
   // the current batch plan and the host images of its descriptors
   spz::BatchPlan plan{};
   bool has_plan = false;
   std::vector<uint8_t> items_img;
-  std::vector<uint64_t> prefix_img;
+  std::vector<uint64_t> work_img;
+  // schedules chosen by the autotuner, by batch kind
+  std::map<std::string, sprintz_schedule> schedules;
 };
 
 namespace spz {
@@ -93,6 +102,8 @@ int sprintz_ctx_create(sprintz_ctx **out, int device) {
       cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&c->h_status, sizeof(int)) != cudaSuccess)
     rc = SPRINTZ_ERR_CUDA;
+  cudaDeviceProp prop;
+  if (rc == SPRINTZ_OK && cudaGetDeviceProperties(&prop, device) == cudaSuccess) c->dev_name = prop.name;
   cudaSetDevice(prev);
   if (rc != SPRINTZ_OK) {
     sprintz_ctx_destroy(c);
@@ -164,6 +175,68 @@ int sprintz_compress(sprintz_ctx *ctx, const void *src, uint64_t rows, uint32_t 
   if (ws_bytes < spz::encode_workspace_bytes(g, ctx->cfg)) return SPRINTZ_ERR_WS_TOO_SMALL;
   return spz::launch_encode_fast(g, ctx->cfg, (const uint8_t *)src, (uint8_t *)dst, dst_cap, d_out_size,
                                  (uint8_t *)workspace, ws_bytes, ctx->d_status, (cudaStream_t)stream);
+}
+
+// The geometry a host-parsed header describes (it must be self-consistent).
+static int info_geom(const sprintz_info *info, Geom *g) {
+  if (!info) return SPRINTZ_ERR_INVALID_ARG;
+  if (spz::make_geom(info->rows, info->D, info->w, &info->opts, g) != SPRINTZ_OK) return SPRINTZ_ERR_INVALID_ARG;
+  if (g->n_chunks != info->n_chunks || g->data_off != info->data_off) return SPRINTZ_ERR_INVALID_ARG;
+  return SPRINTZ_OK;
+}
+
+uint64_t sprintz_decompress_rows_workspace_size(const sprintz_info *info, uint64_t row_begin, uint64_t row_end) {
+  Geom g;
+  if (info_geom(info, &g) != SPRINTZ_OK || row_end > info->rows) return 0;
+  if (row_end <= row_begin) return 0;
+  return spz::decode_rows_workspace_bytes(g, default_cfg(), row_begin, row_end);
+}
+
+int sprintz_decompress_rows(sprintz_ctx *ctx, const void *src, uint64_t src_size, const sprintz_info *info,
+                            uint64_t row_begin, uint64_t row_end, void *dst, uint64_t dst_cap, void *workspace,
+                            uint64_t ws_bytes, void *stream) {
+  if (!ctx || !src) return SPRINTZ_ERR_INVALID_ARG;
+  Geom g;
+  int rc = info_geom(info, &g);
+  if (rc != SPRINTZ_OK) return rc;
+  if (row_end > info->rows) return SPRINTZ_ERR_INVALID_ARG;
+  if (row_end <= row_begin) return SPRINTZ_OK;
+  if (!dst) return SPRINTZ_ERR_INVALID_ARG;
+  if (dst_cap < (row_end - row_begin) * g.D * g.wb) return SPRINTZ_ERR_DST_TOO_SMALL;
+  if (src_size < g.data_off) return SPRINTZ_ERR_CORRUPT;
+  if (!workspace && ws_bytes) return SPRINTZ_ERR_INVALID_ARG;
+  return spz::launch_decode_rows(g, ctx->cfg, (const uint8_t *)src, src_size, row_begin, row_end, (uint8_t *)dst,
+                                 (uint8_t *)workspace, ws_bytes, ctx->d_status, (cudaStream_t)stream);
+}
+
+uint64_t sprintz_append_workspace_size(const sprintz_info *info, uint64_t n_rows) {
+  Geom g;
+  if (info_geom(info, &g) != SPRINTZ_OK) return 0;
+  return spz::append_workspace_bytes(g, default_cfg(), n_rows);
+}
+
+int sprintz_append(sprintz_ctx *ctx, const void *src, uint64_t src_size, const sprintz_info *info, const void *rows,
+                   uint64_t n_rows, void *dst, uint64_t dst_cap, uint64_t *d_out_size, void *workspace,
+                   uint64_t ws_bytes, void *stream) {
+  if (!ctx || !src || !dst || !d_out_size || (n_rows && !rows) || !workspace) return SPRINTZ_ERR_INVALID_ARG;
+  Geom g;
+  int rc = info_geom(info, &g);
+  if (rc != SPRINTZ_OK) return rc;
+  if (g.huffman) return SPRINTZ_ERR_UNSUPPORTED;
+  if (src_size < g.data_off || info->tail_off < g.data_off || info->tail_off > src_size) return SPRINTZ_ERR_CORRUPT;
+  const uint64_t cap = sprintz_max_compressed_size(info->rows + n_rows, info->D, info->w, &info->opts);
+  if (cap == 0) return SPRINTZ_ERR_INVALID_ARG;
+  if (dst_cap < cap) return SPRINTZ_ERR_DST_TOO_SMALL;
+  return spz::launch_append(g, ctx->cfg, (const uint8_t *)src, src_size, info->tail_off, (const uint8_t *)rows,
+                            n_rows, (uint8_t *)dst, dst_cap, d_out_size, (uint8_t *)workspace, ws_bytes,
+                            ctx->d_status, (cudaStream_t)stream);
+}
+
+int sprintz_ctx_set_failure_test(sprintz_ctx *ctx, uint32_t wait_limit, uint32_t skip_first_group) {
+  if (!ctx || skip_first_group > 1) return SPRINTZ_ERR_INVALID_ARG;
+  ctx->cfg.wait_limit = wait_limit;
+  ctx->cfg.skip_first_group = skip_first_group;
+  return SPRINTZ_OK;
 }
 
 int sprintz_forecast(sprintz_ctx *ctx, const void *src, uint64_t rows, uint32_t D, uint32_t w,
@@ -270,51 +343,245 @@ int sprintz_decompress(sprintz_ctx *ctx, const void *src, uint64_t src_size, con
                             (uint8_t *)workspace, ws_bytes, ctx->d_status, (cudaStream_t)stream);
 }
 
-static int plan_any(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n, int compress, uint8_t *ws,
-                    spz::BatchPlan *pl) {
+}  // extern "C"
+
+namespace {
+
+int plan_any(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n, int compress,
+             const sprintz_schedule &sched, uint8_t *ws, spz::BatchPlan *pl) {
   if (!ctx || (!items && n)) return SPRINTZ_ERR_INVALID_ARG;
   if (n == 0) return SPRINTZ_ERR_INVALID_ARG;
-  return compress ? spz::plan_batch_encode(items, n, ctx->cfg, ctx->d_status, ws, pl, &ctx->items_img,
-                                           &ctx->prefix_img)
-                  : spz::plan_batch_decode(items, n, ctx->cfg, ctx->d_status, ws, pl, &ctx->items_img,
-                                           &ctx->prefix_img);
+  return compress ? spz::plan_batch_encode(items, n, ctx->cfg, sched, ctx->d_status, ws, pl, &ctx->items_img,
+                                           &ctx->work_img)
+                  : spz::plan_batch_decode(items, n, ctx->cfg, sched, ctx->d_status, ws, pl, &ctx->items_img,
+                                           &ctx->work_img);
 }
 
-uint64_t sprintz_batch_workspace_size(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n,
-                                      int compress) {
-  spz::BatchPlan pl;
-  if (plan_any(ctx, items, n, compress, nullptr, &pl) != SPRINTZ_OK) return 0;
-  return pl.ws_total;
-}
-
-int sprintz_batch_plan(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n, int compress,
-                       void *workspace, uint64_t ws_bytes, void *stream) {
+// Plan and upload the descriptors and the work list (stream-ordered; the
+// host images must outlive the copies, so the call waits for them).
+int plan_upload(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n, int compress,
+                const sprintz_schedule &sched, void *workspace, uint64_t ws_bytes, cudaStream_t s) {
   if (!workspace) return SPRINTZ_ERR_INVALID_ARG;
   spz::BatchPlan pl;
   if (ctx) ctx->has_plan = false;
-  int rc = plan_any(ctx, items, n, compress, (uint8_t *)workspace, &pl);
+  int rc = plan_any(ctx, items, n, compress, sched, (uint8_t *)workspace, &pl);
   if (rc != SPRINTZ_OK) return rc;
   if (ws_bytes < pl.ws_total) return SPRINTZ_ERR_WS_TOO_SMALL;
   pl.ws = workspace;
-  cudaStream_t s = (cudaStream_t)stream;
   uint8_t *ws = (uint8_t *)workspace;
   if (cudaMemcpyAsync(ws + pl.items_off, ctx->items_img.data(), ctx->items_img.size(), cudaMemcpyHostToDevice,
                       s) != cudaSuccess ||
-      cudaMemcpyAsync(ws + pl.prefix_off, ctx->prefix_img.data(), ctx->prefix_img.size() * 8,
-                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+      (ctx->work_img.size() &&
+       cudaMemcpyAsync(ws + pl.work_off, ctx->work_img.data(), ctx->work_img.size() * 8, cudaMemcpyHostToDevice,
+                       s) != cudaSuccess))
     return SPRINTZ_ERR_CUDA;
-  // the host images must outlive the copies: wait for them here
   if (cudaStreamSynchronize(s) != cudaSuccess) return SPRINTZ_ERR_CUDA;
   ctx->plan = pl;
   ctx->has_plan = true;
   return SPRINTZ_OK;
 }
 
+// The kind of a batch, for the autotuner's memory: device, direction,
+// forecasters used, range requests, size (half powers of two) and the share
+// of uncompressed bytes in each (w, D bucket) class (tenths).
+std::string batch_kind(const sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n, int compress) {
+  static const uint32_t bucket_hi[] = {1, 2, 3, 4, 8, 16, 32};
+  double cls[2][7] = {};
+  double total = 0;
+  uint32_t fc_mask = 0;
+  bool ranged = false;
+  for (uint32_t i = 0; i < n; ++i) {
+    const sprintz_batch_item &it = items[i];
+    const uint64_t rows = (!compress && it.row_end > it.row_begin) ? it.row_end - it.row_begin : it.rows;
+    const double u = (double)rows * it.D * (it.w / 8);
+    int b = 0;
+    while (b < 6 && it.D > bucket_hi[b]) ++b;
+    cls[it.w == 16][b] += u;
+    total += u;
+    fc_mask |= 1u << (it.opts.forecaster & 7);
+    ranged |= !compress && it.row_end > it.row_begin;
+  }
+  char buf[256];
+  int len = snprintf(buf, sizeof buf, "%s|%d|%s|fc%x|%s|lg%.1f|", ctx->dev_name.c_str(), ctx->cfg.sm_count,
+                     compress ? "enc" : "dec", fc_mask, ranged ? "rng" : "all",
+                     total > 0 ? floor(2.0 * log2(total)) / 2.0 : 0.0);
+  std::string key(buf, len > 0 ? (size_t)len : 0);
+  for (int w = 0; w < 2; ++w)
+    for (int b = 0; b < 7; ++b) {
+      const int tenth = total > 0 ? (int)lround(10.0 * cls[w][b] / total) : 0;
+      key += (char)('0' + tenth % 10 + (tenth == 10 ? 17 : 0));  // 0..9, 'A' for all of it
+    }
+  return key;
+}
+
+const char *schedule_cache_path() { return getenv("SPRINTZ_SCHEDULE_CACHE"); }
+
+void load_schedule_cache(sprintz_ctx *ctx) {
+  const char *path = schedule_cache_path();
+  if (!path) return;
+  FILE *f = fopen(path, "r");
+  if (!f) return;
+  char line[512];
+  while (fgets(line, sizeof line, f)) {
+    char key[400];
+    sprintz_schedule s{};
+    if (sscanf(line, "%399[^\t]\t%u\t%u\t%u\t%u", key, &s.ctas_per_sm, &s.ring_segments, &s.prefetch_bytes,
+               &s.order) == 5)
+      ctx->schedules[key] = s;
+  }
+  fclose(f);
+}
+
+void save_schedule(const std::string &key, const sprintz_schedule &s, float ms) {
+  const char *path = schedule_cache_path();
+  if (!path) return;
+  FILE *f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s\t%u\t%u\t%u\t%u\t%.4f\n", key.c_str(), s.ctas_per_sm, s.ring_segments, s.prefetch_bytes,
+          s.order, ms);
+  fclose(f);
+}
+
+int run_plan(sprintz_ctx *ctx, cudaStream_t s) {
+  return ctx->plan.compress ? spz::run_batch_encode(ctx->plan, s) : spz::run_batch_decode(ctx->plan, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t sprintz_batch_workspace_size(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n,
+                                      int compress) {
+  spz::BatchPlan pl;
+  sprintz_schedule none{};
+  if (plan_any(ctx, items, n, compress, none, nullptr, &pl) != SPRINTZ_OK) return 0;
+  return pl.ws_total;
+}
+
+int sprintz_batch_plan_schedule(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n, int compress,
+                                const sprintz_schedule *schedule, void *workspace, uint64_t ws_bytes,
+                                void *stream) {
+  sprintz_schedule s{};
+  if (schedule) s = *schedule;
+  return plan_upload(ctx, items, n, compress, s, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
+int sprintz_batch_plan(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n, int compress,
+                       void *workspace, uint64_t ws_bytes, void *stream) {
+  if (!ctx || (!items && n) || n == 0) return SPRINTZ_ERR_INVALID_ARG;
+  if (ctx->schedules.empty()) load_schedule_cache(ctx);
+  sprintz_schedule s{};
+  auto hit = ctx->schedules.find(batch_kind(ctx, items, n, compress));
+  if (hit != ctx->schedules.end()) s = hit->second;
+  return plan_upload(ctx, items, n, compress, s, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
 int sprintz_batch_run(sprintz_ctx *ctx, void *workspace, uint64_t ws_bytes, void *stream) {
   if (!ctx || !ctx->has_plan || ctx->plan.ws != workspace || ws_bytes < ctx->plan.ws_total)
     return SPRINTZ_ERR_INVALID_ARG;
-  return ctx->plan.compress ? spz::run_batch_encode(ctx->plan, (cudaStream_t)stream)
-                            : spz::run_batch_decode(ctx->plan, (cudaStream_t)stream);
+  return run_plan(ctx, (cudaStream_t)stream);
+}
+
+int sprintz_batch_schedule(sprintz_ctx *ctx, sprintz_schedule *out) {
+  if (!ctx || !out || !ctx->has_plan) return SPRINTZ_ERR_INVALID_ARG;
+  *out = ctx->plan.sched;
+  return SPRINTZ_OK;
+}
+
+int sprintz_batch_autotune(sprintz_ctx *ctx, const sprintz_batch_item *items, uint32_t n, int compress,
+                           void *workspace, uint64_t ws_bytes, void *stream, sprintz_schedule *chosen,
+                           float *ms_out) {
+  if (!ctx || !items || n == 0 || !workspace) return SPRINTZ_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return SPRINTZ_ERR_CUDA;
+  }
+  int rc = SPRINTZ_OK;
+  // time of one run under schedule c (one untimed run, then the mean of two);
+  // a schedule that resolves to one already timed is not run again (*t < 0)
+  std::vector<sprintz_schedule> seen;
+  auto evaluate = [&](const sprintz_schedule &c, float *t, sprintz_schedule *resolved) -> int {
+    int r = plan_upload(ctx, items, n, compress, c, workspace, ws_bytes, s);
+    if (r != SPRINTZ_OK) return r;
+    *resolved = ctx->plan.sched;
+    *t = -1.0f;
+    for (const sprintz_schedule &q : seen)
+      if (memcmp(&q, resolved, sizeof q) == 0) return SPRINTZ_OK;
+    seen.push_back(*resolved);
+    if ((r = run_plan(ctx, s)) != SPRINTZ_OK) return r;
+    if (cudaEventRecord(e0, s) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+    for (int k = 0; k < 2; ++k)
+      if ((r = run_plan(ctx, s)) != SPRINTZ_OK) return r;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(t, e0, e1) != cudaSuccess)
+      return SPRINTZ_ERR_CUDA;
+    *t *= 0.5f;
+    return SPRINTZ_OK;
+  };
+  sprintz_schedule best{}, res{};
+  float best_ms = 0;
+  rc = evaluate(best, &best_ms, &res);
+  if (rc == SPRINTZ_OK) {
+    best = res;
+    // one knob at a time, from the defaults
+    std::vector<std::vector<sprintz_schedule>> knobs;
+    std::vector<sprintz_schedule> k_ctas, k_pf, k_order, k_seg;
+    for (uint32_t v : {2u, 3u, 4u, 5u, 6u, 8u}) {
+      sprintz_schedule c{};
+      c.ctas_per_sm = v;
+      k_ctas.push_back(c);
+    }
+    for (uint32_t v : {1u, 1024u, 2048u, 4096u, 8192u}) {
+      sprintz_schedule c{};
+      c.prefetch_bytes = v;
+      k_pf.push_back(c);
+    }
+    for (uint32_t v : {1u, 2u, 3u}) {
+      sprintz_schedule c{};
+      c.order = v;
+      k_order.push_back(c);
+    }
+    for (uint32_t v : {2u, 4u}) {
+      sprintz_schedule c{};
+      c.ring_segments = v;
+      k_seg.push_back(c);
+    }
+    knobs = {k_ctas, k_pf, k_order};
+    if (!compress) knobs.push_back(k_seg);
+    for (size_t kn = 0; kn < knobs.size() && rc == SPRINTZ_OK; ++kn) {
+      const sprintz_schedule base = best;
+      for (const sprintz_schedule &delta : knobs[kn]) {
+        sprintz_schedule c = base;
+        if (kn == 0) c.ctas_per_sm = delta.ctas_per_sm;
+        if (kn == 1) c.prefetch_bytes = delta.prefetch_bytes;
+        if (kn == 2) c.order = delta.order;
+        if (kn == 3) c.ring_segments = delta.ring_segments;
+        float t = 0;
+        rc = evaluate(c, &t, &res);
+        if (rc != SPRINTZ_OK) break;
+        if (t >= 0 && t < best_ms) {
+          best = res;
+          best_ms = t;
+        }
+      }
+    }
+  }
+  if (rc == SPRINTZ_OK) {
+    rc = plan_upload(ctx, items, n, compress, best, workspace, ws_bytes, s);
+    if (rc == SPRINTZ_OK) {
+      const std::string key = batch_kind(ctx, items, n, compress);
+      ctx->schedules[key] = best;
+      save_schedule(key, best, best_ms);
+      if (chosen) *chosen = best;
+      if (ms_out) *ms_out = best_ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
 }
 
 int sprintz_get_status(sprintz_ctx *ctx, void *stream) {

@@ -35,7 +35,7 @@ constexpr uint32_t kMaxD = 1024;
 constexpr int kFcDelta = 0;       // x_{i-1} (Sec. 4.2.1)
 constexpr int kFcFire = 1;        // FIRE, block form: alpha per block, one averaged update (Sec. 4.2.2)
 constexpr int kFcDDelta = 2;      // double delta x_{i-1} + delta_{i-1} (Sec. 4.2.2, a = 2, b = -1)
-constexpr int kFcFireSample = 3;  // FIRE as Algorithm 3 prints it: alpha and an update every sample
+constexpr int kFcFireSample = 3;  // FIRE per sample (Algorithm 3 without Sec. 4.2.2's changes): alpha and a step every sample
 
 // Everything about a stream's layout that the host knows before launch.
 struct Geom {
@@ -232,11 +232,37 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
   return false;
 }
 
+// Copy n bytes with every thread of the grid: 16-byte vectors when source
+// and destination share their alignment modulo 16, else 4-byte words when
+// they share it modulo 4, else bytes.
+__device__ __forceinline__ void grid_copy(uint8_t *dst, const uint8_t *src, uint64_t n) {
+  const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+  const uintptr_t mis = ((uintptr_t)dst ^ (uintptr_t)src);
+  const uint32_t vec = (mis & 15) == 0 ? 16u : ((mis & 3) == 0 ? 4u : 1u);
+  uint64_t head = vec == 1 ? 0 : ((vec - ((uintptr_t)dst & (vec - 1))) & (vec - 1));
+  if (head > n) head = n;
+  for (uint64_t k = t0; k < head; k += nt) dst[k] = src[k];
+  const uint64_t nv = vec == 1 ? 0 : (n - head) / vec;
+  if (vec == 16) {
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src + head);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst + head);
+    for (uint64_t k = t0; k < nv; k += nt) d4[k] = s4[k];
+  } else if (vec == 4) {
+    const uint32_t *s4 = reinterpret_cast<const uint32_t *>(src + head);
+    uint32_t *d4 = reinterpret_cast<uint32_t *>(dst + head);
+    for (uint64_t k = t0; k < nv; k += nt) d4[k] = s4[k];
+  }
+  for (uint64_t k = head + nv * vec + t0; k < n; k += nt) dst[k] = src[k];
+}
+
 // Host helpers --------------------------------------------------------------
 
 struct LaunchCfg {
   int sm_count;
   int max_smem_optin;
+  uint32_t wait_limit;        // look-back polls before SPRINTZ_ERR_TIMEOUT (0: the default)
+  uint32_t skip_first_group;  // failure test: single-stream encoders start their ticket at 1
 };
 
 int make_geom(uint64_t rows, uint32_t D, uint32_t w, const sprintz_opts *o, Geom *g);
@@ -280,26 +306,57 @@ struct BatchPlan {
   uint32_t n;
   uint32_t grid;
   uint32_t region;        // shared bytes per warp
-  uint64_t slot_region;   // encode: slot bytes per warp
+  uint64_t slot_region;   // encode: slot bytes per warp; decode: nonzero if any range request
   uint64_t items_off;     // descriptor table
-  uint64_t prefix_off;    // chunk-group prefix (n + 1 words)
-  uint64_t slots_off;     // encode: slots
-  uint64_t zero_bytes;    // encode: ticket + look-back words to clear at [0, zero_bytes)
+  uint64_t work_off;      // work list: one u64 (stream << 40 | chunk group) per work item
+  uint64_t n_work;
+  uint64_t slots_off;     // encode: slots; decode: range temporaries
+  uint64_t zero_bytes;    // ticket (+ encode: look-back words) to clear at [0, zero_bytes)
   uint64_t ws_total;
+  sprintz_schedule sched; // the schedule the plan was built with (defaults filled in)
   void *ws;
 };
-// Build the plan and the descriptor image (host bytes to copy to ws + items_off
-// and ws + prefix_off).  Returns SPRINTZ_OK or an error.
-int plan_batch_encode(const sprintz_batch_item *items, uint32_t n, const LaunchCfg &cfg, int *d_status,
-                      uint8_t *ws, BatchPlan *plan, std::vector<uint8_t> *items_img,
-                      std::vector<uint64_t> *prefix_img);
+// A work entry: stream index (< 2^24) and chunk group of that stream.
+constexpr uint32_t kWorkGroupBits = 40;
+constexpr uint32_t kMaxBatchStreams = 1u << 24;
+// Resolve the 0 (= default) fields of a schedule for one direction.
+sprintz_schedule batch_default_schedule(int compress);
+// Build the plan and the descriptor image (host bytes to copy to ws +
+// items_off and ws + work_off).  Returns SPRINTZ_OK or an error.
+int plan_batch_encode(const sprintz_batch_item *items, uint32_t n, const LaunchCfg &cfg,
+                      const sprintz_schedule &sched, int *d_status, uint8_t *ws, BatchPlan *plan,
+                      std::vector<uint8_t> *items_img, std::vector<uint64_t> *work_img);
 int run_batch_encode(const BatchPlan &plan, cudaStream_t stream);
-int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchCfg &cfg, int *d_status,
-                      uint8_t *ws, BatchPlan *plan, std::vector<uint8_t> *items_img,
-                      std::vector<uint64_t> *prefix_img);
+int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchCfg &cfg,
+                      const sprintz_schedule &sched, int *d_status, uint8_t *ws, BatchPlan *plan,
+                      std::vector<uint8_t> *items_img, std::vector<uint64_t> *work_img);
 int run_batch_decode(const BatchPlan &plan, cudaStream_t stream);
+// The work list of a batch: per (w, D) class (classes in a fixed order, the
+// heaviest groups first), the chunk groups of the class's streams in the
+// schedule's order; every stream's groups stay in increasing order.
+void batch_work_list(const std::vector<uint32_t> &w, const std::vector<uint32_t> &D,
+                     const std::vector<uint64_t> &groups, const std::vector<uint64_t> &group_bytes,
+                     uint32_t order, std::vector<uint64_t> *work);
 int launch_decode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint64_t src_size,
                   uint8_t *dst, uint64_t dst_cap, uint8_t *ws, uint64_t ws_bytes, int *d_status,
                   cudaStream_t stream);
+// Decode chunks [c_begin, c_end) of a stream without Huffman coding into dst
+// (8-byte aligned; it receives rows from c_begin * chunk_rows on) with the
+// lane or the wide decoder; no header check and no tail.  Returns
+// SPRINTZ_ERR_UNSUPPORTED when neither decoder takes this stream.
+bool decode_chunks_supported(const Geom &g, const LaunchCfg &cfg);
+int launch_decode_chunks(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint64_t src_size,
+                         uint32_t c_begin, uint32_t c_end, uint8_t *dst, uint64_t dst_cap, int *d_status,
+                         cudaStream_t stream);
+// Rows [row_begin, row_end) of a stream into out (any alignment).
+uint64_t decode_rows_workspace_bytes(const Geom &g, const LaunchCfg &cfg, uint64_t row_begin, uint64_t row_end);
+int launch_decode_rows(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint64_t src_size,
+                       uint64_t row_begin, uint64_t row_end, uint8_t *out, uint8_t *ws, uint64_t ws_bytes,
+                       int *d_status, cudaStream_t stream);
+// A stream followed by n_new more rows (spz_append.cu).
+uint64_t append_workspace_bytes(const Geom &g_old, const LaunchCfg &cfg, uint64_t n_new);
+int launch_append(const Geom &g_old, const LaunchCfg &cfg, const uint8_t *src, uint64_t src_size,
+                  uint64_t old_tail_off, const uint8_t *rows, uint64_t n_new, uint8_t *dst, uint64_t dst_cap,
+                  uint64_t *d_out_size, uint8_t *ws, uint64_t ws_bytes, int *d_status, cudaStream_t stream);
 
 }  // namespace spz

@@ -331,7 +331,7 @@ __device__ void decode_chunk(const DecParams &p, uint8_t *mem, uint32_t c, uint6
     // computed as one multiply-add and shift in 32 bits, x_i = x_{i-1} + delta_i.
     // Double delta: delta_i = wrap_w(delta_{i-1} + e_i).  FIRE per sample:
     // alpha from the accumulator and acc += sign(e_i) * delta_{i-1} at every
-    // row (Algorithm 3 as printed).
+    // row (Algorithm 3's per-sample form).
     for (uint32_t j = threadIdx.x; j < D; j += blockDim.x) {
       int32_t acc = 0, dp = 0;
       uint32_t xp = 0;
@@ -390,22 +390,29 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecParams p) {
   for (uint32_t c = blockIdx.x; c < g.n_chunks; c += gridDim.x) decode_chunk<W>(p, mem, c, data_bytes);
 }
 
+// The stream's 64-byte header agrees with the host's geometry and its sizes
+// with the buffer; *tail_off receives the raw tail's offset.
+__device__ bool header_matches(const Geom &g, const uint8_t *h, uint64_t src_size, uint64_t *tail_off_out) {
+  bool ok = h[0] == 'S' && h[1] == 'P' && h[2] == 'Z' && h[3] == '1' && h[4] == 1 &&
+            h[5] == g.w && h[6] == g.forecaster && h[7] == (g.huffman ? 1 : 0) &&
+            (h[8] | (h[9] << 8)) == g.D && h[10] == g.G && h[11] == g.learn_shift &&
+            le_u32(h + 12) == g.chunk_rows_opt && le_u32(h + 16) == (g.huffman ? g.huff_chunks : 0) &&
+            le_u32(h + 20) == g.n_chunks && le_u64(h + 24) == g.rows &&
+            le_u32(h + 32) == g.tail_rows && le_u32(h + 36) == 0 && le_u64(h + 40) == g.data_off;
+  const uint64_t tail_off = le_u64(h + 48), total = le_u64(h + 56);
+  ok = ok && tail_off >= g.data_off && total <= src_size && total == tail_off + g.tail_rows * g.D * g.wb;
+  *tail_off_out = tail_off;
+  return ok;
+}
+
 // Check the device header against the host's geometry and copy the tail.
 __global__ void k_decode_header_tail(DecParams p) {
   const Geom &g = p.g;
   __shared__ uint32_t s_ok;
   __shared__ uint64_t s_tail_off;
   if (threadIdx.x == 0) {
-    const uint8_t *h = p.src;
-    bool ok = h[0] == 'S' && h[1] == 'P' && h[2] == 'Z' && h[3] == '1' && h[4] == 1 &&
-              h[5] == g.w && h[6] == g.forecaster && h[7] == (g.huffman ? 1 : 0) &&
-              (h[8] | (h[9] << 8)) == g.D && h[10] == g.G && h[11] == g.learn_shift &&
-              le_u32(h + 12) == g.chunk_rows_opt && le_u32(h + 16) == (g.huffman ? g.huff_chunks : 0) &&
-              le_u32(h + 20) == g.n_chunks && le_u64(h + 24) == g.rows &&
-              le_u32(h + 32) == g.tail_rows && le_u32(h + 36) == 0 && le_u64(h + 40) == g.data_off;
-    uint64_t tail_off = le_u64(h + 48), total = le_u64(h + 56);
-    ok = ok && tail_off >= g.data_off && total <= p.src_size &&
-         total == tail_off + g.tail_rows * g.D * g.wb;
+    uint64_t tail_off = 0;
+    const bool ok = header_matches(g, p.src, p.src_size, &tail_off);
     s_ok = ok;
     s_tail_off = tail_off;
     if (!ok) set_status(p.status, SPRINTZ_ERR_CORRUPT);
@@ -1025,28 +1032,55 @@ struct DecBatchItem {
   uint8_t *out;
 };
 
-// Batched decode: the chunk groups of all streams form one work list
-// (gprefix[s] = first group of stream s); each warp takes items in turn.
-__global__ void __launch_bounds__(kLaneThreads) k_decode_batch(const DecBatchItem *items,
-                                                              const uint64_t *gprefix, uint32_t n,
-                                                              uint32_t per_warp) {
+static_assert(sizeof(DecBatchItem) % 8 == 0, "descriptors are copied in 8-byte words");
+
+// One chunk group of a batch item through the lane decoder specialised for
+// its column count (a call per group keeps each variant's code apart).
+template <int W, int DT>
+__device__ __noinline__ void decode_batch_group(const DecBatchItem &it, uint64_t grp, uint8_t *wsm) {
+  decode_group<W, DT>(it.p, it.rg, grp, wsm);
+}
+
+// Variant table: [w == 16][D] (D = 0: any column count up to 32).  One
+// indirect call site for every variant keeps the kernel's frame small.
+typedef void (*DecBatchGroupFn)(const DecBatchItem &, uint64_t, uint8_t *);
+#define SPZ_DEC_ROW(W)                                                                                  \
+  {decode_batch_group<W, 0>,  decode_batch_group<W, 1>,  decode_batch_group<W, 2>,                      \
+   decode_batch_group<W, 3>,  decode_batch_group<W, 4>,  decode_batch_group<W, 5>,                      \
+   decode_batch_group<W, 6>,  decode_batch_group<W, 7>,  decode_batch_group<W, 8>,                      \
+   decode_batch_group<W, 9>,  decode_batch_group<W, 10>, decode_batch_group<W, 11>,                     \
+   decode_batch_group<W, 12>, decode_batch_group<W, 13>, decode_batch_group<W, 14>,                     \
+   decode_batch_group<W, 15>, decode_batch_group<W, 16>}
+__device__ DecBatchGroupFn g_dec_batch_fns[2][17] = {SPZ_DEC_ROW(8), SPZ_DEC_ROW(16)};
+#undef SPZ_DEC_ROW
+
+// Batched decode: persistent warps take work entries (stream, chunk group)
+// from one ticket, in the host's (w, D)-class order; each warp copies its
+// item's descriptor into shared memory once per group.
+__global__ void __launch_bounds__(kLaneThreads, 7) k_decode_batch(const DecBatchItem *items,
+                                                                 const uint64_t *work, uint64_t n_work,
+                                                                 unsigned long long *ticket, uint32_t per_warp) {
   extern __shared__ __align__(16) uint8_t dsm[];
-  const uint32_t warp = threadIdx.x >> 5;
+  __shared__ __align__(16) DecBatchItem s_it[kLaneWarps];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t *wsm = dsm + (uint64_t)warp * per_warp;
-  const uint64_t total = gprefix[n];
-  for (uint64_t item = (uint64_t)blockIdx.x * kLaneWarps + warp; item < total;
-       item += (uint64_t)gridDim.x * kLaneWarps) {
-    // stream of this item: last s with gprefix[s] <= item
-    uint32_t lo = 0, hi = n;
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) / 2;
-      if (gprefix[mid] <= item) lo = mid; else hi = mid;
-    }
-    const DecBatchItem it = items[lo];
-    if (it.p.g.w == 8)
-      decode_group<8, 0>(it.p, it.rg, item - gprefix[lo], wsm);
-    else
-      decode_group<16, 0>(it.p, it.rg, item - gprefix[lo], wsm);
+  constexpr uint32_t kWords = sizeof(DecBatchItem) / 8;
+  for (;;) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(ticket, 1ull);
+    t = __shfl_sync(0xFFFFFFFFu, t, 0);
+    if (t >= n_work) break;
+    const uint64_t e = __ldg(work + t);
+    const uint32_t s = (uint32_t)(e >> kWorkGroupBits);
+    const uint64_t grp = e & ((1ull << kWorkGroupBits) - 1);
+    const uint64_t *from = reinterpret_cast<const uint64_t *>(items + s);
+    uint64_t *to = reinterpret_cast<uint64_t *>(&s_it[warp]);
+    for (uint32_t k = lane; k < kWords; k += 32) to[k] = __ldg(from + k);
+    __syncwarp();
+    const DecBatchItem &it = s_it[warp];
+    const uint32_t D = it.p.g.D;
+    g_dec_batch_fns[it.p.g.w == 16][D <= 16 ? D : 0](it, grp, wsm);
+    __syncwarp();
   }
 }
 
@@ -1175,20 +1209,23 @@ static DecPlan dec_plan(const Geom &g, const LaunchCfg &cfg) {
 
 // ---- batches ----------------------------------------------------------------
 
-int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchCfg &cfg, int *d_status,
-                      uint8_t *ws, BatchPlan *pl, std::vector<uint8_t> *img, std::vector<uint64_t> *pre) {
-  (void)ws;
+int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchCfg &cfg,
+                      const sprintz_schedule &sched_in, int *d_status, uint8_t *ws, BatchPlan *pl,
+                      std::vector<uint8_t> *img, std::vector<uint64_t> *work) {
+  if (n > kMaxBatchStreams) return SPRINTZ_ERR_INVALID_ARG;
+  sprintz_schedule sched = batch_default_schedule(0);
+  if (sched_in.ctas_per_sm) sched.ctas_per_sm = sched_in.ctas_per_sm;
+  if (sched_in.ring_segments == 2 || sched_in.ring_segments == 4) sched.ring_segments = sched_in.ring_segments;
+  if (sched_in.prefetch_bytes) sched.prefetch_bytes = sched_in.prefetch_bytes == 1 ? 1u : sched_in.prefetch_bytes & ~15u;
+  if (sched_in.order >= 1 && sched_in.order <= 3) sched.order = sched_in.order;
   std::vector<DecBatchItem> v(n);
   std::vector<uint64_t> temp_off(n, 0);
+  std::vector<uint32_t> vw(n), vD(n);
+  std::vector<uint64_t> vgroups(n), vgbytes(n);
   uint64_t temp_total = 0;
   bool any_ranged = false;
-  pre->assign((size_t)n + 1, 0);
   uint32_t region = 0;
-  static const uint32_t win = [] {
-    const char *e = getenv("SPRINTZ_DEC_PF_WIN");
-    int x = e ? atoi(e) : 0;
-    return (uint32_t)(x >= 16 ? (x & ~15) : 2048);
-  }();
+  const uint32_t win = sched.prefetch_bytes == 1 ? 0u : sched.prefetch_bytes;
   for (uint32_t i = 0; i < n; ++i) {
     const sprintz_batch_item &it = items[i];
     Geom g;
@@ -1227,27 +1264,36 @@ int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchC
       }
       const uint64_t tmp_rows =
           std::min<uint64_t>((uint64_t)d.p.c_end * g.chunk_rows, g.full_rows) - (uint64_t)d.p.c_begin * g.chunk_rows;
-      d.p.dst = ws ? ws + temp_total : nullptr;  // completed below with the table offset
+      d.p.dst = nullptr;  // set below, once the temporaries' offset is known
       d.p.dst_cap = tmp_rows * g.D * g.wb;
       temp_off[i] = temp_total;
       temp_total = (temp_total + d.p.dst_cap + 255) & ~255ull;
       any_ranged = true;
     }
     if (g.n_chunks) {
-      d.rg = lane_ring_plan(g, cfg, 2, false);  // the batch kernel stores directly
+      // the batch kernel stages the rows of D <= 3 in shared memory, as the
+      // single-stream lane decoder does
+      d.rg = lane_ring_plan(g, cfg, sched.ring_segments, dec_staged((int)g.D));
+      if (!d.rg.per_warp) d.rg = lane_ring_plan(g, cfg, 2, dec_staged((int)g.D));
       if (!d.rg.per_warp) return SPRINTZ_ERR_UNSUPPORTED;
       region = std::max(region, d.rg.per_warp);
     }
     const uint64_t K = 32 / g.D;
-    (*pre)[i + 1] = (*pre)[i] + (d.p.c_end - d.p.c_begin + K - 1) / K;
+    vw[i] = g.w;
+    vD[i] = g.D;
+    vgroups[i] = (d.p.c_end - d.p.c_begin + K - 1) / K;
+    vgbytes[i] = K * g.chunk_rows * g.D * g.wb;
   }
+  batch_work_list(vw, vD, vgroups, vgbytes, sched.order, work);
   memset(pl, 0, sizeof(*pl));
   pl->compress = 0;
   pl->n = n;
   pl->region = std::max<uint32_t>(region, 16);
-  pl->items_off = 0;
-  pl->prefix_off = align256d((uint64_t)n * sizeof(DecBatchItem));
-  pl->slots_off = align256d(pl->prefix_off + 8ull * (n + 1));  // range temporaries
+  pl->n_work = work->size();
+  pl->zero_bytes = 16;  // the ticket
+  pl->items_off = 256;
+  pl->work_off = align256d(pl->items_off + (uint64_t)n * sizeof(DecBatchItem));
+  pl->slots_off = align256d(pl->work_off + 8ull * std::max<uint64_t>(1, pl->n_work));  // range temporaries
   pl->ws_total = pl->slots_off + temp_total;
   pl->slot_region = any_ranged ? 1 : 0;
   for (uint32_t i = 0; i < n; ++i)
@@ -1260,9 +1306,11 @@ int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchC
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_decode_batch, kLaneThreads, smem) != cudaSuccess ||
       occ < 1)
     occ = 1;
-  const uint64_t total = (*pre)[n];
-  pl->grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((total + kLaneWarps - 1) / kLaneWarps,
-                                                                (uint64_t)cfg.sm_count * occ));
+  const uint32_t per_sm = std::min<uint32_t>((uint32_t)occ, sched.ctas_per_sm);
+  pl->grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((pl->n_work + kLaneWarps - 1) / kLaneWarps,
+                                                                (uint64_t)cfg.sm_count * per_sm));
+  pl->sched = sched;
+  pl->sched.ctas_per_sm = per_sm;
   img->assign(reinterpret_cast<const uint8_t *>(v.data()),
               reinterpret_cast<const uint8_t *>(v.data()) + (size_t)n * sizeof(DecBatchItem));
   return SPRINTZ_OK;
@@ -1271,10 +1319,12 @@ int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchC
 int run_batch_decode(const BatchPlan &pl, cudaStream_t stream) {
   uint8_t *ws = (uint8_t *)pl.ws;
   const DecBatchItem *items = reinterpret_cast<const DecBatchItem *>(ws + pl.items_off);
-  const uint64_t *pre = reinterpret_cast<const uint64_t *>(ws + pl.prefix_off);
+  const uint64_t *work = reinterpret_cast<const uint64_t *>(ws + pl.work_off);
+  if (cudaMemsetAsync(ws, 0, pl.zero_bytes, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
   k_decode_batch_tails<<<pl.n, 128, 0, stream>>>(items);
-  k_decode_batch<<<pl.grid, kLaneThreads, (uint64_t)kLaneWarps * pl.region, stream>>>(items, pre, pl.n,
-                                                                                     pl.region);
+  if (pl.n_work)
+    k_decode_batch<<<pl.grid, kLaneThreads, (uint64_t)kLaneWarps * pl.region, stream>>>(
+        items, work, pl.n_work, reinterpret_cast<unsigned long long *>(ws), pl.region);
   if (pl.slot_region) k_decode_batch_rows<<<dim3(8, pl.n), 256, 0, stream>>>(items);
   return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
 }
@@ -1345,6 +1395,144 @@ int launch_decode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint6
     else
       k_decode<16><<<pl.grid, kDecThreads, pl.smem, stream>>>(p);
   }
+  return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
+}
+
+
+// ---- ranges of rows ----------------------------------------------------------
+
+bool decode_chunks_supported(const Geom &g, const LaunchCfg &cfg) {
+  if (g.huffman || g.n_chunks == 0) return false;
+  if (g.D <= 32) return g.max_body < (1ull << 28) && lane_ring_plan(g, cfg, dec_ring_segments(), dec_staged((int)g.D)).per_warp;
+  const uint64_t smem = (((uint64_t)g.hdr_bytes + (uint64_t)g.G * g.D * g.w + 8 + 15) & ~15ull);
+  return g.n_chunks <= 0x7FFFFFFFull && smem <= (uint64_t)cfg.max_smem_optin;
+}
+
+int launch_decode_chunks(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint64_t src_size,
+                         uint32_t c_begin, uint32_t c_end, uint8_t *dst, uint64_t dst_cap, int *d_status,
+                         cudaStream_t stream) {
+  if (!decode_chunks_supported(g, cfg) || ((uintptr_t)dst & 7) != 0) return SPRINTZ_ERR_UNSUPPORTED;
+  if (c_end <= c_begin) return SPRINTZ_OK;
+  DecParams p{};
+  p.src = src;
+  p.src_size = src_size;
+  p.dst = dst;
+  p.dst_cap = dst_cap;
+  p.status = d_status;
+  p.g = g;
+  p.c_begin = c_begin;
+  p.c_end = c_end;
+  p.pf_win = 2048;
+  const uint64_t n = c_end - c_begin;
+  if (g.D <= 32) {
+    LaneRing rg = lane_ring_plan(g, cfg, dec_ring_segments(), dec_staged((int)g.D));
+    const uint64_t K = 32 / g.D;
+    const uint64_t grid = ((n + K - 1) / K + kLaneWarps - 1) / kLaneWarps;
+    if (grid > 0x7FFFFFFFull) return SPRINTZ_ERR_INVALID_ARG;
+    const uint64_t smem = (uint64_t)rg.per_warp * kLaneWarps;
+    const void *fn = g.w == 8 ? lane_decoder<8>(g.D) : lane_decoder<16>(g.D);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return SPRINTZ_ERR_CUDA;
+    void *args[] = {&p, &rg};
+    if (cudaLaunchKernel(fn, dim3((uint32_t)grid), dim3(kLaneThreads), args, smem, stream) != cudaSuccess)
+      return SPRINTZ_ERR_CUDA;
+    return SPRINTZ_OK;
+  }
+  const uint32_t threads = (g.D + 31) & ~31u;
+  const uint64_t smem = (((uint64_t)g.hdr_bytes + (uint64_t)g.G * g.D * g.w + 8 + 15) & ~15ull);
+  const void *fn = g.w == 8 ? (const void *)k_decode_wide<8> : (const void *)k_decode_wide<16>;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return SPRINTZ_ERR_CUDA;
+  void *args[] = {&p};
+  if (cudaLaunchKernel(fn, dim3((uint32_t)n), dim3(threads), args, smem, stream) != cudaSuccess)
+    return SPRINTZ_ERR_CUDA;
+  return SPRINTZ_OK;
+}
+
+// Rows [row_begin, row_end) to out: the rows of the decoded chunks held at
+// tmp (from row tmp_row0 on), then the raw tail rows from the stream; the
+// header is checked first (every CTA checks it, one reports it).
+__global__ void k_decode_rows_finish(DecParams p, uint64_t row_begin, uint64_t row_end, uint64_t tmp_row0,
+                                     const uint8_t *tmp, uint8_t *out) {
+  const Geom &g = p.g;
+  __shared__ uint32_t s_ok;
+  __shared__ uint64_t s_tail_off;
+  if (threadIdx.x == 0) {
+    uint64_t tail_off = 0;
+    const bool ok = header_matches(g, p.src, p.src_size, &tail_off);
+    s_ok = ok;
+    s_tail_off = tail_off;
+    if (!ok && blockIdx.x == 0) set_status(p.status, SPRINTZ_ERR_CORRUPT);
+  }
+  __syncthreads();
+  if (!s_ok) return;
+  const uint64_t rb = (uint64_t)g.D * g.wb;
+  const uint64_t r_full = min(row_end, g.full_rows);
+  const uint64_t n_mid = r_full > row_begin ? (r_full - row_begin) * rb : 0;
+  if (n_mid) grid_copy(out, tmp + (row_begin - tmp_row0) * rb, n_mid);
+  if (row_end > g.full_rows) {
+    const uint64_t t0 = max(row_begin, g.full_rows);
+    grid_copy(out + n_mid, p.src + s_tail_off + (t0 - g.full_rows) * rb, (row_end - t0) * rb);
+  }
+}
+
+// Chunks that cover rows [row_begin, row_end) (none when the rows all lie
+// in the raw tail).
+static void covering_chunks(const Geom &g, uint64_t row_begin, uint64_t row_end, uint32_t *c0, uint32_t *c1) {
+  const uint64_t r_full = std::min<uint64_t>(row_end, g.full_rows);
+  if (r_full > row_begin) {
+    *c0 = (uint32_t)(row_begin / g.chunk_rows);
+    *c1 = (uint32_t)((r_full + g.chunk_rows - 1) / g.chunk_rows);
+  } else {
+    *c0 = *c1 = 0;
+  }
+}
+
+uint64_t decode_rows_workspace_bytes(const Geom &g, const LaunchCfg &cfg, uint64_t row_begin, uint64_t row_end) {
+  const uint64_t rb = (uint64_t)g.D * g.wb;
+  if (decode_chunks_supported(g, cfg)) {
+    uint32_t c0, c1;
+    covering_chunks(g, row_begin, row_end, &c0, &c1);
+    const uint64_t r1 = std::min<uint64_t>((uint64_t)c1 * g.chunk_rows, g.full_rows);
+    return c1 > c0 ? align256d((r1 - (uint64_t)c0 * g.chunk_rows) * rb) : 0;
+  }
+  // every chunk decoded by the whole-stream decoder, then the rows copied
+  const uint64_t inner = g.huffman ? huff_decode_workspace_bytes(g, cfg) : decode_workspace_bytes(g, cfg);
+  return align256d(g.rows * rb) + inner;
+}
+
+int launch_decode_rows(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint64_t src_size,
+                       uint64_t row_begin, uint64_t row_end, uint8_t *out, uint8_t *ws, uint64_t ws_bytes,
+                       int *d_status, cudaStream_t stream) {
+  if (row_end <= row_begin) return SPRINTZ_OK;
+  if (ws_bytes < decode_rows_workspace_bytes(g, cfg, row_begin, row_end)) return SPRINTZ_ERR_WS_TOO_SMALL;
+  DecParams p{};
+  p.src = src;
+  p.src_size = src_size;
+  p.status = d_status;
+  p.g = g;
+  const uint64_t rb = (uint64_t)g.D * g.wb;
+  uint64_t tmp_row0 = 0;
+  int rc = SPRINTZ_OK;
+  if (decode_chunks_supported(g, cfg)) {
+    uint32_t c0, c1;
+    covering_chunks(g, row_begin, row_end, &c0, &c1);
+    tmp_row0 = (uint64_t)c0 * g.chunk_rows;
+    const uint64_t r1 = std::min<uint64_t>((uint64_t)c1 * g.chunk_rows, g.full_rows);
+    if (c1 > c0) rc = launch_decode_chunks(g, cfg, src, src_size, c0, c1, ws, (r1 - tmp_row0) * rb, d_status, stream);
+  } else {
+    const uint64_t tb = align256d(g.rows * rb);
+    rc = g.huffman ? launch_decode_huffman(g, cfg, src, src_size, ws, g.rows * rb, ws + tb, ws_bytes - tb, d_status,
+                                           stream)
+                   : launch_decode(g, cfg, src, src_size, ws, g.rows * rb, ws + tb, ws_bytes - tb, d_status, stream);
+  }
+  if (rc != SPRINTZ_OK) return rc;
+  const uint64_t bytes = (row_end - row_begin) * rb;
+  const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((bytes + 4095) / 4096,
+                                                                          (uint64_t)cfg.sm_count * 8));
+  k_decode_rows_finish<<<grid, 256, 0, stream>>>(p, row_begin, row_end, tmp_row0, ws, out);
   return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
 }
 

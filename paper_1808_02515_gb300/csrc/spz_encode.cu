@@ -72,8 +72,18 @@ struct EncParams {
   uint8_t *scratch;
   uint64_t scratch_per_cta;
   uint32_t stage_rows;  // 1: rows and working arrays in shared memory
+  uint32_t spin_limit;  // look-back polls before SPRINTZ_ERR_TIMEOUT (0: kSpinLimit)
   Geom g;
 };
+
+// Clear the ticket and look-back words of a single-stream launch; the
+// failure test starts the ticket at 1, so that chunk group 0 is never taken
+// and its successors' look-backs run out.
+static int init_ticket(uint8_t *ws, uint64_t zero_bytes, const LaunchCfg &cfg, cudaStream_t stream) {
+  if (cudaMemsetAsync(ws, 0, zero_bytes, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  if (cfg.skip_first_group && cudaMemsetAsync(ws, 1, 1, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  return SPRINTZ_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Small device helpers
@@ -406,7 +416,7 @@ __device__ void encode_chunk(const EncParams &p, uint8_t *mem, uint32_t c) {
         uint64_t v = ld_acquire_u64(&lb[k]);
         uint64_t flag = v & ~kValueMask;
         if (flag == 0) {
-          if (++spins > kSpinLimit) {
+          if (++spins > (p.spin_limit ? p.spin_limit : kSpinLimit)) {
             set_status(p.status, SPRINTZ_ERR_TIMEOUT);
             break;
           }
@@ -539,7 +549,9 @@ __device__ __forceinline__ void ring_or(uint32_t *ring, uint32_t ring_words, uin
 // would invalidate the SM's L1 on every poll).  Polls back off exponentially
 // and are bounded (SPRINTZ_ERR_TIMEOUT).  Returns the exclusive prefix in
 // every lane.
-__device__ uint64_t lookback_warp(uint64_t *lb, uint32_t grp, uint64_t total, int *status) {
+__device__ uint64_t lookback_warp(uint64_t *lb, uint32_t grp, uint64_t total, int *status,
+                                  uint32_t spin_limit) {
+  const uint32_t limit = spin_limit ? spin_limit : kSpinLimit;
   const uint32_t lane = threadIdx.x & 31;
   if (grp == 0) {
     if (lane == 0) st_relaxed_u64(&lb[0], kFlagPrefix | total);
@@ -566,7 +578,7 @@ __device__ uint64_t lookback_warp(uint64_t *lb, uint32_t grp, uint64_t total, in
     if (done) break;
     k -= take;
     if (take == 0) {
-      if (++spins > kSpinLimit) {
+      if (++spins > limit) {
         if (lane == 0) set_status(status, SPRINTZ_ERR_TIMEOUT);
         break;
       }
@@ -841,7 +853,7 @@ __global__ void __launch_bounds__(kEncLaneThreads) k_encode_lanes(EncParams p, E
     const uint64_t group_total = __shfl_sync(0xFFFFFFFFu, v, 31);
     const uint64_t excl = __shfl_sync(0xFFFFFFFFu, v, seg0) - __shfl_sync(0xFFFFFFFFu, (live && j == 0) ? S : 0ull, seg0);
     // look-back over groups
-    const uint64_t prefix = lookback_warp(p.lookback, grp, group_total, p.status);
+    const uint64_t prefix = lookback_warp(p.lookback, grp, group_total, p.status, p.spin_limit);
     const uint64_t off = prefix + excl;
 
     // pass B: the body at its place
@@ -949,15 +961,17 @@ struct EncSlotCfg {
   uint32_t window;       // ring bytes per chunk (power of two)
   uint32_t n_groups;
   uint32_t slot_stride;  // bytes per chunk slot (multiple of 32, >= the largest body + 32)
+  uint32_t pf_bytes;     // L2 bulk prefetch of the chunk's rows, this far ahead (0: none)
   uint8_t *slots;        // [warp][K] slots
 };
 
 // Encode chunk group `grp` of one stream with one warp: wsm is the warp's
 // shared region (stage, then K rings), wslots its K body slots.
-// PF: prefetch the chunks' rows into L2 ahead of the reads (the batched
-// kernel, with few warps per SM, gains; the single-stream kernel, whose one
-// wave of warps covers the whole input, loses: its windows evict each other).
-template <int W, int DT, bool PF = false>
+// cfg.pf_bytes > 0 prefetches the chunks' rows into L2 ahead of the reads
+// (the batched kernel, whose streams are short, can gain; the single-stream
+// kernel, whose one wave of warps covers the whole input, loses: its windows
+// evict each other).
+template <int W, int DT>
 __device__ __forceinline__ void encode_group_slots(const EncParams &p, const EncSlotCfg &cfg, uint32_t grp,
                                                    uint8_t *wsm, uint8_t *wslots) {
   const Geom &g = p.g;
@@ -1017,8 +1031,9 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
     const uintptr_t rows_lo = (uintptr_t)(p.src + row0 * D * wb);
     const uintptr_t rows_hi = rows_lo + (uint64_t)nb * kBlockRows * D * wb;
     uintptr_t pf = rows_lo;
-    if (PF && live && j == 0) {
-      const uintptr_t e2 = min(rows_hi, pf + 8192);
+    const uint32_t pfb = cfg.pf_bytes;
+    if (pfb && live && j == 0) {
+      const uintptr_t e2 = min(rows_hi, pf + 2 * pfb);
       prefetch_l2_range(pf, e2, rows_lo, rows_hi);
       pf = e2;
     }
@@ -1226,8 +1241,8 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
           }
           end_record(size);
         }
-        if (PF && j == 0 && pf < rows_hi && rows_lo + (uint64_t)(b + 1) * kBlockRows * D * wb + 4096 > pf) {
-          const uintptr_t e2 = min(rows_hi, pf + 4096);
+        if (pfb && j == 0 && pf < rows_hi && rows_lo + (uint64_t)(b + 1) * kBlockRows * D * wb + pfb > pf) {
+          const uintptr_t e2 = min(rows_hi, pf + pfb);
           prefetch_l2_range(pf, e2, rows_lo, rows_hi);
           pf = e2;
         }
@@ -1255,7 +1270,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
     }
     const uint64_t group_total = __shfl_sync(0xFFFFFFFFu, v, 31);
     const uint64_t excl = __shfl_sync(0xFFFFFFFFu, v, seg0) - __shfl_sync(0xFFFFFFFFu, (uint64_t)S, seg0);
-    const uint64_t prefix = lookback_warp(p.lookback, grp, group_total, p.status);
+    const uint64_t prefix = lookback_warp(p.lookback, grp, group_total, p.status, p.spin_limit);
     const uint64_t off = prefix + excl;
 
     // the body to its place: bytes up to a 16-byte boundary, 16-byte units
@@ -1366,36 +1381,62 @@ struct EncBatchItem {
   EncParams p;    // its own look-back words, destination and size word
   EncSlotCfg cfg;
 };
+static_assert(sizeof(EncBatchItem) % 8 == 0, "descriptors are copied in 8-byte words");
 
-// Batched encode: the chunk groups of all streams, in stream order, form one
-// work list taken from a single ticket, so a group's look-back only waits on
-// earlier groups of its own stream, all of which are already running.
-__global__ void __launch_bounds__(kEncLaneThreads) k_encode_batch(const EncBatchItem *items,
-                                                                 const uint64_t *gprefix, uint32_t n,
-                                                                 uint32_t *ticket, uint32_t region,
-                                                                 uint8_t *slots, uint64_t slot_region) {
+// One chunk group of a batch item, through the slot encoder specialised for
+// the item's column count (a call per group keeps each variant's code apart).
+template <int W, int DT>
+__device__ __noinline__ void encode_batch_group(const EncBatchItem &it, uint32_t grp, uint8_t *wsm,
+                                                uint8_t *wslots) {
+  encode_group_slots<W, DT>(it.p, it.cfg, grp, wsm, wslots);
+}
+
+// Variant table: [w == 16][D] (D = 0: any column count up to 32).  One
+// indirect call site for every variant keeps the kernel's frame small.
+typedef void (*EncBatchGroupFn)(const EncBatchItem &, uint32_t, uint8_t *, uint8_t *);
+#define SPZ_ENC_ROW(W)                                                                                  \
+  {encode_batch_group<W, 0>,  encode_batch_group<W, 1>,  encode_batch_group<W, 2>,                      \
+   encode_batch_group<W, 3>,  encode_batch_group<W, 4>,  encode_batch_group<W, 5>,                      \
+   encode_batch_group<W, 6>,  encode_batch_group<W, 7>,  encode_batch_group<W, 8>,                      \
+   encode_batch_group<W, 9>,  encode_batch_group<W, 10>, encode_batch_group<W, 11>,                     \
+   encode_batch_group<W, 12>, encode_batch_group<W, 13>, encode_batch_group<W, 14>,                     \
+   encode_batch_group<W, 15>, encode_batch_group<W, 16>}
+__device__ EncBatchGroupFn g_enc_batch_fns[2][17] = {SPZ_ENC_ROW(8), SPZ_ENC_ROW(16)};
+#undef SPZ_ENC_ROW
+
+// Batched encode: persistent warps take work entries (stream, chunk group)
+// from one ticket.  The host orders the list by (w, D) class, and every
+// stream's groups in increasing order, so a group's look-back only waits on
+// earlier groups of its own stream, all of which were taken earlier and are
+// running or done.  Each warp copies its item's descriptor into shared
+// memory once per group.
+__global__ void __launch_bounds__(kEncLaneThreads, 7) k_encode_batch(const EncBatchItem *items,
+                                                                    const uint64_t *work, uint64_t n_work,
+                                                                    uint32_t *ticket, uint32_t region,
+                                                                    uint8_t *slots, uint64_t slot_region) {
   extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ __align__(16) EncBatchItem s_it[kEncLaneWarps];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t *wsm = smem + (uint64_t)warp * region;
   const uint64_t gwarp = (uint64_t)blockIdx.x * kEncLaneWarps + warp;
   uint8_t *wslots = slots + gwarp * slot_region;
-  const uint64_t total = gprefix[n];
+  constexpr uint32_t kWords = sizeof(EncBatchItem) / 8;
   for (;;) {
-    unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(reinterpret_cast<unsigned long long *>(ticket), 1ull);
-    item = __shfl_sync(0xFFFFFFFFu, item, 0);
-    if (item >= total) break;
-    uint32_t lo = 0, hi = n;
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) / 2;
-      if (gprefix[mid] <= item) lo = mid; else hi = mid;
-    }
-    const EncBatchItem it = items[lo];
-    const uint32_t grp = (uint32_t)(item - gprefix[lo]);
-    if (it.p.g.w == 8)
-      encode_group_slots<8, 0, true>(it.p, it.cfg, grp, wsm, wslots);
-    else
-      encode_group_slots<16, 0, true>(it.p, it.cfg, grp, wsm, wslots);
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(reinterpret_cast<unsigned long long *>(ticket), 1ull);
+    t = __shfl_sync(0xFFFFFFFFu, t, 0);
+    if (t >= n_work) break;
+    const uint64_t e = __ldg(work + t);
+    const uint32_t s = (uint32_t)(e >> kWorkGroupBits);
+    const uint32_t grp = (uint32_t)(e & ((1ull << kWorkGroupBits) - 1));
+    const uint64_t *from = reinterpret_cast<const uint64_t *>(items + s);
+    uint64_t *to = reinterpret_cast<uint64_t *>(&s_it[warp]);
+    for (uint32_t k = lane; k < kWords; k += 32) to[k] = __ldg(from + k);
+    __syncwarp();
+    const EncBatchItem &it = s_it[warp];
+    const uint32_t D = it.p.g.D;
+    g_enc_batch_fns[it.p.g.w == 16][D <= 16 ? D : 0](it, grp, wsm, wslots);
+    __syncwarp();
   }
 }
 
@@ -1523,6 +1564,8 @@ int launch_encode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint8
   p.out_size = d_out_size;
   p.status = d_status;
   p.g = g;
+  p.spin_limit = cfg.wait_limit;
+  int rc = SPRINTZ_OK;
   if (g.n_chunks == 0) {
     k_encode_tail_only<<<1, 128, 0, stream>>>(p);
     return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
@@ -1546,7 +1589,7 @@ int launch_encode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint8
     const uint64_t want_ctas = (lc.n_groups + kEncLaneWarps - 1) / kEncLaneWarps;
     const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(want_ctas, (uint64_t)cfg.sm_count *
                                                                                    enc_lane_ctas_per_sm()));
-    if (cudaMemsetAsync(ws, 0, 16 + 8ull * lc.n_groups, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+    if ((rc = init_ticket(ws, 16 + 8ull * lc.n_groups, cfg, stream)) != SPRINTZ_OK) return rc;
     if (g.w == 8)
       k_encode_lanes<8><<<(uint32_t)grid, kEncLaneThreads, smem, stream>>>(p, lc);
     else
@@ -1561,7 +1604,7 @@ int launch_encode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint8
   p.scratch = ws + base;
   p.scratch_per_cta = pl.scratch_per_cta;
   p.stage_rows = pl.stage_rows ? 1 : 0;
-  if (cudaMemsetAsync(ws, 0, 16 + 8ull * g.n_chunks, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  if ((rc = init_ticket(ws, 16 + 8ull * g.n_chunks, cfg, stream)) != SPRINTZ_OK) return rc;
   if (g.w == 8)
     k_encode<8><<<pl.grid, kEncThreads, pl.smem, stream>>>(p);
   else
@@ -1776,7 +1819,7 @@ __global__ void __launch_bounds__(1024) k_encode_wide(EncParams p, EncWideCfg cf
 
     // offset of the body: look-back over chunks (warp 0), then the copy
     if (warp == 0) {
-      const uint64_t pre = lookback_warp(p.lookback, c, S, p.status);
+      const uint64_t pre = lookback_warp(p.lookback, c, S, p.status, p.spin_limit);
       if (lane == 0) s_prefix = pre;
     }
     __syncthreads();
@@ -1866,6 +1909,8 @@ static int launch_encode_wide(const Geom &g, const LaunchCfg &cfg, const WidePla
   p.out_size = d_out_size;
   p.status = d_status;
   p.g = g;
+  p.spin_limit = cfg.wait_limit;
+  int rc = SPRINTZ_OK;
   p.ticket = reinterpret_cast<uint32_t *>(ws);
   p.lookback = reinterpret_cast<uint64_t *>(ws + 16);
   EncWideCfg wc = pl.wc;
@@ -1873,7 +1918,7 @@ static int launch_encode_wide(const Geom &g, const LaunchCfg &cfg, const WidePla
   const void *fn = g.w == 8 ? (const void *)k_encode_wide<8> : (const void *)k_encode_wide<16>;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem) != cudaSuccess)
     return SPRINTZ_ERR_CUDA;
-  if (cudaMemsetAsync(ws, 0, 16 + 8ull * g.n_chunks, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  if ((rc = init_ticket(ws, 16 + 8ull * g.n_chunks, cfg, stream)) != SPRINTZ_OK) return rc;
   void *args[] = {&p, &wc};
   if (cudaLaunchKernel(fn, dim3(pl.grid), dim3(pl.threads), args, pl.smem, stream) != cudaSuccess)
     return SPRINTZ_ERR_CUDA;
@@ -1906,6 +1951,8 @@ int launch_encode_fast(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, 
   p.out_size = d_out_size;
   p.status = d_status;
   p.g = g;
+  p.spin_limit = cfg.wait_limit;
+  int rc = SPRINTZ_OK;
   p.ticket = reinterpret_cast<uint32_t *>(ws);
   p.lookback = reinterpret_cast<uint64_t *>(ws + 16);
   EncSlotCfg sc = sp.sc;
@@ -1914,7 +1961,7 @@ int launch_encode_fast(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, 
   if (sp.smem > 48 * 1024 &&
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem) != cudaSuccess)
     return SPRINTZ_ERR_CUDA;
-  if (cudaMemsetAsync(ws, 0, 16 + 8ull * sc.n_groups, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
+  if ((rc = init_ticket(ws, 16 + 8ull * sc.n_groups, cfg, stream)) != SPRINTZ_OK) return rc;
   void *args[] = {&p, &sc};
   if (cudaLaunchKernel(fn, dim3(sp.grid), dim3(kEncLaneThreads), args, sp.smem, stream) != cudaSuccess)
     return SPRINTZ_ERR_CUDA;
@@ -1923,19 +1970,87 @@ int launch_encode_fast(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, 
 
 // ---- batches ----------------------------------------------------------------
 
-static uint32_t enc_batch_ctas_per_sm() {
-  static uint32_t v = [] {
-    const char *e = getenv("SPRINTZ_ENC_BATCH_CTAS_PER_SM");
-    int x = e ? atoi(e) : 0;
-    return (uint32_t)(x > 0 && x <= 32 ? x : 8);
-  }();
-  return v;
+sprintz_schedule batch_default_schedule(int compress) {
+  sprintz_schedule s;
+  s.ctas_per_sm = compress ? 7 : 7;
+  s.ring_segments = 2;
+  s.prefetch_bytes = compress ? 4096 : 2048;
+  s.order = 1;
+  return s;
 }
 
-int plan_batch_encode(const sprintz_batch_item *items, uint32_t n, const LaunchCfg &cfg, int *d_status,
-                      uint8_t *ws, BatchPlan *pl, std::vector<uint8_t> *img, std::vector<uint64_t> *pre) {
+static sprintz_schedule resolve_schedule(const sprintz_schedule &in, int compress) {
+  const sprintz_schedule d = batch_default_schedule(compress);
+  sprintz_schedule s = in;
+  if (!s.ctas_per_sm) s.ctas_per_sm = d.ctas_per_sm;
+  if (s.ring_segments != 2 && s.ring_segments != 4) s.ring_segments = d.ring_segments;
+  if (!s.prefetch_bytes) s.prefetch_bytes = d.prefetch_bytes;
+  if (s.prefetch_bytes != 1) s.prefetch_bytes &= ~15u;
+  if (s.order < 1 || s.order > 3) s.order = d.order;
+  return s;
+}
+
+void batch_work_list(const std::vector<uint32_t> &w, const std::vector<uint32_t> &D,
+                     const std::vector<uint64_t> &groups, const std::vector<uint64_t> &group_bytes,
+                     uint32_t order, std::vector<uint64_t> *work) {
+  const uint32_t n = (uint32_t)w.size();
+  // classes (w, D), heaviest groups first, then by w and D
+  std::vector<uint32_t> idx(n);
+  for (uint32_t i = 0; i < n; ++i) idx[i] = i;
+  auto cls = [&](uint32_t i) { return (uint64_t)w[i] << 32 | D[i]; };
+  std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) {
+    if (cls(a) != cls(b)) {
+      const uint64_t ga = (uint64_t)(32 / D[a]) * D[a] * w[a], gb = (uint64_t)(32 / D[b]) * D[b] * w[b];
+      if (ga != gb) return ga > gb;
+      return cls(a) < cls(b);
+    }
+    if (order == 2 && groups[a] != groups[b]) return groups[a] > groups[b];
+    return a < b;
+  });
+  (void)group_bytes;
+  work->clear();
+  uint64_t total = 0;
+  for (uint32_t i = 0; i < n; ++i) total += groups[i];
+  work->reserve(total);
+  for (uint32_t a = 0; a < n;) {
+    uint32_t b = a;
+    while (b < n && cls(idx[b]) == cls(idx[a])) ++b;
+    if (order == 3) {
+      // round robin: group r of every stream of the class that has one
+      uint64_t rmax = 0;
+      for (uint32_t k = a; k < b; ++k) rmax = std::max<uint64_t>(rmax, groups[idx[k]]);
+      for (uint64_t r = 0; r < rmax; ++r)
+        for (uint32_t k = a; k < b; ++k)
+          if (r < groups[idx[k]]) work->push_back((uint64_t)idx[k] << kWorkGroupBits | r);
+    } else {
+      for (uint32_t k = a; k < b; ++k)
+        for (uint64_t r = 0; r < groups[idx[k]]; ++r) work->push_back((uint64_t)idx[k] << kWorkGroupBits | r);
+    }
+    a = b;
+  }
+}
+
+// CTAs of the batched encoder that fit one SM with `region` shared bytes per warp.
+static uint32_t enc_batch_occupancy(uint32_t region, const LaunchCfg &cfg) {
+  const uint64_t smem = (uint64_t)kEncLaneWarps * region;
+  if (smem > (uint64_t)cfg.max_smem_optin) return 0;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_encode_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_encode_batch, kEncLaneThreads, smem) != cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  return (uint32_t)occ;
+}
+
+int plan_batch_encode(const sprintz_batch_item *items, uint32_t n, const LaunchCfg &cfg,
+                      const sprintz_schedule &sched_in, int *d_status, uint8_t *ws, BatchPlan *pl,
+                      std::vector<uint8_t> *img, std::vector<uint64_t> *work) {
+  if (n > kMaxBatchStreams) return SPRINTZ_ERR_INVALID_ARG;
+  const sprintz_schedule sched = resolve_schedule(sched_in, 1);
   std::vector<EncBatchItem> v(n);
-  pre->assign((size_t)n + 1, 0);
+  std::vector<uint32_t> vw(n), vD(n);
+  std::vector<uint64_t> vgroups(n), vgbytes(n);
   uint64_t lb_words = 0;
   uint32_t region = kEncStage;
   uint64_t slot_region = 16;
@@ -1961,33 +2076,38 @@ int plan_batch_encode(const sprintz_batch_item *items, uint32_t n, const LaunchC
     e.cfg.window = enc_window_bytes(g);
     e.cfg.n_groups = (uint32_t)((g.n_chunks + K - 1) / K);
     e.cfg.slot_stride = (uint32_t)(((g.max_body + 31) & ~31ull) + 32);
+    e.cfg.pf_bytes = sched.prefetch_bytes == 1 ? 0u : sched.prefetch_bytes;
     lb_words += e.cfg.n_groups;
-    (*pre)[i + 1] = (*pre)[i] + e.cfg.n_groups;
-    region = std::max<uint32_t>(region, enc_slot_region(g, e.cfg.window));
-    slot_region = std::max<uint64_t>(slot_region, (uint64_t)K * e.cfg.slot_stride);
+    vw[i] = g.w;
+    vD[i] = g.D;
+    vgroups[i] = e.cfg.n_groups;
+    vgbytes[i] = (uint64_t)K * g.chunk_rows * g.D * g.wb;
+    if (g.n_chunks) {
+      region = std::max<uint32_t>(region, enc_slot_region(g, e.cfg.window));
+      slot_region = std::max<uint64_t>(slot_region, (uint64_t)K * e.cfg.slot_stride);
+    }
   }
+  batch_work_list(vw, vD, vgroups, vgbytes, sched.order, work);
   memset(pl, 0, sizeof(*pl));
   pl->compress = 1;
   pl->n = n;
   pl->region = region;
   pl->slot_region = slot_region;
+  pl->n_work = work->size();
   pl->zero_bytes = 16 + 8 * lb_words;
   pl->items_off = align256(pl->zero_bytes);
-  pl->prefix_off = align256(pl->items_off + (uint64_t)n * sizeof(EncBatchItem));
-  pl->slots_off = align256(pl->prefix_off + 8ull * (n + 1));
-  const uint64_t smem = (uint64_t)kEncLaneWarps * region;
-  if (smem > (uint64_t)cfg.max_smem_optin) return SPRINTZ_ERR_UNSUPPORTED;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_encode_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_encode_batch, kEncLaneThreads, smem) != cudaSuccess ||
-      occ < 1)
-    occ = 1;
-  const uint64_t total = (*pre)[n];
-  const uint64_t per_sm = std::min<uint64_t>((uint64_t)occ, enc_batch_ctas_per_sm());
-  pl->grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((total + kEncLaneWarps - 1) / kEncLaneWarps,
-                                                                (uint64_t)cfg.sm_count * per_sm));
-  pl->ws_total = pl->slots_off + (uint64_t)pl->grid * kEncLaneWarps * slot_region;
+  pl->work_off = align256(pl->items_off + (uint64_t)n * sizeof(EncBatchItem));
+  pl->slots_off = align256(pl->work_off + 8ull * std::max<uint64_t>(1, pl->n_work));
+  const uint32_t occ = enc_batch_occupancy(region, cfg);
+  if (!occ) return SPRINTZ_ERR_UNSUPPORTED;
+  const uint64_t want = (pl->n_work + kEncLaneWarps - 1) / kEncLaneWarps;
+  const uint64_t max_grid = std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)cfg.sm_count * occ));
+  pl->grid = (uint32_t)std::max<uint64_t>(
+      1, std::min<uint64_t>(want, (uint64_t)cfg.sm_count * std::min<uint32_t>(occ, sched.ctas_per_sm)));
+  // the workspace holds the slots of the largest grid any schedule may take
+  pl->ws_total = pl->slots_off + max_grid * kEncLaneWarps * slot_region;
+  pl->sched = sched;
+  pl->sched.ctas_per_sm = std::min<uint32_t>(occ, sched.ctas_per_sm);
   if (ws)
     for (auto &e : v) e.p.ticket = reinterpret_cast<uint32_t *>(ws);
   img->assign(reinterpret_cast<const uint8_t *>(v.data()),
@@ -1998,11 +2118,12 @@ int plan_batch_encode(const sprintz_batch_item *items, uint32_t n, const LaunchC
 int run_batch_encode(const BatchPlan &pl, cudaStream_t stream) {
   uint8_t *ws = (uint8_t *)pl.ws;
   const EncBatchItem *items = reinterpret_cast<const EncBatchItem *>(ws + pl.items_off);
-  const uint64_t *pre = reinterpret_cast<const uint64_t *>(ws + pl.prefix_off);
+  const uint64_t *work = reinterpret_cast<const uint64_t *>(ws + pl.work_off);
   if (cudaMemsetAsync(ws, 0, pl.zero_bytes, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
   k_encode_batch_tails<<<pl.n, 128, 0, stream>>>(items);
-  k_encode_batch<<<pl.grid, kEncLaneThreads, (uint64_t)kEncLaneWarps * pl.region, stream>>>(
-      items, pre, pl.n, reinterpret_cast<uint32_t *>(ws), pl.region, ws + pl.slots_off, pl.slot_region);
+  if (pl.n_work)
+    k_encode_batch<<<pl.grid, kEncLaneThreads, (uint64_t)kEncLaneWarps * pl.region, stream>>>(
+        items, work, pl.n_work, reinterpret_cast<uint32_t *>(ws), pl.region, ws + pl.slots_off, pl.slot_region);
   return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
 }
 
@@ -2023,9 +2144,11 @@ int run_batch_encode(const BatchPlan &pl, cudaStream_t stream) {
 
 namespace spz {
 
-constexpr uint64_t kNoAllocMaxChunks = 65536;                        // chunks per call
-constexpr uint64_t kNoAllocStatusOff = 16 + 8 * kNoAllocMaxChunks;   // ticket + look-back words
-constexpr uint64_t kNoAllocBytes = kNoAllocStatusOff + 256;          // + status word, padding
+constexpr uint64_t kNoAllocMaxChunks = 65536;  // chunks per call
+// ticket + one look-back word per chunk, rounded up as the encoders' own
+// workspace layout rounds it, then the status word
+constexpr uint64_t kNoAllocStatusOff = (16 + 8 * kNoAllocMaxChunks + 255) & ~255ull;
+constexpr uint64_t kNoAllocBytes = kNoAllocStatusOff + 256;
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];
 
@@ -2059,7 +2182,8 @@ extern "C" int sprintz_compress_noalloc(const void *src, uint64_t rows, uint32_t
   if (cudaGetDevice(&dev) != cudaSuccess) return SPRINTZ_ERR_CUDA;
   if (dev < 0 || dev >= kNoAllocMaxDevices) return SPRINTZ_ERR_UNSUPPORTED;
   NoAllocDevice &nd = g_noalloc_dev[dev];
-  // first call on this device (device current): find the array's address
+  // first call on this device (device current): find the array's address.
+  // It is kept for the process's life; a cudaDeviceReset() makes it stale.
   std::call_once(nd.once, [&nd, dev] {
     void *ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess ||
@@ -2073,9 +2197,16 @@ extern "C" int sprintz_compress_noalloc(const void *src, uint64_t rows, uint32_t
   });
   if (nd.rc != SPRINTZ_OK) return nd.rc;
   // the fixed array bounds the call: at most kNoAllocMaxChunks chunks, and no
-  // chunk so large that the encoder would need per-block global scratch
-  if (g.n_chunks > kNoAllocMaxChunks || encode_workspace_basic(g, nd.cfg) > kNoAllocStatusOff)
-    return SPRINTZ_ERR_WS_TOO_SMALL;
+  // chunk so large that the encoder would need per-block global scratch.
+  // The scratch needed is that of the path launch_encode() takes: the lane
+  // encoder (D <= 32, 8-byte-aligned samples) needs the ticket and one word
+  // per chunk; the CTA-per-chunk encoder also its per-CTA arrays when a chunk
+  // does not fit shared memory.
+  const bool lane_path = g.D <= 32 && ((uintptr_t)src & 7) == 0;
+  const uint64_t need = g.n_chunks == 0 ? 0
+                        : lane_path     ? 16 + 8ull * g.n_chunks
+                                        : encode_workspace_basic(g, nd.cfg);
+  if (g.n_chunks > kNoAllocMaxChunks || need > kNoAllocStatusOff) return SPRINTZ_ERR_WS_TOO_SMALL;
   int *status = reinterpret_cast<int *>(nd.ptr + kNoAllocStatusOff);
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return SPRINTZ_ERR_CUDA;

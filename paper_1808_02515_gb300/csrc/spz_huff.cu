@@ -10,14 +10,25 @@
 //   raw       a segment whose coded bytes (each chunk padded to a byte) are not
 //             fewer than its packed bytes keeps an all-zero table and raw bodies.
 //
+//   sub-blocks each chunk's code is cut into n = ceil(packed / 2048) sub-blocks
+//             of about equal packed size, each padded to a byte and preceded
+//             (after the first) by a u32 jump-table offset, so that every
+//             sub-block decodes on its own.
+//
 // Encode: the regular encoder writes the Huffman-free stream P into the
-// workspace; k_huff_build (one CTA per segment) histograms the segment's
-// packed bytes, builds its lengths and table and sizes every chunk's code;
-// k_huff_scan places the segments; k_huff_encode (one CTA per segment) writes
-// the coded chunks, the chunk table and, in the last segment, header and tail.
-// Decode: k_huff_decode (one CTA per segment, one thread per chunk) decodes
-// each chunk's bitstream with an 11-bit lookup table into a Huffman-free
-// stream in the workspace, which the regular decoder then decodes.
+// workspace; k_huff_hist (CTAs over 64 KB slices of a segment) counts the
+// segment's packed bytes; k_huff_lengths (a CTA per segment) runs
+// package-merge and builds the canonical code table; k_huff_sizes (a warp per
+// chunk) sums the coded bits of every sub-block; k_huff_decide (a CTA per
+// segment) chooses raw or coded and places the chunks inside the segment;
+// k_huff_scan places the segments; k_huff_encode (a warp per sub-block)
+// writes the coded bytes, the jump tables and the chunk table, and
+// k_huff_enc_finish the header and the raw tail.
+// Decode: k_huff_dec_prep (a CTA per segment) checks the table (lengths <= 11,
+// Kraft), builds its 11-bit lookup table and maps the segment's sub-blocks to
+// their chunks; k_huff_decode (a thread per sub-block) decodes each sub-block
+// into a Huffman-free stream in the workspace, and k_huff_dec_finish writes
+// its header and tail; the regular decoder then decodes that stream.
 #include <algorithm>
 
 #include "spz_common.cuh"

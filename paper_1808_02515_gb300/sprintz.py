@@ -51,6 +51,27 @@ class _BatchItem(ctypes.Structure):
                 ("row_begin", ctypes.c_uint64), ("row_end", ctypes.c_uint64)]
 
 
+class _Schedule(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_uint32), ("ring_segments", ctypes.c_uint32),
+                ("prefetch_bytes", ctypes.c_uint32), ("order", ctypes.c_uint32)]
+
+
+@dataclass(frozen=True)
+class Schedule:
+    """Launch schedule of a batched launch (sprintz_schedule); 0 = default."""
+    ctas_per_sm: int = 0
+    ring_segments: int = 0
+    prefetch_bytes: int = 0
+    order: int = 0
+
+    def c(self) -> _Schedule:
+        return _Schedule(self.ctas_per_sm, self.ring_segments, self.prefetch_bytes, self.order)
+
+    @staticmethod
+    def of(c: _Schedule) -> "Schedule":
+        return Schedule(c.ctas_per_sm, c.ring_segments, c.prefetch_bytes, c.order)
+
+
 @dataclass(frozen=True)
 class Opts:
     forecaster: int = FIRE
@@ -97,6 +118,16 @@ def lib() -> ctypes.CDLL:
         L.sprintz_compress.argtypes = [vp, vp, u64, u32, u32, PO, vp, u64, vp, vp, u64, vp]
         L.sprintz_decompress.restype = i32
         L.sprintz_decompress.argtypes = [vp, vp, u64, PI, vp, u64, vp, u64, vp]
+        L.sprintz_decompress_rows_workspace_size.restype = u64
+        L.sprintz_decompress_rows_workspace_size.argtypes = [PI, u64, u64]
+        L.sprintz_decompress_rows.restype = i32
+        L.sprintz_decompress_rows.argtypes = [vp, vp, u64, PI, u64, u64, vp, u64, vp, u64, vp]
+        L.sprintz_append_workspace_size.restype = u64
+        L.sprintz_append_workspace_size.argtypes = [PI, u64]
+        L.sprintz_append.restype = i32
+        L.sprintz_append.argtypes = [vp, vp, u64, PI, vp, u64, vp, u64, vp, vp, u64, vp]
+        L.sprintz_ctx_set_failure_test.restype = i32
+        L.sprintz_ctx_set_failure_test.argtypes = [vp, u32, u32]
         L.sprintz_compress_noalloc.restype = i32
         L.sprintz_compress_noalloc.argtypes = [vp, u64, u32, u32, PO, vp, u64, vp, vp]
         PB = ctypes.POINTER(_BatchItem)
@@ -106,6 +137,13 @@ def lib() -> ctypes.CDLL:
         L.sprintz_batch_plan.argtypes = [vp, PB, u32, i32, vp, u64, vp]
         L.sprintz_batch_run.restype = i32
         L.sprintz_batch_run.argtypes = [vp, vp, u64, vp]
+        PS = ctypes.POINTER(_Schedule)
+        L.sprintz_batch_plan_schedule.restype = i32
+        L.sprintz_batch_plan_schedule.argtypes = [vp, PB, u32, i32, PS, vp, u64, vp]
+        L.sprintz_batch_schedule.restype = i32
+        L.sprintz_batch_schedule.argtypes = [vp, PS]
+        L.sprintz_batch_autotune.restype = i32
+        L.sprintz_batch_autotune.argtypes = [vp, PB, u32, i32, vp, u64, vp, PS, ctypes.POINTER(ctypes.c_float)]
         L.sprintz_forecast.restype = i32
         L.sprintz_forecast.argtypes = [vp, vp, u64, u32, u32, u32, u32, u32, i32, vp, vp]
         L.sprintz_quant_workspace_size.restype = u64
@@ -351,6 +389,58 @@ class Codec:
         self.decompress_into(src, n, info, dst, ws, stream)
         return dst
 
+    def decompress_rows(self, src, info: Info, row_begin: int, row_end: int, src_size: int | None = None,
+                        out=None, stream=None):
+        """sprintz_decompress_rows: rows [row_begin, row_end) of a device
+        stream as a (row_end - row_begin, D) tensor (only the covering chunks
+        are decoded)."""
+        torch = self.torch
+        dt = torch.uint8 if info.w == 8 else torch.int16
+        n = max(0, row_end - row_begin)
+        y = out if out is not None else torch.empty((n, info.D), dtype=dt, device=src.device)
+        ci = info.c()
+        wsn = int(lib().sprintz_decompress_rows_workspace_size(ctypes.byref(ci), row_begin, row_end))
+        ws = torch.empty(max(wsn, 1), dtype=torch.uint8, device=src.device)
+        rc = lib().sprintz_decompress_rows(self.ctx, ctypes.c_void_p(src.data_ptr()),
+                                           src_size if src_size is not None else src.numel(), ctypes.byref(ci),
+                                           row_begin, row_end, ctypes.c_void_p(y.data_ptr() if n else 0),
+                                           y.numel() * y.element_size(), ctypes.c_void_p(ws.data_ptr()), wsn,
+                                           self._stream(stream))
+        _check(rc, "sprintz_decompress_rows")
+        self._keep = ws
+        return y
+
+    def append(self, src, info: Info, rows, src_size: int | None = None, stream=None):
+        """sprintz_append: the stream of the old series followed by `rows`
+        ((n, D) device tensor of the stream's w). Returns (dst, size)."""
+        torch = self.torch
+        if rows.dim() == 1:
+            rows = rows.view(-1, 1)
+        rows = rows.contiguous()
+        n = rows.shape[0]
+        ci = info.c()
+        cap = max_compressed_size(info.rows + n, info.D, info.w, info.opts)
+        dst = torch.empty(cap, dtype=torch.uint8, device=src.device)
+        size = torch.zeros(1, dtype=torch.int64, device=src.device)
+        wsn = int(lib().sprintz_append_workspace_size(ctypes.byref(ci), n))
+        if wsn == 0:
+            raise SprintzError(ERR_UNSUPPORTED if info.opts.huffman else ERR_INVALID_ARG,
+                               "sprintz_append_workspace_size")
+        ws = torch.empty(wsn, dtype=torch.uint8, device=src.device)
+        rc = lib().sprintz_append(self.ctx, ctypes.c_void_p(src.data_ptr()),
+                                  src_size if src_size is not None else src.numel(), ctypes.byref(ci),
+                                  ctypes.c_void_p(rows.data_ptr() if n else 0), n, ctypes.c_void_p(dst.data_ptr()),
+                                  cap, ctypes.c_void_p(size.data_ptr()), ctypes.c_void_p(ws.data_ptr()), wsn,
+                                  self._stream(stream))
+        _check(rc, "sprintz_append")
+        self._keep = ws
+        return dst, size
+
+    def set_failure_test(self, wait_limit: int = 0, skip_first_group: int = 0) -> None:
+        """sprintz_ctx_set_failure_test (0, 0 = normal use)."""
+        _check(lib().sprintz_ctx_set_failure_test(self.ctx, wait_limit, skip_first_group),
+               "sprintz_ctx_set_failure_test")
+
     def status(self, stream=None) -> int:
         return int(lib().sprintz_get_status(self.ctx, self._stream(stream)))
 
@@ -367,47 +457,71 @@ class Codec:
                                 dsts[k][1], ctypes.c_void_p(out_sizes[k]), rows, D, w, o.c(), rb, re_)
         return arr
 
-    def batch_plan_run(self, arr, compress: int, stream=None):
-        """Size a workspace, plan the batch into it and run it once; returns
-        the workspace (keep it to call batch_run again)."""
+    def batch_plan_run(self, arr, compress: int, stream=None, schedule: "Schedule | None" = None,
+                       autotune: bool = False, run: bool = True):
+        """Size a workspace, plan the batch into it (with `schedule`, or the
+        context's remembered/default one; autotune=True searches for the
+        fastest schedule first, running the batch several times) and run it
+        once; returns the workspace (keep it to call batch_run again)."""
         n = len(arr)
         wsn = int(lib().sprintz_batch_workspace_size(self.ctx, arr, n, compress))
         if wsn == 0:
             raise SprintzError(ERR_INVALID_ARG, "sprintz_batch_workspace_size")
         ws = self.torch.empty(wsn, dtype=self.torch.uint8, device=f"cuda:{self.device}")
-        _check(lib().sprintz_batch_plan(self.ctx, arr, n, compress, ctypes.c_void_p(ws.data_ptr()), wsn,
-                                        self._stream(stream)), "sprintz_batch_plan")
-        self.batch_run(ws, stream)
+        wp, st = ctypes.c_void_p(ws.data_ptr()), self._stream(stream)
+        if autotune:
+            chosen, ms = _Schedule(), ctypes.c_float()
+            _check(lib().sprintz_batch_autotune(self.ctx, arr, n, compress, wp, wsn, st, ctypes.byref(chosen),
+                                                ctypes.byref(ms)), "sprintz_batch_autotune")
+            self.last_tune = (Schedule.of(chosen), float(ms.value))
+        elif schedule is not None:
+            sc = schedule.c()
+            _check(lib().sprintz_batch_plan_schedule(self.ctx, arr, n, compress, ctypes.byref(sc), wp, wsn, st),
+                   "sprintz_batch_plan_schedule")
+        else:
+            _check(lib().sprintz_batch_plan(self.ctx, arr, n, compress, wp, wsn, st), "sprintz_batch_plan")
+        if run:
+            self.batch_run(ws, stream)
         return ws
+
+    def batch_schedule(self) -> Schedule:
+        """The resolved schedule of the current plan."""
+        c = _Schedule()
+        _check(lib().sprintz_batch_schedule(self.ctx, ctypes.byref(c)), "sprintz_batch_schedule")
+        return Schedule.of(c)
 
     def batch_run(self, ws, stream=None) -> None:
         _check(lib().sprintz_batch_run(self.ctx, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                        self._stream(stream)), "sprintz_batch_run")
 
-    def compress_batch(self, xs, opts, stream=None):
+    def compress_batch(self, xs, opts, stream=None, schedule=None, autotune=False, bufs=None, sizes=None):
         """Compress a list of (rows, D) uint8/16-bit device tensors in one
         batched launch; `opts` is one Opts or one per stream. Returns
-        (streams, sizes, ws): stream buffers, a device int64 tensor of sizes,
-        and the planned workspace."""
+        (streams, sizes, ws): stream buffers (`bufs` if given: uint8 tensors
+        of at least max_compressed_size bytes each), a device int64 tensor of
+        sizes (`sizes` if given), and the planned workspace."""
         torch = self.torch
         n = len(xs)
         ol = list(opts) if isinstance(opts, (list, tuple)) else [opts] * n
         shapes, srcs, dsts = [], [], []
-        sizes = torch.zeros(n, dtype=torch.int64, device=xs[0].device)
+        if sizes is None:
+            sizes = torch.zeros(n, dtype=torch.int64, device=xs[0].device)
+        given = bufs
         bufs = []
-        for x, o in zip(xs, ol):
+        for k, (x, o) in enumerate(zip(xs, ol)):
             x2 = x.view(-1, 1) if x.dim() == 1 else x
             rows, D = x2.shape
             w = 8 if x2.dtype == torch.uint8 else 16
             cap = max_compressed_size(rows, D, w, o)
-            buf = torch.empty(cap, dtype=torch.uint8, device=x.device)
+            buf = given[k] if given is not None else torch.empty(cap, dtype=torch.uint8, device=x.device)
+            cap = buf.numel()
             bufs.append(buf)
             shapes.append((rows, D, w, o))
             srcs.append(x2.data_ptr() if rows else 0)
             dsts.append((buf.data_ptr(), cap))
         arr = self._items(shapes, srcs, [0] * n, dsts,
                           [sizes.data_ptr() + 8 * k for k in range(n)])
-        ws = self.batch_plan_run(arr, 1, stream)
+        ws = self.batch_plan_run(arr, 1, stream, schedule=schedule, autotune=autotune)
         return bufs, sizes, ws
 
     def decompress_ranges(self, streams, infos, sizes, ranges, outs=None, stream=None):
@@ -427,20 +541,21 @@ class Codec:
         ws = self.batch_plan_run(arr, 0, stream)
         return res, ws
 
-    def decompress_batch(self, streams, infos, sizes, stream=None):
+    def decompress_batch(self, streams, infos, sizes, stream=None, schedule=None, autotune=False, outs=None):
         """Decompress device streams (with their host-parsed infos and byte
-        sizes) in one batched launch; returns the decoded tensors and the
-        planned workspace."""
+        sizes) in one batched launch into `outs` (or new tensors); returns
+        the decoded tensors and the planned workspace."""
         torch = self.torch
+        given = outs
         outs, shapes, srcs, dsts = [], [], [], []
-        for s, info, n in zip(streams, infos, sizes):
+        for k, (s, info, n) in enumerate(zip(streams, infos, sizes)):
             dt = torch.uint8 if info.w == 8 else torch.int16
-            y = torch.empty((info.rows, info.D), dtype=dt, device=s.device)
+            y = given[k] if given is not None else torch.empty((info.rows, info.D), dtype=dt, device=s.device)
             outs.append(y)
             shapes.append((info.rows, info.D, info.w, info.opts))
             srcs.append(s.data_ptr())
             dsts.append((y.data_ptr() if y.numel() else 0, y.numel() * y.element_size()))
         arr = self._items(shapes, srcs, list(sizes), dsts, [0] * len(streams))
-        ws = self.batch_plan_run(arr, 0, stream)
+        ws = self.batch_plan_run(arr, 0, stream, schedule=schedule, autotune=autotune)
         return outs, ws
 

@@ -133,6 +133,15 @@ def uniform(rows: int, cols: int, w: int, seed: int) -> np.ndarray:
     return rng.integers(0, hi, size=(rows, cols), dtype=np.uint32).astype(dt)
 
 
+def batch_stream_shape(idx: int, max_rows: int = 1_000_000, min_rows: int = 1_000) -> tuple[int, int, int]:
+    """(rows, D, w) of stream `idx` of the batched workload, from the same
+    first draws as batch_stream, without generating it."""
+    rng = _rng(2 + idx)
+    rows = int(math.exp(rng.uniform(math.log(min_rows), math.log(max_rows))))
+    cols = int(rng.integers(1, 17))
+    return rows, cols, 8 if idx % 2 == 0 else 16
+
+
 def batch_stream(idx: int, max_rows: int = 1_000_000, min_rows: int = 1_000) -> np.ndarray:
     """Stream `idx` of the batched workload: rows log-U(min_rows, max_rows),
     D ~ U{1..16}, uint8 for even idx (random walk with scale U(0.5, 4) and
@@ -184,11 +193,33 @@ def random_walk_u8_torch(rows: int, cols: int, scale: float, const_frac: float, 
     g = _tgen(seed, device)
     p = 1.0 - math.exp(-1.0 / scale)
     s = (torch.empty((rows, cols), device=device).geometric_(p, generator=g)
-         - torch.empty((rows, cols), device=device).geometric_(p, generator=g)).to(torch.int64)
+         - torch.empty((rows, cols), device=device).geometric_(p, generator=g)).to(torch.int32)
     n_blocks = (rows + BLOCK_ROWS - 1) // BLOCK_ROWS
     flat = torch.rand(n_blocks, generator=g, device=device) < const_frac
-    s[flat.repeat_interleave(BLOCK_ROWS)[:rows]] = 0
-    return (torch.cumsum(s, 0) % 256).to(torch.uint8)
+    # no step in the chosen blocks (a masked fill: no host synchronisation)
+    s.masked_fill_(flat.repeat_interleave(BLOCK_ROWS)[:rows, None], 0)
+    return torch.remainder(torch.cumsum(s, 0, dtype=torch.int64), 256).to(torch.uint8)
+
+
+def _stretch_map(rng: np.random.Generator, rows: int, frac: float, lo: int = 16, hi: int = 8192) -> np.ndarray:
+    """Row index map of the flat stretches of `_flat_stretches` (same draws):
+    row r takes the value of row map[r]."""
+    m = np.arange(rows, dtype=np.int64)
+    target = int(frac * rows)
+    if rows < 2 * lo or target == 0:
+        return m
+    covered = np.zeros(rows, dtype=bool)
+    done = attempts = 0
+    while done < target and attempts < 100_000:
+        attempts += 1
+        length = min(int(math.exp(rng.uniform(math.log(lo), math.log(hi)))), rows - 1)
+        start = int(rng.integers(0, rows - length + 1))
+        if covered[start:start + length].any():
+            continue
+        covered[start:start + length] = True
+        m[start:start + length] = start
+        done += length
+    return m
 
 
 def sensor_u16_torch(rows: int, cols: int, seed: int, flat_frac: float = 0.05, device="cuda"):
@@ -196,27 +227,20 @@ def sensor_u16_torch(rows: int, cols: int, seed: int, flat_frac: float = 0.05, d
     import torch
     rng = _rng(seed)
     g = _tgen(seed, device)
-    t = torch.arange(rows, dtype=torch.float64, device=device)
-    x = torch.empty((rows, cols), dtype=torch.int32, device=device)
-    for j in range(cols):
-        v = torch.randn(rows, generator=g, dtype=torch.float64, device=device) * 20.0
-        for _ in range(2):
-            period, amp, phase = rng.uniform(50.0, 5000.0), rng.uniform(0.0, 8000.0), rng.uniform(0.0, 2 * math.pi)
-            v += amp * torch.sin(2.0 * math.pi * t / period + phase)
-        x[:, j] = torch.clamp(torch.round(v) + 32768.0, 0, 65535).to(torch.int32)
-    # flat stretches over flat_frac of the rows, every column held
-    target = int(flat_frac * rows)
-    done, attempts = 0, 0
-    covered = np.zeros(rows, dtype=bool)
-    while done < target and attempts < 100_000 and rows >= 32:
-        attempts += 1
-        length = min(int(math.exp(rng.uniform(math.log(16), math.log(8192)))), rows - 1)
-        start = int(rng.integers(0, rows - length + 1))
-        if covered[start:start + length].any():
-            continue
-        covered[start:start + length] = True
-        x[start:start + length] = x[start]
-        done += length
+    # per column: two (period, amplitude, phase) draws, in the numpy recipe's order
+    par = np.array([[rng.uniform(50.0, 5000.0), rng.uniform(0.0, 8000.0), rng.uniform(0.0, 2 * math.pi)]
+                    for _ in range(2 * cols)]).reshape(cols, 2, 3)
+    t = torch.arange(rows, dtype=torch.float64, device=device)[:, None]
+    v = torch.randn((rows, cols), generator=g, dtype=torch.float64, device=device) * 20.0
+    for k in range(2):
+        per = torch.from_numpy(par[:, k, 0]).to(device)
+        amp = torch.from_numpy(par[:, k, 1]).to(device)
+        ph = torch.from_numpy(par[:, k, 2]).to(device)
+        v += amp * torch.sin(2.0 * math.pi * t / per + ph)
+    x = torch.clamp(torch.round(v) + 32768.0, 0, 65535).to(torch.int32)
+    if rows >= 32:
+        m = torch.from_numpy(_stretch_map(rng, rows, flat_frac)).to(device)
+        x = x.index_select(0, m)
     return (x - 65536 * (x >= 32768)).to(torch.int16)
 
 

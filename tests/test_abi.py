@@ -111,3 +111,29 @@ def test_quant_workspace_size(spz):
     assert L.sprintz_quant_workspace_size(0) == 0
     assert L.sprintz_quant_workspace_size(1025) == 0
     assert L.sprintz_quant_workspace_size(8) == 256
+
+
+def test_rows_and_append_host_checks(spz, oracle_mod):
+    """Workspace sizes and argument checks of the range decode and append
+    calls (host logic only)."""
+    from paper_1808_02515_gb300 import synth
+    L = spz.lib()
+    x = synth.sensor_u16(10 * 1024 + 5, 4, seed=9)
+    s = oracle_mod.compress(x, forecaster=1, chunk_rows=1024)
+    info = spz.query(s[:64].tobytes())
+    ci = info.c()
+    rb = 4 * 2
+    # rows [1500, 3000) are covered by chunks 1 and 2: 2048 rows decoded
+    assert L.sprintz_decompress_rows_workspace_size(ctypes.byref(ci), 1500, 3000) == 2048 * rb
+    # rows in the raw tail need no chunk decoded
+    assert L.sprintz_decompress_rows_workspace_size(ctypes.byref(ci), 10 * 1024 + 1, 10 * 1024 + 5) == 0
+    assert L.sprintz_decompress_rows_workspace_size(ctypes.byref(ci), 0, 10 * 1024 + 6) == 0  # past the end
+    assert L.sprintz_append_workspace_size(ctypes.byref(ci), 8192) > 0
+    h = oracle_mod.compress(x, forecaster=1, huffman=1, huff_chunks=2)
+    hi = spz.query(h[:64].tobytes()).c()
+    assert L.sprintz_append_workspace_size(ctypes.byref(hi), 8192) == 0
+    assert L.sprintz_decompress_rows_workspace_size(ctypes.byref(hi), 0, 10) >= x.nbytes
+    # null context / stream / info
+    assert L.sprintz_decompress_rows(None, None, 0, None, 0, 1, None, 0, None, 0, None) == spz.ERR_INVALID_ARG
+    assert L.sprintz_append(None, None, 0, None, None, 0, None, 0, None, None, 0, None) == spz.ERR_INVALID_ARG
+    assert L.sprintz_ctx_set_failure_test(None, 0, 0) == spz.ERR_INVALID_ARG

@@ -2,7 +2,8 @@
 
 Forecaster 2 is double-delta coding, the a = 2, b = -1 member of the
 autoregressive family of Sec. 4.2.2 (predict x_{i-1} + delta_{i-1}).
-Forecaster 3 is FIRE exactly as Algorithm 3 prints it: alpha derived from the
+Forecaster 3 is FIRE in its per-sample form (Algorithm 3 without the practical
+changes of Sec. 4.2.2): alpha derived from the
 accumulator and one gradient step at every sample, instead of the block form
 (alpha per block, one averaged update from every other sample) that Sec. 4.2.2
 says is used in practice and that forecaster 1 implements.
@@ -57,7 +58,7 @@ def test_double_delta_ramp(oracle_mod, w, slope):
 
 
 # --------------------------------------------------------------------------
-# FIRE per sample (Algorithm 3 as printed)
+# FIRE per sample (Algorithm 3's per-sample form)
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("w", [8, 16])

@@ -45,10 +45,13 @@ def _dev(x):
     return torch.from_numpy(x.view(np.int16) if x.dtype == np.uint16 else x).cuda()
 
 
-def test_noalloc_matches_compress_on_two_calls(spz):
+def test_noalloc_matches_compress_on_two_calls(spz, oracle_mod):
     codec = spz.Codec(0)
     try:
         for x, o in _workloads():
+            full = dict(forecaster=1, huffman=0, group_blocks=2, learn_shift=1, chunk_rows=1024, huff_chunks=64)
+            full.update(o)
+            oracle_bytes = oracle_mod.compress(x, **full)
             opts = spz.Opts(**o)
             xt = _dev(x)
             ref, ref_size = codec.compress(xt, opts)
@@ -63,6 +66,35 @@ def test_noalloc_matches_compress_on_two_calls(spz):
                 torch.cuda.synchronize()
                 assert int(size.item()) == n, call
                 assert torch.equal(dst[:n], ref[:n]), call
+                assert n == oracle_bytes.size and np.array_equal(dst[:n].cpu().numpy(), oracle_bytes), call
+    finally:
+        codec.close()
+
+
+def test_noalloc_at_its_chunk_limit(spz, oracle_mod):
+    """Exactly 65,536 chunks (8-row chunks) is the largest call the fixed
+    array holds: accepted, and equal to sprintz_compress and the oracle."""
+    from paper_1808_02515_gb300 import synth
+    x = synth.random_walk_u8(8 * 65536 + 3, 2, scale=1.5, const_frac=0.3, seed=26)
+    opts = spz.Opts(forecaster=1, chunk_rows=8)
+    codec = spz.Codec(0)
+    try:
+        xt = _dev(x)
+        ref, ref_size = codec.compress(xt, opts)
+        torch.cuda.synchronize()
+        assert codec.status() == spz.OK
+        n = int(ref_size.item())
+        cap = spz.max_compressed_size(x.shape[0], x.shape[1], 8, opts)
+        for call in range(2):
+            dst = torch.full((cap,), 0x5A, dtype=torch.uint8, device="cuda")
+            size = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+            spz.compress_noalloc(xt, opts, dst, size)
+            torch.cuda.synchronize()
+            assert int(size.item()) == n, call
+            assert torch.equal(dst[:n], ref[:n]), call
+        o = oracle_mod.compress(x, forecaster=1, huffman=0, group_blocks=2, learn_shift=1, chunk_rows=8,
+                                huff_chunks=64)
+        assert np.array_equal(ref[:n].cpu().numpy(), o)
     finally:
         codec.close()
 
