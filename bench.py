@@ -324,9 +324,14 @@ def _aligned_offsets(sizes, align=256):
 class BatchWorkload:
     """This rank's streams on the device, laid out in `n_slices` contiguous
     slices (each slice one buffer: inputs, outputs and stream buffers alike),
-    so that a slice moves to or from the host in one copy."""
+    so that a slice moves to or from the host in one copy.  The streams are
+    drawn with the numpy recipe (synth.batch_stream) on all host cores, one
+    stream per thread, straight into one host buffer per slice with the
+    device layout (`host`, kept: the end-to-end figure's host input)."""
 
     def __init__(self, ids, shapes, nbytes, n_slices, dev, spz, synth, torch):
+        from concurrent.futures import ThreadPoolExecutor
+
         from paper_1808_02515_gb300 import shard
         self.ids = ids
         self.dev = dev
@@ -335,34 +340,53 @@ class BatchWorkload:
                        if s[1] > s[0]]
         o = spz.Opts(**opts_dict())
         self.xs, self.outs, self.bufs = [None] * n, [None] * n, [None] * n
-        self.in_bufs, self.out_bufs, self.st_bufs = [], [], []
-        self.view = []  # per slice: (byte offsets in the sample buffers, in the stream buffer)
+        self.in_bufs, self.out_bufs, self.st_bufs, self.host = [], [], [], []
         t0 = time.perf_counter()
+        plan = []
         for a, b in self.slices:
             sz = [nbytes[ids[k]] for k in range(a, b)]
             offs, tot = _aligned_offsets(sz)
             caps = [spz.max_compressed_size(*shapes[ids[k]], o) for k in range(a, b)]
             coffs, ctot = _aligned_offsets(caps)
-            xin = torch.zeros(tot, dtype=torch.uint8, device=dev)
+            self.host.append(np.zeros(tot, dtype=np.uint8))
+            plan.append((a, b, sz, offs, tot, caps, coffs, ctot))
+
+        def draw(job):
+            s_i, k, lo, nb = job
+            x = synth.batch_stream(ids[k])
+            self.host[s_i][lo:lo + nb] = x.reshape(-1).view(np.uint8)
+
+        jobs = [(s_i, k, offs[k - a], sz[k - a]) for s_i, (a, b, sz, offs, *_) in enumerate(plan)
+                for k in range(a, b)]
+        with ThreadPoolExecutor(max(1, len(os.sched_getaffinity(0)))) as ex:
+            list(ex.map(draw, jobs))
+        for s_i, (a, b, sz, offs, tot, caps, coffs, ctot) in enumerate(plan):
+            xin = torch.from_numpy(self.host[s_i]).to(dev)
             xout = torch.zeros(tot, dtype=torch.uint8, device=dev)
             st = torch.empty(ctot, dtype=torch.uint8, device=dev)
             for k in range(a, b):
                 rows, D, w = shapes[ids[k]]
                 dt = torch.uint8 if w == 8 else torch.int16
                 lo, nb = offs[k - a], sz[k - a]
-                v = xin[lo:lo + nb].view(dt).view(rows, D)
-                v.copy_(synth.batch_stream_torch(ids[k], device=dev))
-                self.xs[k] = v
+                self.xs[k] = xin[lo:lo + nb].view(dt).view(rows, D)
                 self.outs[k] = xout[lo:lo + nb].view(dt).view(rows, D)
                 self.bufs[k] = st[coffs[k - a]:coffs[k - a] + caps[k - a]]
             self.in_bufs.append(xin)
             self.out_bufs.append(xout)
             self.st_bufs.append(st)
-            self.view.append((offs, coffs))
         torch.cuda.synchronize()
         self.gen_s = time.perf_counter() - t0
         self.U = sum(nbytes[i] for i in ids)
         self.chunks = sum(-(-(shapes[i][0] - shapes[i][0] % 8) // 1024) if shapes[i][0] >= 8 else 0 for i in ids)
+
+    def host_stream(self, k):
+        """Host copy of stream k (a view of the slice's host buffer)."""
+        for s_i, (a, b) in enumerate(self.slices):
+            if a <= k < b:
+                lo = self.xs[k].data_ptr() - self.in_bufs[s_i].data_ptr()
+                x = self.host[s_i][lo:lo + self.xs[k].numel() * self.xs[k].element_size()]
+                return x.view(np.uint8 if self.xs[k].element_size() == 1 else np.uint16).reshape(self.xs[k].shape)
+        raise IndexError(k)
 
     def outputs_equal_inputs(self, torch):
         return all(torch.equal(a, b) for a, b in zip(self.in_bufs, self.out_bufs))
@@ -511,18 +535,16 @@ def run_batch(args, rank, world, local):
         lib.cudaHostUnregister.restype = ctypes.c_int
         lib.cudaHostUnregister.argtypes = [ctypes.c_void_p]
         in_sizes = [t.numel() for t in wl.in_bufs]
-        h_off, h_tot = _aligned_offsets(in_sizes, 4096)
         c_off, c_tot = _aligned_offsets(F["sz"], 256)
-        hin = np.empty(h_tot, dtype=np.uint8)
         hc = np.empty(c_tot, dtype=np.uint8)
-        for arr in (hin, hc):
+        hin_ptr = [h.ctypes.data for h in wl.host]
+        hc_ptr = hc.ctypes.data
+        registered = []
+        for arr in (*wl.host, hc):
             if lib.cudaHostRegister(arr.ctypes.data, arr.nbytes, 0) != 0:
                 raise SystemExit("cudaHostRegister failed")
+            registered.append(arr)
         try:
-            for s_i, t in enumerate(wl.in_bufs):
-                cr.copy(hin.ctypes.data + h_off[s_i], t.data_ptr(), t.numel(), Cudart.D2H,
-                        stream.cuda_stream)
-            torch.cuda.synchronize()
             nl = max(1, args.e2e_lanes)
             lanes = [torch.cuda.Stream(dev) for _ in range(nl)]
             sc = spz.Schedule(**{k: v for k, v in F["sched"]["compress"].items() if k != "tune_ms"})
@@ -538,18 +560,22 @@ def run_batch(args, rank, world, local):
                                              schedule=sd, outs=wl.outs[lo:hi])
                 sl.append((ls, cc, cd, wsc, wsd, lo, hi))
             torch.cuda.synchronize()
+            in_ptr = [t.data_ptr() for t in wl.in_bufs]
+            out_ptr = [t.data_ptr() for t in wl.out_bufs]
+            buf_ptr = [b.data_ptr() for b in wl.bufs]
+            sz = F["sz"]
 
             def e2e_step():
                 for s_i, (ls, cc, cd, wsc, wsd, lo, hi) in enumerate(sl):
                     sp = ls.cuda_stream
-                    cr.copy(wl.in_bufs[s_i].data_ptr(), hin.ctypes.data + h_off[s_i], in_sizes[s_i], Cudart.H2D, sp)
+                    cr.copy(in_ptr[s_i], hin_ptr[s_i], in_sizes[s_i], Cudart.H2D, sp)
                     cc.batch_run(wsc, stream=ls)
                     for k in range(lo, hi):
-                        cr.copy(hc.ctypes.data + c_off[k], wl.bufs[k].data_ptr(), F["sz"][k], Cudart.D2H, sp)
+                        cr.copy(hc_ptr + c_off[k], buf_ptr[k], sz[k], Cudart.D2H, sp)
                     for k in range(lo, hi):
-                        cr.copy(wl.bufs[k].data_ptr(), hc.ctypes.data + c_off[k], F["sz"][k], Cudart.H2D, sp)
+                        cr.copy(buf_ptr[k], hc_ptr + c_off[k], sz[k], Cudart.H2D, sp)
                     cd.batch_run(wsd, stream=ls)
-                    cr.copy(hin.ctypes.data + h_off[s_i], wl.out_bufs[s_i].data_ptr(), in_sizes[s_i], Cudart.D2H, sp)
+                    cr.copy(hin_ptr[s_i], out_ptr[s_i], in_sizes[s_i], Cudart.D2H, sp)
 
             e2e_step()
             torch.cuda.synchronize()
@@ -569,8 +595,7 @@ def run_batch(args, rank, world, local):
             for _, cc, cd, *_ in sl:
                 cc.check()
                 cd.check()
-            ok = all(torch.equal(torch.from_numpy(hin[h_off[s_i]:h_off[s_i] + in_sizes[s_i]]).to(dev), t)
-                     for s_i, t in enumerate(wl.in_bufs))
+            ok = all(torch.equal(torch.from_numpy(h).to(dev), t) for h, t in zip(wl.host, wl.in_bufs))
             if not ok:
                 raise SystemExit("end-to-end round trip mismatch")
             e2e_ms = slowest_rank_ms(a2.elapsed_time(b2) / n_e2e, dist, dev)
@@ -578,13 +603,14 @@ def run_batch(args, rank, world, local):
                    "h2d_bytes_per_step": sum(in_sizes) + F["C"], "d2h_bytes_per_step": F["C"] + sum(in_sizes),
                    "ms_per_step": e2e_ms, "steps": n_e2e,
                    "pipelining": f"{len(sl)} slices on {nl} CUDA streams; pinned host buffers; "
-                                 "one copy per slice for samples, one per stream for compressed bytes"}
+                                 "one copy per slice for samples, one per stream for compressed bytes; "
+                                 "the decoded samples return into the host buffer the inputs came from"}
             for _, cc, cd, *_ in sl:
                 cc.close()
                 cd.close()
         finally:
-            lib.cudaHostUnregister(hin.ctypes.data)
-            lib.cudaHostUnregister(hc.ctypes.data)
+            for arr in registered:
+                lib.cudaHostUnregister(arr.ctypes.data)
 
     # the delta forecaster (its own autotuned plans; overwrites the stream buffers)
     delta = None
@@ -625,7 +651,8 @@ def run_batch(args, rank, world, local):
         "config": {"workload": WORKLOAD, "streams": args.streams, **opts_dict(),
                    "step": "batched compress + batched decompress of every stream (FIRE)",
                    "uncompressed_bytes": U_total, "compressed_bytes": C_total, "ratio": U_total / C_total,
-                   "chunks": chunks_total, "generator": "batch_stream recipe drawn on the GPU (torch)",
+                   "chunks": chunks_total,
+                   "generator": "synth.batch_stream (numpy PCG64, seed 2 + stream id) on all host cores",
                    "generator_s": wl.gen_s,
                    "l2": "inputs (18 GB) and streams far larger than the 129 MB L2",
                    "parallelism": f"{world} rank(s), each a contiguous byte-balanced range of the streams",
@@ -658,11 +685,7 @@ def run_batch(args, rank, world, local):
         line["e2e"] = e2e
     if not args.no_cpu_baseline and world == 1:
         sample = oracle_sample(list(range(len(ids))), 50)
-        xs_host = []
-        for k in sample:
-            h = wl.xs[k].cpu().numpy()
-            xs_host.append(h.view(np.uint16) if h.dtype == np.int16 else h)
-        line["cpu_baseline"] = cpu_baseline(xs_host)
+        line["cpu_baseline"] = cpu_baseline([wl.host_stream(k).copy() for k in sample])
     print(json.dumps(line), flush=True)
     F["cc"].close()
     F["cd"].close()

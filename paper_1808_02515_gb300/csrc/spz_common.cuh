@@ -174,6 +174,40 @@ __device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
   return v;
 }
 
+// L2 eviction policies (createpolicy) and global accesses that carry one:
+// data read once and streamed through is marked evict_first, data written
+// now and read back soon (the encoder's body slots) evict_last.
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// Read-only (non-coherent) 8-byte load with an L2 policy.
+__device__ __forceinline__ unsigned long long ldg_u64_hint(const unsigned long long *p, uint64_t pol) {
+  unsigned long long v;
+  asm("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+  return v;
+}
+// 16-byte load / store with an L2 policy (data this kernel writes).
+__device__ __forceinline__ uint4 ld_v4_hint(const void *p, uint64_t pol) {
+  uint4 v;
+  asm volatile("ld.global.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_v4_hint(void *p, uint4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w), "l"(pol)
+               : "memory");
+}
+
 // Bulk prefetch of [p, p + bytes) into L2 (TMA unit; p and bytes multiples of 16).
 __device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");

@@ -741,8 +741,24 @@ __device__ __forceinline__ void decode_group(const DecParams &p, const LaneRing 
       // zigzagged errors of this lane's column, 8 rows (all zero in a run:
       // mask 0)
       uint32_t z[kBlockRows];
+      if (W == 8 && DT != 0 && DT * W <= 32) {
+        // column-major u8: the 8 values (stride = n <= 8 bits each) are
+        // contiguous, 64 bits at most: three words, two funnel shifts, and
+        // values 4..7 from the window 4n bits on
+        const uint32_t q = gq + pbit;
+        const uint32_t i0 = q >> 5;
+        const uint32_t a0 = ring32[i0], a1 = ring32[i0 + 1], a2 = ring32[i0 + 2];
+        const uint32_t lo = __funnelshift_r(a0, a1, q), hi = __funnelshift_r(a1, a2, q);
+        const uint32_t mid = __funnelshift_rc(lo, hi, 4 * stride);
 #pragma unroll
-      for (int i = 0; i < kBlockRows; ++i) z[i] = rbits(pbit + i * stride, mask);
+        for (int i = 0; i < 4; ++i) {
+          z[i] = (lo >> (i * stride)) & mask;
+          z[i + 4] = (mid >> (i * stride)) & mask;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < kBlockRows; ++i) z[i] = rbits(pbit + i * stride, mask);
+      }
       if (g.forecaster == kFcDelta) {
 #pragma unroll
         for (int i = 0; i < kBlockRows; ++i) {
@@ -1143,7 +1159,7 @@ static LaneRing lane_ring_plan(const Geom &g, const LaunchCfg &cfg, uint32_t nse
   const uint32_t gmax = g.hdr_bytes + g.G * g.D * g.w;
   r.seg = 128;
   r.seg_shift = 7;
-  r.mirror = (gmax + 8 + 15) & ~15u;  // a group plus the word read past its end
+  r.mirror = (gmax + 16 + 15) & ~15u;  // a group plus the words read past its end (at most 12 bytes)
   while (r.seg < r.mirror) {
     r.seg <<= 1;
     r.seg_shift++;

@@ -996,6 +996,10 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
   constexpr bool kHdrShfl = DT >= 2 && (DT & (DT - 1)) == 0 && DT * HB <= 32;
   const bool colmaj = DT ? (DT * W <= 32) : (g.col_major != 0);
   uint8_t *slot = wslots + (uint64_t)kc * cfg.slot_stride;
+  // L2 policies: the rows stream through (evict first); the body slot is
+  // written now and read back at the chunk's end (evict last); the stream
+  // itself is written once (evict first)
+  const uint64_t pol_stream = l2_policy_evict_first(), pol_slot = l2_policy_evict_last();
 
   // cooperative stage loads: this lane's (up to two) 8-byte words of a block step
   const uint32_t words_per = D * wb, total_words = K * words_per;
@@ -1078,7 +1082,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
       const uint32_t u1 = fin ? (limit + 15) >> 4 : (limit >> 5) << 1;
       for (uint32_t u = (flushed >> 4) + j; u < u1; u += D) {
         uint4 *r4 = reinterpret_cast<uint4 *>(&ring[(u * 4) & ring_wmask]);
-        *reinterpret_cast<uint4 *>(slot + 16ull * u) = *r4;
+        st_v4_hint(slot + 16ull * u, *r4, pol_slot);
         *r4 = make_uint4(0, 0, 0, 0);
       }
       if (u1 * 16 > flushed) flushed = u1 * 16;
@@ -1086,7 +1090,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
 
     unsigned long long wcur[2], wnext[2];
 #pragma unroll
-    for (int t = 0; t < 2; ++t) wcur[t] = (has[t] && nbw[t] > 0) ? __ldg(srcw[t]) : 0ull;
+    for (int t = 0; t < 2; ++t) wcur[t] = (has[t] && nbw[t] > 0) ? ldg_u64_hint(srcw[t], pol_stream) : 0ull;
     __syncwarp();
     for (uint32_t b = 0; b < nb_max; ++b) {
 #pragma unroll
@@ -1094,7 +1098,8 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
         if (has[t]) reinterpret_cast<unsigned long long *>(stage)[st_word[t]] = wcur[t];
 #pragma unroll
       for (int t = 0; t < 2; ++t)
-        wnext[t] = (has[t] && b + 1 < nbw[t]) ? __ldg(srcw[t] + (uint64_t)(b + 1) * words_per) : 0ull;
+        wnext[t] = (has[t] && b + 1 < nbw[t]) ? ldg_u64_hint(srcw[t] + (uint64_t)(b + 1) * words_per, pol_stream)
+                                              : 0ull;
       __syncwarp();
       const bool here = live && b < nb;
       uint32_t z[kBlockRows];
@@ -1291,8 +1296,8 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
         for (int t = 0; t < 2; ++t) {
           const uint32_t u = u0 + t * D;
           if (u < n16) {
-            A[t] = s4[u];
-            B[t] = s4[u + 1];
+            A[t] = ld_v4_hint(s4 + u, pol_stream);
+            B[t] = ld_v4_hint(s4 + u + 1, pol_stream);
           }
         }
 #pragma unroll
@@ -1310,7 +1315,7 @@ __device__ __forceinline__ void encode_group_slots(const EncParams &p, const Enc
             o.y = __funnelshift_r(a1, a2, sh);
             o.z = __funnelshift_r(a2, a3, sh);
             o.w = __funnelshift_r(a3, a4, sh);
-            *reinterpret_cast<uint4 *>(d + head + 16 * u) = o;
+            st_v4_hint(d + head + 16 * u, o, pol_stream);
           }
         }
       }
