@@ -243,6 +243,29 @@ class Cudart:
             raise RuntimeError(f"cudaMemcpyAsync failed ({rc})")
 
 
+class PinnedBuffer:
+    """Page-locked host memory of exactly `n` bytes (cudaHostAlloc), seen as
+    a numpy uint8 array.  Pinned from the start: host buffers that the GPU
+    first read as pageable memory copy far slower once registered later."""
+
+    def __init__(self, n: int, cudart: "Cudart"):
+        lib = cudart.lib
+        lib.cudaHostAlloc.restype = ctypes.c_int
+        lib.cudaHostAlloc.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t, ctypes.c_uint]
+        lib.cudaFreeHost.restype = ctypes.c_int
+        lib.cudaFreeHost.argtypes = [ctypes.c_void_p]
+        self.lib, self.n, self.ptr = lib, max(int(n), 1), ctypes.c_void_p()
+        if lib.cudaHostAlloc(ctypes.byref(self.ptr), self.n, 0) != 0:
+            raise RuntimeError(f"cudaHostAlloc of {self.n} bytes failed")
+        self.array = np.ctypeslib.as_array((ctypes.c_uint8 * self.n).from_address(self.ptr.value))
+
+    def free(self) -> None:
+        if self.ptr.value:
+            self.array = None
+            self.lib.cudaFreeHost(self.ptr)
+            self.ptr = ctypes.c_void_p()
+
+
 def oracle_sample(ids, every):
     """Every `every`-th of the given stream ids (at least one)."""
     s = ids[::max(1, every)]
@@ -326,8 +349,8 @@ class BatchWorkload:
     slices (each slice one buffer: inputs, outputs and stream buffers alike),
     so that a slice moves to or from the host in one copy.  The streams are
     drawn with the numpy recipe (synth.batch_stream) on all host cores, one
-    stream per thread, straight into one host buffer per slice with the
-    device layout (`host`, kept: the end-to-end figure's host input)."""
+    stream per thread, straight into one pinned host buffer per slice with
+    the device layout (`host`, kept: the end-to-end figure's host input)."""
 
     def __init__(self, ids, shapes, nbytes, n_slices, dev, spz, synth, torch):
         from concurrent.futures import ThreadPoolExecutor
@@ -340,7 +363,8 @@ class BatchWorkload:
                        if s[1] > s[0]]
         o = spz.Opts(**opts_dict())
         self.xs, self.outs, self.bufs = [None] * n, [None] * n, [None] * n
-        self.in_bufs, self.out_bufs, self.st_bufs, self.host = [], [], [], []
+        self.in_bufs, self.out_bufs, self.st_bufs, self.host, self.pinned = [], [], [], [], []
+        self.cudart = Cudart()
         t0 = time.perf_counter()
         plan = []
         for a, b in self.slices:
@@ -348,7 +372,10 @@ class BatchWorkload:
             offs, tot = _aligned_offsets(sz)
             caps = [spz.max_compressed_size(*shapes[ids[k]], o) for k in range(a, b)]
             coffs, ctot = _aligned_offsets(caps)
-            self.host.append(np.zeros(tot, dtype=np.uint8))
+            buf = PinnedBuffer(tot, self.cudart)
+            buf.array[:] = 0
+            self.pinned.append(buf)
+            self.host.append(buf.array[:tot])
             plan.append((a, b, sz, offs, tot, caps, coffs, ctot))
 
         def draw(job):
@@ -361,7 +388,9 @@ class BatchWorkload:
         with ThreadPoolExecutor(max(1, len(os.sched_getaffinity(0)))) as ex:
             list(ex.map(draw, jobs))
         for s_i, (a, b, sz, offs, tot, caps, coffs, ctot) in enumerate(plan):
-            xin = torch.from_numpy(self.host[s_i]).to(dev)
+            xin = torch.empty(tot, dtype=torch.uint8, device=dev)
+            self.cudart.copy(xin.data_ptr(), self.host[s_i].ctypes.data, tot, Cudart.H2D,
+                             torch.cuda.current_stream(dev).cuda_stream)
             xout = torch.zeros(tot, dtype=torch.uint8, device=dev)
             st = torch.empty(ctot, dtype=torch.uint8, device=dev)
             for k in range(a, b):
@@ -378,6 +407,11 @@ class BatchWorkload:
         self.gen_s = time.perf_counter() - t0
         self.U = sum(nbytes[i] for i in ids)
         self.chunks = sum(-(-(shapes[i][0] - shapes[i][0] % 8) // 1024) if shapes[i][0] >= 8 else 0 for i in ids)
+
+    def free(self):
+        for b in self.pinned:
+            b.free()
+        self.pinned, self.host = [], []
 
     def host_stream(self, k):
         """Host copy of stream k (a view of the slice's host buffer)."""
@@ -528,22 +562,12 @@ def run_batch(args, rank, world, local):
     # copies overlap another's kernels and the two directions overlap.
     e2e = None
     if not args.no_e2e:
-        cr = Cudart()
-        lib = cr.lib
-        lib.cudaHostRegister.restype = ctypes.c_int
-        lib.cudaHostRegister.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint]
-        lib.cudaHostUnregister.restype = ctypes.c_int
-        lib.cudaHostUnregister.argtypes = [ctypes.c_void_p]
+        cr = wl.cudart
         in_sizes = [t.numel() for t in wl.in_bufs]
         c_off, c_tot = _aligned_offsets(F["sz"], 256)
-        hc = np.empty(c_tot, dtype=np.uint8)
+        hc = PinnedBuffer(c_tot, cr)
         hin_ptr = [h.ctypes.data for h in wl.host]
-        hc_ptr = hc.ctypes.data
-        registered = []
-        for arr in (*wl.host, hc):
-            if lib.cudaHostRegister(arr.ctypes.data, arr.nbytes, 0) != 0:
-                raise SystemExit("cudaHostRegister failed")
-            registered.append(arr)
+        hc_ptr = hc.ptr.value
         try:
             nl = max(1, args.e2e_lanes)
             lanes = [torch.cuda.Stream(dev) for _ in range(nl)]
@@ -602,15 +626,14 @@ def run_batch(args, rank, world, local):
             e2e = {"value": total_gbs(U_total, e2e_ms), "unit": "GB/s",
                    "h2d_bytes_per_step": sum(in_sizes) + F["C"], "d2h_bytes_per_step": F["C"] + sum(in_sizes),
                    "ms_per_step": e2e_ms, "steps": n_e2e,
-                   "pipelining": f"{len(sl)} slices on {nl} CUDA streams; pinned host buffers; "
+                   "pipelining": f"{len(sl)} slices on {nl} CUDA streams; pinned host buffers (cudaHostAlloc); "
                                  "one copy per slice for samples, one per stream for compressed bytes; "
                                  "the decoded samples return into the host buffer the inputs came from"}
             for _, cc, cd, *_ in sl:
                 cc.close()
                 cd.close()
         finally:
-            for arr in registered:
-                lib.cudaHostUnregister(arr.ctypes.data)
+            hc.free()
 
     # the delta forecaster (its own autotuned plans; overwrites the stream buffers)
     delta = None
@@ -634,6 +657,7 @@ def run_batch(args, rank, world, local):
     if rank != 0:
         F["cc"].close()
         F["cd"].close()
+        wl.free()
         return
     peak, peak_kind = peaks()
     enc_bytes = U_total + C_total + 16 * chunks_total
@@ -689,6 +713,7 @@ def run_batch(args, rank, world, local):
     print(json.dumps(line), flush=True)
     F["cc"].close()
     F["cd"].close()
+    wl.free()
 
 
 def main():

@@ -353,6 +353,22 @@ struct BatchPlan {
 // A work entry: stream index (< 2^24) and chunk group of that stream.
 constexpr uint32_t kWorkGroupBits = 40;
 constexpr uint32_t kMaxBatchStreams = 1u << 24;
+// The work list's classes (one per (w, D) pair) and each SM's home class:
+// warps take work from their SM's home class first, so that the warps of an
+// SM run one specialisation at a time (the instruction cache holds one), and
+// move on to the other classes once it is exhausted.  The table precedes
+// the work entries in the workspace; the class tickets are the first
+// kClassTicketBytes of the workspace.
+constexpr uint32_t kMaxBatchClasses = 64;
+constexpr uint32_t kMaxHomeSm = 512;
+constexpr uint64_t kClassTicketBytes = 4 * kMaxBatchClasses;
+struct BatchClasses {
+  uint32_t n_classes;
+  uint32_t n_sm;                          // SM ids are taken modulo n_sm
+  uint64_t start[kMaxBatchClasses + 1];   // work entries [start[c], start[c + 1]) are class c's
+  uint8_t home[kMaxHomeSm];
+};
+constexpr uint64_t kClassTableBytes = (sizeof(BatchClasses) + 255) & ~255ull;
 // Resolve the 0 (= default) fields of a schedule for one direction.
 sprintz_schedule batch_default_schedule(int compress);
 // Build the plan and the descriptor image (host bytes to copy to ws +
@@ -365,12 +381,39 @@ int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchC
                       const sprintz_schedule &sched, int *d_status, uint8_t *ws, BatchPlan *plan,
                       std::vector<uint8_t> *items_img, std::vector<uint64_t> *work_img);
 int run_batch_decode(const BatchPlan &plan, cudaStream_t stream);
-// The work list of a batch: per (w, D) class (classes in a fixed order, the
-// heaviest groups first), the chunk groups of the class's streams in the
-// schedule's order; every stream's groups stay in increasing order.
+// The work image of a batch: the class table (kClassTableBytes), then per
+// (w, D) class (classes in a fixed order, the heaviest groups first) the
+// chunk groups of the class's streams in the schedule's order; every
+// stream's groups stay in increasing order.  SMs get home classes in
+// proportion to the classes' chunk groups.
 void batch_work_list(const std::vector<uint32_t> &w, const std::vector<uint32_t> &D,
-                     const std::vector<uint64_t> &groups, const std::vector<uint64_t> &group_bytes,
-                     uint32_t order, std::vector<uint64_t> *work);
+                     const std::vector<uint64_t> &groups, uint32_t order, uint32_t sm_count,
+                     std::vector<uint64_t> *image, uint64_t *n_work);
+// The next work entry of a warp of a batched kernel (the same value in every
+// lane): from the SM's home class while it lasts, then from the others in
+// turn.  False when every class is exhausted.
+__device__ __forceinline__ bool batch_next(const BatchClasses *cls, const uint64_t *work, uint32_t *tickets,
+                                           uint32_t &c, uint64_t *entry) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nc = cls->n_classes;
+  for (uint32_t tried = 0; tried < nc; ++tried) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(&tickets[c], 1u);
+    t = __shfl_sync(0xFFFFFFFFu, t, 0);
+    const uint64_t s0 = cls->start[c], n = cls->start[c + 1] - s0;
+    if (t < n) {
+      *entry = __ldg(work + s0 + t);
+      return true;
+    }
+    c = c + 1 == nc ? 0 : c + 1;
+  }
+  return false;
+}
+__device__ __forceinline__ uint32_t batch_home(const BatchClasses *cls) {
+  uint32_t smid;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+  return cls->n_classes ? cls->home[smid % cls->n_sm] : 0u;
+}
 int launch_decode(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint64_t src_size,
                   uint8_t *dst, uint64_t dst_cap, uint8_t *ws, uint64_t ws_bytes, int *d_status,
                   cudaStream_t stream);

@@ -1070,23 +1070,21 @@ typedef void (*DecBatchGroupFn)(const DecBatchItem &, uint64_t, uint8_t *);
 __device__ DecBatchGroupFn g_dec_batch_fns[2][17] = {SPZ_DEC_ROW(8), SPZ_DEC_ROW(16)};
 #undef SPZ_DEC_ROW
 
-// Batched decode: persistent warps take work entries (stream, chunk group)
-// from one ticket, in the host's (w, D)-class order; each warp copies its
-// item's descriptor into shared memory once per group.
+// Batched decode: persistent warps take work entries (stream, chunk group),
+// one ticket per (w, D) class, from their SM's home class first; each warp
+// copies its item's descriptor into shared memory once per group.
 __global__ void __launch_bounds__(kLaneThreads, 7) k_decode_batch(const DecBatchItem *items,
-                                                                 const uint64_t *work, uint64_t n_work,
-                                                                 unsigned long long *ticket, uint32_t per_warp) {
+                                                                 const BatchClasses *classes,
+                                                                 const uint64_t *work, uint32_t *tickets,
+                                                                 uint32_t per_warp) {
   extern __shared__ __align__(16) uint8_t dsm[];
   __shared__ __align__(16) DecBatchItem s_it[kLaneWarps];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t *wsm = dsm + (uint64_t)warp * per_warp;
   constexpr uint32_t kWords = sizeof(DecBatchItem) / 8;
-  for (;;) {
-    unsigned long long t = 0;
-    if (lane == 0) t = atomicAdd(ticket, 1ull);
-    t = __shfl_sync(0xFFFFFFFFu, t, 0);
-    if (t >= n_work) break;
-    const uint64_t e = __ldg(work + t);
+  uint32_t c = batch_home(classes);
+  uint64_t e = 0;
+  while (batch_next(classes, work, tickets, c, &e)) {
     const uint32_t s = (uint32_t)(e >> kWorkGroupBits);
     const uint64_t grp = e & ((1ull << kWorkGroupBits) - 1);
     const uint64_t *from = reinterpret_cast<const uint64_t *>(items + s);
@@ -1153,12 +1151,20 @@ __global__ void k_decode_batch_tails(const DecBatchItem *items) {
   for (uint64_t k = threadIdx.x; k < tail_bytes; k += blockDim.x) d[k] = src[k];
 }
 
-static LaneRing lane_ring_plan(const Geom &g, const LaunchCfg &cfg, uint32_t nseg_want, bool staged) {
+// min_seg: smallest ring segment (a power of two >= 64); the batched decoder
+// takes 64 so that the rings of its narrowest streams (D = 1: 32 chunks per
+// warp) do not set the shared memory of every warp.
+static LaneRing lane_ring_plan(const Geom &g, const LaunchCfg &cfg, uint32_t nseg_want, bool staged,
+                               uint32_t min_seg = 128) {
   LaneRing r{};
   const uint32_t K = 32 / g.D;
   const uint32_t gmax = g.hdr_bytes + g.G * g.D * g.w;
-  r.seg = 128;
-  r.seg_shift = 7;
+  r.seg = 64;
+  r.seg_shift = 6;
+  while (r.seg < min_seg) {
+    r.seg <<= 1;
+    r.seg_shift++;
+  }
   r.mirror = (gmax + 16 + 15) & ~15u;  // a group plus the words read past its end (at most 12 bytes)
   while (r.seg < r.mirror) {
     r.seg <<= 1;
@@ -1237,7 +1243,7 @@ int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchC
   std::vector<DecBatchItem> v(n);
   std::vector<uint64_t> temp_off(n, 0);
   std::vector<uint32_t> vw(n), vD(n);
-  std::vector<uint64_t> vgroups(n), vgbytes(n);
+  std::vector<uint64_t> vgroups(n);
   uint64_t temp_total = 0;
   bool any_ranged = false;
   uint32_t region = 0;
@@ -1289,8 +1295,8 @@ int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchC
     if (g.n_chunks) {
       // the batch kernel stages the rows of D <= 3 in shared memory, as the
       // single-stream lane decoder does
-      d.rg = lane_ring_plan(g, cfg, sched.ring_segments, dec_staged((int)g.D));
-      if (!d.rg.per_warp) d.rg = lane_ring_plan(g, cfg, 2, dec_staged((int)g.D));
+      d.rg = lane_ring_plan(g, cfg, sched.ring_segments, dec_staged((int)g.D), 64);
+      if (!d.rg.per_warp) d.rg = lane_ring_plan(g, cfg, 2, dec_staged((int)g.D), 64);
       if (!d.rg.per_warp) return SPRINTZ_ERR_UNSUPPORTED;
       region = std::max(region, d.rg.per_warp);
     }
@@ -1298,18 +1304,18 @@ int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchC
     vw[i] = g.w;
     vD[i] = g.D;
     vgroups[i] = (d.p.c_end - d.p.c_begin + K - 1) / K;
-    vgbytes[i] = K * g.chunk_rows * g.D * g.wb;
   }
-  batch_work_list(vw, vD, vgroups, vgbytes, sched.order, work);
+  uint64_t n_work = 0;
+  batch_work_list(vw, vD, vgroups, sched.order, (uint32_t)cfg.sm_count, work, &n_work);
   memset(pl, 0, sizeof(*pl));
   pl->compress = 0;
   pl->n = n;
   pl->region = std::max<uint32_t>(region, 16);
-  pl->n_work = work->size();
-  pl->zero_bytes = 16;  // the ticket
-  pl->items_off = 256;
+  pl->n_work = n_work;
+  pl->zero_bytes = kClassTicketBytes;  // the class tickets
+  pl->items_off = align256d(kClassTicketBytes);
   pl->work_off = align256d(pl->items_off + (uint64_t)n * sizeof(DecBatchItem));
-  pl->slots_off = align256d(pl->work_off + 8ull * std::max<uint64_t>(1, pl->n_work));  // range temporaries
+  pl->slots_off = align256d(pl->work_off + 8ull * work->size());  // range temporaries
   pl->ws_total = pl->slots_off + temp_total;
   pl->slot_region = any_ranged ? 1 : 0;
   for (uint32_t i = 0; i < n; ++i)
@@ -1335,12 +1341,13 @@ int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchC
 int run_batch_decode(const BatchPlan &pl, cudaStream_t stream) {
   uint8_t *ws = (uint8_t *)pl.ws;
   const DecBatchItem *items = reinterpret_cast<const DecBatchItem *>(ws + pl.items_off);
-  const uint64_t *work = reinterpret_cast<const uint64_t *>(ws + pl.work_off);
+  const BatchClasses *classes = reinterpret_cast<const BatchClasses *>(ws + pl.work_off);
+  const uint64_t *work = reinterpret_cast<const uint64_t *>(ws + pl.work_off + kClassTableBytes);
   if (cudaMemsetAsync(ws, 0, pl.zero_bytes, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
   k_decode_batch_tails<<<pl.n, 128, 0, stream>>>(items);
   if (pl.n_work)
     k_decode_batch<<<pl.grid, kLaneThreads, (uint64_t)kLaneWarps * pl.region, stream>>>(
-        items, work, pl.n_work, reinterpret_cast<unsigned long long *>(ws), pl.region);
+        items, classes, work, reinterpret_cast<uint32_t *>(ws), pl.region);
   if (pl.slot_region) k_decode_batch_rows<<<dim3(8, pl.n), 256, 0, stream>>>(items);
   return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
 }

@@ -1409,16 +1409,17 @@ typedef void (*EncBatchGroupFn)(const EncBatchItem &, uint32_t, uint8_t *, uint8
 __device__ EncBatchGroupFn g_enc_batch_fns[2][17] = {SPZ_ENC_ROW(8), SPZ_ENC_ROW(16)};
 #undef SPZ_ENC_ROW
 
-// Batched encode: persistent warps take work entries (stream, chunk group)
-// from one ticket.  The host orders the list by (w, D) class, and every
-// stream's groups in increasing order, so a group's look-back only waits on
-// earlier groups of its own stream, all of which were taken earlier and are
-// running or done.  Each warp copies its item's descriptor into shared
-// memory once per group.
+// Batched encode: persistent warps take work entries (stream, chunk group),
+// one ticket per (w, D) class, from their SM's home class first.  Every
+// stream's groups are in increasing order inside their class's list, so a
+// group's look-back only waits on earlier groups of its own stream, all of
+// which were taken earlier and are running or done.  Each warp copies its
+// item's descriptor into shared memory once per group.
 __global__ void __launch_bounds__(kEncLaneThreads, 7) k_encode_batch(const EncBatchItem *items,
-                                                                    const uint64_t *work, uint64_t n_work,
-                                                                    uint32_t *ticket, uint32_t region,
-                                                                    uint8_t *slots, uint64_t slot_region) {
+                                                                    const BatchClasses *classes,
+                                                                    const uint64_t *work, uint32_t *tickets,
+                                                                    uint32_t region, uint8_t *slots,
+                                                                    uint64_t slot_region) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ __align__(16) EncBatchItem s_it[kEncLaneWarps];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1426,12 +1427,9 @@ __global__ void __launch_bounds__(kEncLaneThreads, 7) k_encode_batch(const EncBa
   const uint64_t gwarp = (uint64_t)blockIdx.x * kEncLaneWarps + warp;
   uint8_t *wslots = slots + gwarp * slot_region;
   constexpr uint32_t kWords = sizeof(EncBatchItem) / 8;
-  for (;;) {
-    unsigned long long t = 0;
-    if (lane == 0) t = atomicAdd(reinterpret_cast<unsigned long long *>(ticket), 1ull);
-    t = __shfl_sync(0xFFFFFFFFu, t, 0);
-    if (t >= n_work) break;
-    const uint64_t e = __ldg(work + t);
+  uint32_t c = batch_home(classes);
+  uint64_t e = 0;
+  while (batch_next(classes, work, tickets, c, &e)) {
     const uint32_t s = (uint32_t)(e >> kWorkGroupBits);
     const uint32_t grp = (uint32_t)(e & ((1ull << kWorkGroupBits) - 1));
     const uint64_t *from = reinterpret_cast<const uint64_t *>(items + s);
@@ -1996,8 +1994,8 @@ static sprintz_schedule resolve_schedule(const sprintz_schedule &in, int compres
 }
 
 void batch_work_list(const std::vector<uint32_t> &w, const std::vector<uint32_t> &D,
-                     const std::vector<uint64_t> &groups, const std::vector<uint64_t> &group_bytes,
-                     uint32_t order, std::vector<uint64_t> *work) {
+                     const std::vector<uint64_t> &groups, uint32_t order, uint32_t sm_count,
+                     std::vector<uint64_t> *image, uint64_t *n_work) {
   const uint32_t n = (uint32_t)w.size();
   // classes (w, D), heaviest groups first, then by w and D
   std::vector<uint32_t> idx(n);
@@ -2012,27 +2010,47 @@ void batch_work_list(const std::vector<uint32_t> &w, const std::vector<uint32_t>
     if (order == 2 && groups[a] != groups[b]) return groups[a] > groups[b];
     return a < b;
   });
-  (void)group_bytes;
-  work->clear();
+  const uint64_t hdr_words = kClassTableBytes / 8;
+  image->assign(hdr_words, 0);
   uint64_t total = 0;
   for (uint32_t i = 0; i < n; ++i) total += groups[i];
-  work->reserve(total);
+  image->reserve(hdr_words + total);
+  BatchClasses tab;
+  memset(&tab, 0, sizeof(tab));
   for (uint32_t a = 0; a < n;) {
     uint32_t b = a;
     while (b < n && cls(idx[b]) == cls(idx[a])) ++b;
-    if (order == 3) {
-      // round robin: group r of every stream of the class that has one
-      uint64_t rmax = 0;
-      for (uint32_t k = a; k < b; ++k) rmax = std::max<uint64_t>(rmax, groups[idx[k]]);
-      for (uint64_t r = 0; r < rmax; ++r)
+    uint64_t cg = 0;
+    for (uint32_t k = a; k < b; ++k) cg += groups[idx[k]];
+    if (cg) {
+      const uint32_t c = tab.n_classes < kMaxBatchClasses ? tab.n_classes++ : kMaxBatchClasses - 1;
+      tab.start[c] = image->size() - hdr_words;
+      if (order == 3) {
+        // round robin: group r of every stream of the class that has one
+        uint64_t rmax = 0;
+        for (uint32_t k = a; k < b; ++k) rmax = std::max<uint64_t>(rmax, groups[idx[k]]);
+        for (uint64_t r = 0; r < rmax; ++r)
+          for (uint32_t k = a; k < b; ++k)
+            if (r < groups[idx[k]]) image->push_back((uint64_t)idx[k] << kWorkGroupBits | r);
+      } else {
         for (uint32_t k = a; k < b; ++k)
-          if (r < groups[idx[k]]) work->push_back((uint64_t)idx[k] << kWorkGroupBits | r);
-    } else {
-      for (uint32_t k = a; k < b; ++k)
-        for (uint64_t r = 0; r < groups[idx[k]]; ++r) work->push_back((uint64_t)idx[k] << kWorkGroupBits | r);
+          for (uint64_t r = 0; r < groups[idx[k]]; ++r) image->push_back((uint64_t)idx[k] << kWorkGroupBits | r);
+      }
+      tab.start[c + 1] = image->size() - hdr_words;
     }
     a = b;
   }
+  *n_work = image->size() - hdr_words;
+  // home classes: SM s takes the class that holds the point (s + 1/2) / n_sm
+  // of the work
+  tab.n_sm = std::max<uint32_t>(1, std::min<uint32_t>(sm_count, kMaxHomeSm));
+  for (uint32_t sm = 0; sm < tab.n_sm && tab.n_classes; ++sm) {
+    const double p = (sm + 0.5) * (double)*n_work / tab.n_sm;
+    uint32_t c = 0;
+    while (c + 1 < tab.n_classes && (double)tab.start[c + 1] <= p) ++c;
+    tab.home[sm] = (uint8_t)c;
+  }
+  memcpy(image->data(), &tab, sizeof(tab));
 }
 
 // CTAs of the batched encoder that fit one SM with `region` shared bytes per warp.
@@ -2055,7 +2073,7 @@ int plan_batch_encode(const sprintz_batch_item *items, uint32_t n, const LaunchC
   const sprintz_schedule sched = resolve_schedule(sched_in, 1);
   std::vector<EncBatchItem> v(n);
   std::vector<uint32_t> vw(n), vD(n);
-  std::vector<uint64_t> vgroups(n), vgbytes(n);
+  std::vector<uint64_t> vgroups(n);
   uint64_t lb_words = 0;
   uint32_t region = kEncStage;
   uint64_t slot_region = 16;
@@ -2077,7 +2095,7 @@ int plan_batch_encode(const sprintz_batch_item *items, uint32_t n, const LaunchC
     e.p.out_size = it.out_size;
     e.p.status = d_status;
     e.p.g = g;
-    e.p.lookback = reinterpret_cast<uint64_t *>(ws + 16 + 8 * lb_words);
+    e.p.lookback = reinterpret_cast<uint64_t *>(ws + kClassTicketBytes + 8 * lb_words);
     e.cfg.window = enc_window_bytes(g);
     e.cfg.n_groups = (uint32_t)((g.n_chunks + K - 1) / K);
     e.cfg.slot_stride = (uint32_t)(((g.max_body + 31) & ~31ull) + 32);
@@ -2086,23 +2104,23 @@ int plan_batch_encode(const sprintz_batch_item *items, uint32_t n, const LaunchC
     vw[i] = g.w;
     vD[i] = g.D;
     vgroups[i] = e.cfg.n_groups;
-    vgbytes[i] = (uint64_t)K * g.chunk_rows * g.D * g.wb;
     if (g.n_chunks) {
       region = std::max<uint32_t>(region, enc_slot_region(g, e.cfg.window));
       slot_region = std::max<uint64_t>(slot_region, (uint64_t)K * e.cfg.slot_stride);
     }
   }
-  batch_work_list(vw, vD, vgroups, vgbytes, sched.order, work);
+  uint64_t n_work = 0;
+  batch_work_list(vw, vD, vgroups, sched.order, (uint32_t)cfg.sm_count, work, &n_work);
   memset(pl, 0, sizeof(*pl));
   pl->compress = 1;
   pl->n = n;
   pl->region = region;
   pl->slot_region = slot_region;
-  pl->n_work = work->size();
-  pl->zero_bytes = 16 + 8 * lb_words;
+  pl->n_work = n_work;
+  pl->zero_bytes = kClassTicketBytes + 8 * lb_words;
   pl->items_off = align256(pl->zero_bytes);
   pl->work_off = align256(pl->items_off + (uint64_t)n * sizeof(EncBatchItem));
-  pl->slots_off = align256(pl->work_off + 8ull * std::max<uint64_t>(1, pl->n_work));
+  pl->slots_off = align256(pl->work_off + 8ull * work->size());
   const uint32_t occ = enc_batch_occupancy(region, cfg);
   if (!occ) return SPRINTZ_ERR_UNSUPPORTED;
   const uint64_t want = (pl->n_work + kEncLaneWarps - 1) / kEncLaneWarps;
@@ -2123,12 +2141,13 @@ int plan_batch_encode(const sprintz_batch_item *items, uint32_t n, const LaunchC
 int run_batch_encode(const BatchPlan &pl, cudaStream_t stream) {
   uint8_t *ws = (uint8_t *)pl.ws;
   const EncBatchItem *items = reinterpret_cast<const EncBatchItem *>(ws + pl.items_off);
-  const uint64_t *work = reinterpret_cast<const uint64_t *>(ws + pl.work_off);
+  const BatchClasses *classes = reinterpret_cast<const BatchClasses *>(ws + pl.work_off);
+  const uint64_t *work = reinterpret_cast<const uint64_t *>(ws + pl.work_off + kClassTableBytes);
   if (cudaMemsetAsync(ws, 0, pl.zero_bytes, stream) != cudaSuccess) return SPRINTZ_ERR_CUDA;
   k_encode_batch_tails<<<pl.n, 128, 0, stream>>>(items);
   if (pl.n_work)
     k_encode_batch<<<pl.grid, kEncLaneThreads, (uint64_t)kEncLaneWarps * pl.region, stream>>>(
-        items, work, pl.n_work, reinterpret_cast<uint32_t *>(ws), pl.region, ws + pl.slots_off, pl.slot_region);
+        items, classes, work, reinterpret_cast<uint32_t *>(ws), pl.region, ws + pl.slots_off, pl.slot_region);
   return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
 }
 
