@@ -59,6 +59,7 @@ def parse(argv=None):
     ap.add_argument("--no-tune", action="store_true", help="batch: default schedules, no autotuner")
     ap.add_argument("--no-per-stream", action="store_true", help="batch: skip the per-stream launches")
     ap.add_argument("--no-delta", action="store_true", help="batch: skip the delta forecaster")
+    ap.add_argument("--no-sensor", action="store_true", help="batch: skip the single-stream sensor series")
     ap.add_argument("--workload", default="batch",
                     choices=["batch", "sensor", "walk", "huffman", "serve", "fire_speed", "dsweep", "gsweep",
                              "quantize"])
@@ -426,6 +427,50 @@ class BatchWorkload:
         return all(torch.equal(a, b) for a, b in zip(self.in_bufs, self.out_bufs))
 
 
+def sensor_extra(args, dev, local, spz, synth, torch, stream):
+    """One compress and one decompress of the 2^24 x 8 uint16 sensor series
+    (FIRE, chunk_rows 1024) per step, CUDA events, the lane kernels."""
+    x = synth.sensor_u16_torch(ROWS, COLS, seed=SEED, device=dev)
+    rows, D, w = ROWS, COLS, 16
+    o = spz.Opts(**opts_dict())
+    codec = spz.Codec(local)
+    try:
+        dst = torch.empty(spz.max_compressed_size(rows, D, w, o), dtype=torch.uint8, device=dev)
+        size = torch.zeros(1, dtype=torch.int64, device=dev)
+        ws_c = torch.empty(max(spz.compress_workspace_size(rows, D, w, o), 1), dtype=torch.uint8, device=dev)
+        codec.compress_into(x, rows, D, w, o, dst, size, ws_c)
+        torch.cuda.synchronize()
+        C = int(size.item())
+        info = spz.query(dst[:64].cpu().numpy().tobytes())
+        ws_d = torch.empty(max(spz.decompress_workspace_size(info), 1), dtype=torch.uint8, device=dev)
+        out = torch.empty_like(x)
+        steps = max(3, args.steps)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps + 3)]
+        for k in range(steps + 3):
+            ev[k][0].record(stream)
+            codec.compress_into(x, rows, D, w, o, dst, size, ws_c)
+            ev[k][1].record(stream)
+            codec.decompress_into(dst, C, info, out, ws_d)
+            ev[k][2].record(stream)
+        torch.cuda.synchronize()
+        codec.check()
+        if not torch.equal(out, x):
+            raise SystemExit("single-stream round trip mismatch")
+        enc = statistics.mean(e[0].elapsed_time(e[1]) for e in ev[3:])
+        dec = statistics.mean(e[1].elapsed_time(e[2]) for e in ev[3:])
+        U = x.numel() * 2
+        peak, _ = peaks()
+        return {"workload": SENSOR_WORKLOAD, "uncompressed_bytes": U, "compressed_bytes": C, "ratio": U / C,
+                "compress_gbs": U / (enc * 1e-3) / 1e9, "decompress_gbs": U / (dec * 1e-3) / 1e9,
+                "compress_ms": enc, "decompress_ms": dec,
+                "encode_frac": (U + C + 16 * info.n_chunks) / (enc * 1e-3) / 1e9 / peak,
+                "decode_frac": (U + C) / (dec * 1e-3) / 1e9 / peak,
+                "kernels": "k_encode_slots<16, 8>, k_decode_lanes<16, 8>", "steps": steps,
+                "generator": "sensor_u16 recipe drawn on the GPU (torch)"}
+    finally:
+        codec.close()
+
+
 def _headers(bufs, torch):
     """Host copies of every stream's 64-byte header (one gather, one copy)."""
     return torch.stack([b[:64] for b in bufs]).cpu().numpy()
@@ -646,6 +691,9 @@ def run_batch(args, rank, world, local):
         Dl["cc"].close()
         Dl["cd"].close()
 
+    # the single-stream workload beside it: uint16, D = 8, 2^24 rows, FIRE
+    sensor = None if args.no_sensor else sensor_extra(args, dev, local, spz, synth, torch, stream)
+
     C_total = F["C"]
     chunks_total = wl.chunks
     if dist:
@@ -703,6 +751,8 @@ def run_batch(args, rank, world, local):
     }
     if per_stream:
         line["per_stream_launches"] = per_stream
+    if sensor:
+        line["single_stream_sensor"] = sensor
     if delta:
         line["delta"] = delta
     if e2e:
