@@ -476,6 +476,98 @@ def _headers(bufs, torch):
     return torch.stack([b[:64] for b in bufs]).cpu().numpy()
 
 
+def run_e2e(wl, F, args, dev, local, dist, spz, torch, U_total):
+    """End to end through the public API with pinned host buffers.  Every
+    step, per slice of the batch: one host-to-device copy of its samples, a
+    batched compress, sprintz_pack of its compressed streams into one
+    device buffer, one device-to-host copy of those bytes and one back (a
+    store / load round trip through the host), a batched decompress reading
+    the packed streams, and one device-to-host copy of the decoded samples
+    into the host buffer the inputs came from (the round trip is lossless,
+    so every step's input is again the workload).  Slices take CUDA streams
+    in turn, so one slice's copies overlap another's kernels and the two
+    copy directions overlap."""
+    cr = wl.cudart
+    in_sizes = [t.numel() for t in wl.in_bufs]
+    nl = max(1, args.e2e_lanes)
+    lanes = [torch.cuda.Stream(dev) for _ in range(nl)]
+    sc = spz.Schedule(**{k: v for k, v in F["sched"]["compress"].items() if k != "tune_ms"})
+    sd = spz.Schedule(**{k: v for k, v in F["sched"]["decompress"].items() if k != "tune_ms"})
+    sz = F["sz"]
+    sl, packed = [], []
+    tot = [sum(sz[lo:hi]) for lo, hi in wl.slices]
+    h_off, h_tot = _aligned_offsets(tot, 256)
+    hc = PinnedBuffer(h_tot, cr)
+    try:
+        for s_i, (lo, hi) in enumerate(wl.slices):
+            ls = lanes[s_i % nl]
+            cc, cd = spz.Codec(local), spz.Codec(local)
+            _, _, wsc = cc.compress_batch(wl.xs[lo:hi], F["o"], stream=ls, schedule=sc, bufs=wl.bufs[lo:hi],
+                                          sizes=F["sizes"][lo:hi])
+            ptrs = torch.tensor([b.data_ptr() for b in wl.bufs[lo:hi]], dtype=torch.int64, device=dev)
+            offs = torch.zeros(hi - lo + 1, dtype=torch.int64, device=dev)
+            pk = torch.empty(max(tot[s_i], 1), dtype=torch.uint8, device=dev)
+            # the packed streams, where the warm-up sizes put them (the sizes are
+            # the same every step: the inputs are)
+            o_host = np.concatenate([[0], np.cumsum(sz[lo:hi])]).astype(np.int64)
+            views = [pk[int(o_host[k]):int(o_host[k + 1])] for k in range(hi - lo)]
+            _, wsd = cd.decompress_batch(views, F["infos"][lo:hi], sz[lo:hi], stream=ls, schedule=sd,
+                                         outs=wl.outs[lo:hi])
+            sl.append((ls, cc, cd, wsc, wsd, ptrs, offs, pk))
+        torch.cuda.synchronize()
+        in_ptr = [t.data_ptr() for t in wl.in_bufs]
+        out_ptr = [t.data_ptr() for t in wl.out_bufs]
+        hin_ptr = [h.ctypes.data for h in wl.host]
+        hc_ptr = hc.ptr.value
+
+        def step():
+            for s_i, (ls, cc, cd, wsc, wsd, ptrs, offs, pk) in enumerate(sl):
+                lo, hi = wl.slices[s_i]
+                sp = ls.cuda_stream
+                cr.copy(in_ptr[s_i], hin_ptr[s_i], in_sizes[s_i], Cudart.H2D, sp)
+                cc.batch_run(wsc, stream=ls)
+                cc.pack(ptrs, F["sizes"][lo:hi], pk, offs, stream=ls)
+                cr.copy(hc_ptr + h_off[s_i], pk.data_ptr(), tot[s_i], Cudart.D2H, sp)
+                cr.copy(pk.data_ptr(), hc_ptr + h_off[s_i], tot[s_i], Cudart.H2D, sp)
+                cd.batch_run(wsd, stream=ls)
+                cr.copy(hin_ptr[s_i], out_ptr[s_i], in_sizes[s_i], Cudart.D2H, sp)
+
+        step()
+        torch.cuda.synchronize()
+        a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_e2e = 3
+        a2.record(lanes[0])
+        for ls in lanes[1:]:
+            ls.wait_event(a2)
+        for _ in range(n_e2e):
+            step()
+        for ls in lanes[1:]:
+            done = torch.cuda.Event()
+            done.record(ls)
+            lanes[0].wait_event(done)
+        b2.record(lanes[0])
+        torch.cuda.synchronize()
+        for _, cc, cd, *_ in sl:
+            cc.check()
+            cd.check()
+        if not all(torch.equal(torch.from_numpy(h).to(dev), t) for h, t in zip(wl.host, wl.in_bufs)):
+            raise SystemExit("end-to-end round trip mismatch")
+        e2e_ms = slowest_rank_ms(a2.elapsed_time(b2) / n_e2e, dist, dev)
+        C = sum(tot)
+        return {"value": total_gbs(U_total, e2e_ms), "unit": "GB/s",
+                "h2d_bytes_per_step": sum(in_sizes) + C, "d2h_bytes_per_step": C + sum(in_sizes),
+                "ms_per_step": e2e_ms, "steps": n_e2e,
+                "pipelining": f"{len(sl)} slices on {nl} CUDA streams; pinned host buffers (cudaHostAlloc); "
+                              "per slice one copy of its samples each way and one of its packed compressed "
+                              "streams each way (sprintz_pack); the decoded samples return into the host "
+                              "buffer the inputs came from"}
+    finally:
+        for _, cc, cd, *_ in sl:
+            cc.close()
+            cd.close()
+        hc.free()
+
+
 def run_batch(args, rank, world, local):
     import torch
     import paper_1808_02515_gb300.sprintz as spz
@@ -598,87 +690,7 @@ def run_batch(args, rank, world, local):
                       "launches": "one sprintz_compress / sprintz_decompress call per stream, one CUDA stream"}
         codec.close()
 
-    # end to end through the public API with host buffers: every step copies
-    # each slice's samples in (one copy), compresses it, copies every stream's
-    # compressed bytes out and back in (one copy per stream), decompresses
-    # and copies the samples out (one copy) into the same pinned host buffer
-    # they came from (the round trip is lossless, so every step's input is
-    # again the workload).  Slices take CUDA streams in turn, so one slice's
-    # copies overlap another's kernels and the two directions overlap.
-    e2e = None
-    if not args.no_e2e:
-        cr = wl.cudart
-        in_sizes = [t.numel() for t in wl.in_bufs]
-        c_off, c_tot = _aligned_offsets(F["sz"], 256)
-        hc = PinnedBuffer(c_tot, cr)
-        hin_ptr = [h.ctypes.data for h in wl.host]
-        hc_ptr = hc.ptr.value
-        try:
-            nl = max(1, args.e2e_lanes)
-            lanes = [torch.cuda.Stream(dev) for _ in range(nl)]
-            sc = spz.Schedule(**{k: v for k, v in F["sched"]["compress"].items() if k != "tune_ms"})
-            sd = spz.Schedule(**{k: v for k, v in F["sched"]["decompress"].items() if k != "tune_ms"})
-            sl = []
-            for s_i, (lo, hi) in enumerate(wl.slices):
-                ls = lanes[s_i % nl]
-                cc, cd = spz.Codec(local), spz.Codec(local)
-                sizes = F["sizes"][lo:hi]
-                _, _, wsc = cc.compress_batch(wl.xs[lo:hi], F["o"], stream=ls, schedule=sc, bufs=wl.bufs[lo:hi],
-                                              sizes=sizes)
-                _, wsd = cd.decompress_batch(wl.bufs[lo:hi], F["infos"][lo:hi], F["sz"][lo:hi], stream=ls,
-                                             schedule=sd, outs=wl.outs[lo:hi])
-                sl.append((ls, cc, cd, wsc, wsd, lo, hi))
-            torch.cuda.synchronize()
-            in_ptr = [t.data_ptr() for t in wl.in_bufs]
-            out_ptr = [t.data_ptr() for t in wl.out_bufs]
-            buf_ptr = [b.data_ptr() for b in wl.bufs]
-            sz = F["sz"]
-
-            def e2e_step():
-                for s_i, (ls, cc, cd, wsc, wsd, lo, hi) in enumerate(sl):
-                    sp = ls.cuda_stream
-                    cr.copy(in_ptr[s_i], hin_ptr[s_i], in_sizes[s_i], Cudart.H2D, sp)
-                    cc.batch_run(wsc, stream=ls)
-                    for k in range(lo, hi):
-                        cr.copy(hc_ptr + c_off[k], buf_ptr[k], sz[k], Cudart.D2H, sp)
-                    for k in range(lo, hi):
-                        cr.copy(buf_ptr[k], hc_ptr + c_off[k], sz[k], Cudart.H2D, sp)
-                    cd.batch_run(wsd, stream=ls)
-                    cr.copy(hin_ptr[s_i], out_ptr[s_i], in_sizes[s_i], Cudart.D2H, sp)
-
-            e2e_step()
-            torch.cuda.synchronize()
-            a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            n_e2e = 3
-            a2.record(lanes[0])
-            for ls in lanes[1:]:
-                ls.wait_event(a2)
-            for _ in range(n_e2e):
-                e2e_step()
-            for ls in lanes[1:]:
-                done = torch.cuda.Event()
-                done.record(ls)
-                lanes[0].wait_event(done)
-            b2.record(lanes[0])
-            torch.cuda.synchronize()
-            for _, cc, cd, *_ in sl:
-                cc.check()
-                cd.check()
-            ok = all(torch.equal(torch.from_numpy(h).to(dev), t) for h, t in zip(wl.host, wl.in_bufs))
-            if not ok:
-                raise SystemExit("end-to-end round trip mismatch")
-            e2e_ms = slowest_rank_ms(a2.elapsed_time(b2) / n_e2e, dist, dev)
-            e2e = {"value": total_gbs(U_total, e2e_ms), "unit": "GB/s",
-                   "h2d_bytes_per_step": sum(in_sizes) + F["C"], "d2h_bytes_per_step": F["C"] + sum(in_sizes),
-                   "ms_per_step": e2e_ms, "steps": n_e2e,
-                   "pipelining": f"{len(sl)} slices on {nl} CUDA streams; pinned host buffers (cudaHostAlloc); "
-                                 "one copy per slice for samples, one per stream for compressed bytes; "
-                                 "the decoded samples return into the host buffer the inputs came from"}
-            for _, cc, cd, *_ in sl:
-                cc.close()
-                cd.close()
-        finally:
-            hc.free()
+    e2e = None if args.no_e2e else run_e2e(wl, F, args, dev, local, dist, spz, torch, U_total)
 
     # the delta forecaster (its own autotuned plans; overwrites the stream buffers)
     delta = None

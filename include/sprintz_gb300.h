@@ -159,6 +159,18 @@ int sprintz_append(sprintz_ctx *ctx, const void *src, uint64_t src_size, const s
                    const void *rows, uint64_t n_rows, void *dst, uint64_t dst_cap, uint64_t *d_out_size,
                    void *workspace, uint64_t ws_bytes, void *stream);
 
+/* Pack n device buffers back to back (for storing or moving many compressed
+ * streams with one copy; the paper has no counterpart).  Buffer k is
+ * d_src_ptrs[k] (a device array of n device addresses) and holds d_sizes[k]
+ * bytes (device array, e.g. the out_size words of a batched compress); dst
+ * receives them in order with no gaps, d_offsets[k] (device array of n + 1
+ * words) where each starts and d_offsets[n] the total -- an exclusive scan
+ * taken on the device, so the host reads nothing.  A total above dst_cap
+ * copies nothing and records SPRINTZ_ERR_DST_TOO_SMALL in the status word.
+ * The sources must not overlap dst. */
+int sprintz_pack(sprintz_ctx *ctx, const uint64_t *d_src_ptrs, const uint64_t *d_sizes, uint32_t n, void *dst,
+                 uint64_t dst_cap, uint64_t *d_offsets, void *stream);
+
 /* ---- Batches of independent streams --------------------------------------
  * Many streams of uneven length, width and D encoded or decoded by one
  * persistent kernel launch over the chunk groups of all of them.  The paper

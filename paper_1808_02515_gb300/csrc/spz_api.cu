@@ -15,6 +15,7 @@
 struct sprintz_ctx {
   int device;
   int *d_status;
+  uint32_t *d_pack_ok = nullptr;  // sprintz_pack: the scan's capacity verdict
   int *h_status;  // pinned
   spz::LaunchCfg cfg;
   std::string dev_name;
@@ -100,6 +101,7 @@ int sprintz_ctx_create(sprintz_ctx **out, int device) {
           cudaSuccess ||
       cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess ||
       cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&c->d_pack_ok, sizeof(uint32_t)) != cudaSuccess ||
       cudaMallocHost(&c->h_status, sizeof(int)) != cudaSuccess)
     rc = SPRINTZ_ERR_CUDA;
   cudaDeviceProp prop;
@@ -116,6 +118,7 @@ int sprintz_ctx_create(sprintz_ctx **out, int device) {
 void sprintz_ctx_destroy(sprintz_ctx *c) {
   if (!c) return;
   if (c->d_status) cudaFree(c->d_status);
+  if (c->d_pack_ok) cudaFree(c->d_pack_ok);
   if (c->h_status) cudaFreeHost(c->h_status);
   delete c;
 }
@@ -230,6 +233,13 @@ int sprintz_append(sprintz_ctx *ctx, const void *src, uint64_t src_size, const s
   return spz::launch_append(g, ctx->cfg, (const uint8_t *)src, src_size, info->tail_off, (const uint8_t *)rows,
                             n_rows, (uint8_t *)dst, dst_cap, d_out_size, (uint8_t *)workspace, ws_bytes,
                             ctx->d_status, (cudaStream_t)stream);
+}
+
+int sprintz_pack(sprintz_ctx *ctx, const uint64_t *d_src_ptrs, const uint64_t *d_sizes, uint32_t n, void *dst,
+                 uint64_t dst_cap, uint64_t *d_offsets, void *stream) {
+  if (!ctx || !d_offsets || (n && (!d_src_ptrs || !d_sizes || !dst))) return SPRINTZ_ERR_INVALID_ARG;
+  return spz::launch_pack(ctx->cfg, d_src_ptrs, d_sizes, n, (uint8_t *)dst, dst_cap, d_offsets, ctx->d_status,
+                          ctx->d_pack_ok, (cudaStream_t)stream);
 }
 
 int sprintz_ctx_set_failure_test(sprintz_ctx *ctx, uint32_t wait_limit, uint32_t skip_first_group) {

@@ -226,4 +226,103 @@ int launch_append(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint6
   return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
 }
 
+// ---- packing buffers back to back ---------------------------------------------
+
+// Exclusive scan of n sizes with one CTA (1024 threads, chunks of 1024),
+// then the capacity check.
+__global__ void __launch_bounds__(1024) k_pack_scan(const uint64_t *sizes, uint32_t n, uint64_t *offsets,
+                                                    uint64_t cap, int *status, uint32_t *ok) {
+  __shared__ uint64_t s_warp[32];
+  __shared__ uint64_t s_carry;
+  const uint32_t t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  if (t == 0) s_carry = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < n; base += 1024) {
+    const uint32_t i = base + t;
+    const uint64_t v = i < n ? sizes[i] : 0;
+    uint64_t x = v;
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      uint64_t w = s_warp[lane];
+#pragma unroll
+      for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+        if (lane >= o) w += y;
+      }
+      s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint64_t before = s_carry + (wid ? s_warp[wid - 1] : 0) + x - v;
+    if (i < n) offsets[i] = before;
+    __syncthreads();
+    if (t == 1023) s_carry = before + v;
+    __syncthreads();
+  }
+  if (t == 0) {
+    offsets[n] = s_carry;
+    const bool fits = s_carry <= cap;
+    *ok = fits ? 1u : 0u;
+    if (!fits) set_status(status, SPRINTZ_ERR_DST_TOO_SMALL);
+  }
+}
+
+// Every CTA copies the buffers k = blockIdx.x, blockIdx.x + gridDim.x, ...
+__global__ void __launch_bounds__(256) k_pack_copy(const uint64_t *srcs, const uint64_t *sizes, uint32_t n,
+                                                   uint8_t *dst, const uint64_t *offsets, const uint32_t *ok) {
+  if (!*ok) return;
+  for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
+    const uint8_t *src = reinterpret_cast<const uint8_t *>(srcs[k]);
+    uint8_t *d = dst + offsets[k];
+    const uint64_t len = sizes[k];
+    const uintptr_t mis = (uintptr_t)d ^ (uintptr_t)src;
+    uint64_t head = (16 - ((uintptr_t)d & 15)) & 15;
+    if (head > len) head = len;
+    if ((mis & 15) == 0) {
+      for (uint64_t q = threadIdx.x; q < head; q += blockDim.x) d[q] = src[q];
+      const uint64_t nv = (len - head) / 16;
+      const uint4 *s4 = reinterpret_cast<const uint4 *>(src + head);
+      uint4 *d4 = reinterpret_cast<uint4 *>(d + head);
+      for (uint64_t q = threadIdx.x; q < nv; q += blockDim.x) d4[q] = s4[q];
+      for (uint64_t q = head + nv * 16 + threadIdx.x; q < len; q += blockDim.x) d[q] = src[q];
+    } else {
+      // 16-byte stores built from the source's aligned words
+      for (uint64_t q = threadIdx.x; q < head; q += blockDim.x) d[q] = src[q];
+      const uint8_t *s1 = src + head;
+      const uint32_t sh = (uint32_t)((uintptr_t)s1 & 3) * 8;
+      const uint32_t *sw = reinterpret_cast<const uint32_t *>((uintptr_t)s1 & ~(uintptr_t)3);
+      const uint64_t nv = (len - head) / 16;
+      uint4 *d4 = reinterpret_cast<uint4 *>(d + head);
+      // the last unit of a misaligned source reads up to one word past its
+      // 16 bytes, inside [src, src + len) only when a whole word remains
+      const uint64_t safe = nv && (len - head) - 16 * nv < 4 ? nv - 1 : nv;
+      for (uint64_t q = threadIdx.x; q < safe; q += blockDim.x) {
+        const uint32_t *w = sw + 4 * q;
+        uint4 v;
+        v.x = __funnelshift_r(w[0], w[1], sh);
+        v.y = __funnelshift_r(w[1], w[2], sh);
+        v.z = __funnelshift_r(w[2], w[3], sh);
+        v.w = __funnelshift_r(w[3], w[4], sh);
+        d4[q] = v;
+      }
+      for (uint64_t q = head + safe * 16 + threadIdx.x; q < len; q += blockDim.x) d[q] = src[q];
+    }
+  }
+}
+
+int launch_pack(const LaunchCfg &cfg, const uint64_t *srcs, const uint64_t *sizes, uint32_t n, uint8_t *dst,
+                uint64_t dst_cap, uint64_t *offsets, int *d_status, uint32_t *d_ok, cudaStream_t stream) {
+  k_pack_scan<<<1, 1024, 0, stream>>>(sizes, n, offsets, dst_cap, d_status, d_ok);
+  if (n) {
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(n, (uint64_t)cfg.sm_count * 8);
+    k_pack_copy<<<grid, 256, 0, stream>>>(srcs, sizes, n, dst, offsets, d_ok);
+  }
+  return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
+}
+
 }  // namespace spz

@@ -430,6 +430,9 @@ uint64_t decode_rows_workspace_bytes(const Geom &g, const LaunchCfg &cfg, uint64
 int launch_decode_rows(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, uint64_t src_size,
                        uint64_t row_begin, uint64_t row_end, uint8_t *out, uint8_t *ws, uint64_t ws_bytes,
                        int *d_status, cudaStream_t stream);
+// Buffers back to back, offsets by a device-side exclusive scan (spz_append.cu).
+int launch_pack(const LaunchCfg &cfg, const uint64_t *srcs, const uint64_t *sizes, uint32_t n, uint8_t *dst,
+                uint64_t dst_cap, uint64_t *offsets, int *d_status, uint32_t *d_ok, cudaStream_t stream);
 // A stream followed by n_new more rows (spz_append.cu).
 uint64_t append_workspace_bytes(const Geom &g_old, const LaunchCfg &cfg, uint64_t n_new);
 int launch_append(const Geom &g_old, const LaunchCfg &cfg, const uint8_t *src, uint64_t src_size,

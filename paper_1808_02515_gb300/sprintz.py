@@ -126,6 +126,8 @@ def lib() -> ctypes.CDLL:
         L.sprintz_append_workspace_size.argtypes = [PI, u64]
         L.sprintz_append.restype = i32
         L.sprintz_append.argtypes = [vp, vp, u64, PI, vp, u64, vp, u64, vp, vp, u64, vp]
+        L.sprintz_pack.restype = i32
+        L.sprintz_pack.argtypes = [vp, vp, vp, u32, vp, u64, vp, vp]
         L.sprintz_ctx_set_failure_test.restype = i32
         L.sprintz_ctx_set_failure_test.argtypes = [vp, u32, u32]
         L.sprintz_compress_noalloc.restype = i32
@@ -435,6 +437,16 @@ class Codec:
         _check(rc, "sprintz_append")
         self._keep = ws
         return dst, size
+
+    def pack(self, src_ptrs, sizes, dst, offsets, stream=None) -> None:
+        """sprintz_pack: the buffers at the device addresses src_ptrs (int64
+        device tensor) of device sizes `sizes` (int64 tensor) back to back in
+        dst; offsets (int64 tensor, n + 1) receives where each starts."""
+        n = int(src_ptrs.numel())
+        rc = lib().sprintz_pack(self.ctx, ctypes.c_void_p(src_ptrs.data_ptr()), ctypes.c_void_p(sizes.data_ptr()),
+                                n, ctypes.c_void_p(dst.data_ptr()), dst.numel() * dst.element_size(),
+                                ctypes.c_void_p(offsets.data_ptr()), self._stream(stream))
+        _check(rc, "sprintz_pack")
 
     def set_failure_test(self, wait_limit: int = 0, skip_first_group: int = 0) -> None:
         """sprintz_ctx_set_failure_test (0, 0 = normal use)."""
