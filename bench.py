@@ -511,6 +511,7 @@ def run_e2e(wl, F, args, dev, local, dist, spz, torch, U_total):
             # the same every step: the inputs are)
             o_host = np.concatenate([[0], np.cumsum(sz[lo:hi])]).astype(np.int64)
             views = [pk[int(o_host[k]):int(o_host[k + 1])] for k in range(hi - lo)]
+            cc.pack(ptrs, F["sizes"][lo:hi], pk, offs, stream=ls)  # the plan below runs once on them
             _, wsd = cd.decompress_batch(views, F["infos"][lo:hi], sz[lo:hi], stream=ls, schedule=sd,
                                          outs=wl.outs[lo:hi])
             sl.append((ls, cc, cd, wsc, wsd, ptrs, offs, pk))
