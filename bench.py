@@ -144,27 +144,31 @@ class ClockSampler:
                 "samples_in_timed_region": len(inside)}
 
 
-def traffic_bytes(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary
-    (profiles/traffic.json), or None when the kernel sources changed since
-    the counters were taken."""
+def sources_sha256(files):
+    """Hash of the named files of the CUDA sources (the set one kernel is built from)."""
     import hashlib
+    csrc = os.path.join(ROOT, "paper_1808_02515_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(files):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def traffic_bytes(kernel: str):
+    """DRAM bytes per launch of `kernel` on this workload from the committed
+    ncu summary (profiles/traffic.json), or None when the kernel's sources
+    changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
+        k = rec["kernels"][kernel]
+        if k.get("sources_sha256") != sources_sha256(k["sources"]):
+            return None
+        return k.get("dram_bytes_per_launch")
     except Exception:
         return None
-    csrc = os.path.join(ROOT, "paper_1808_02515_gb300", "csrc")
-    h = hashlib.sha256()
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
-    if rec.get("sources_sha256") != h.hexdigest():
-        return None
-    k = rec.get("kernels", {}).get(kernel)
-    return None if k is None else k.get("dram_bytes_per_launch")
 
 
 def slowest_rank_ms(ms, dist, device):
