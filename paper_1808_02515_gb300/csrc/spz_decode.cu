@@ -1165,7 +1165,10 @@ static LaneRing lane_ring_plan(const Geom &g, const LaunchCfg &cfg, uint32_t nse
     r.seg <<= 1;
     r.seg_shift++;
   }
-  r.mirror = (gmax + 16 + 15) & ~15u;  // a group plus the words read past its end (at most 12 bytes)
+  // a group plus the words read past its end: 4 bytes, or 12 for the u8
+  // column-major records read as three words
+  const uint32_t slack = (g.w == 8 && g.col_major) ? 16u : 8u;
+  r.mirror = (gmax + slack + 15) & ~15u;
   while (r.seg < r.mirror) {
     r.seg <<= 1;
     r.seg_shift++;

@@ -158,10 +158,11 @@ class Server:
         store = self.store
         if slot.new_shards:
             sz = slot.sizes.cpu().numpy()
-            for r, buf, k in slot.new_shards:
+            # every new shard's header in one gather and one copy
+            heads = self.torch.stack([buf[:64] for _, buf, _ in slot.new_shards]).cpu().numpy()
+            for (r, buf, k), head in zip(slot.new_shards, heads):
                 n = int(sz[k])
-                head = buf[:64].cpu().numpy().tobytes()
-                info = spz.query(head)
+                info = spz.query(head.tobytes())
                 sh = Shard(buf[:n], n, info, r.row0)
                 store.streams[r.sid].append(sh)
                 store.streams[r.sid].sort(key=lambda x: x.row0)

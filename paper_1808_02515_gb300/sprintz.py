@@ -72,6 +72,26 @@ class Schedule:
         return Schedule(c.ctas_per_sm, c.ring_segments, c.prefetch_bytes, c.order)
 
 
+def _item_dtype():
+    """numpy layout of sprintz_batch_item, taken from the ctypes struct."""
+    import numpy as np
+    kinds = {ctypes.c_void_p: "<u8", ctypes.c_uint64: "<u8", ctypes.c_uint32: "<u4", ctypes.c_uint8: "u1"}
+    names, formats, offsets = [], [], []
+    for name, t in _BatchItem._fields_:
+        off = getattr(_BatchItem, name).offset
+        if t is _Opts:
+            for on, ot in _Opts._fields_:
+                names.append(on)
+                formats.append(kinds[ot])
+                offsets.append(off + getattr(_Opts, on).offset)
+        else:
+            names.append(name)
+            formats.append(kinds[t])
+            offsets.append(off)
+    return np.dtype({"names": names, "formats": formats, "offsets": offsets,
+                     "itemsize": ctypes.sizeof(_BatchItem)})
+
+
 @dataclass(frozen=True)
 class Opts:
     forecaster: int = FIRE
@@ -84,6 +104,9 @@ class Opts:
     def c(self) -> _Opts:
         return _Opts(self.forecaster, self.huffman, self.group_blocks, self.learn_shift,
                      self.chunk_rows, self.huff_chunks)
+
+
+_ITEM_DTYPE = _item_dtype()
 
 
 class SprintzError(RuntimeError):
@@ -462,11 +485,31 @@ class Codec:
     # ---- batches of independent streams -----------------------------------
 
     def _items(self, rows_d_w_opts, srcs, src_bytes, dsts, out_sizes, ranges=None):
-        arr = (_BatchItem * len(rows_d_w_opts))()
-        for k, (rows, D, w, o) in enumerate(rows_d_w_opts):
-            rb, re_ = ranges[k] if ranges else (0, 0)
-            arr[k] = _BatchItem(ctypes.c_void_p(srcs[k]), src_bytes[k], ctypes.c_void_p(dsts[k][0]),
-                                dsts[k][1], ctypes.c_void_p(out_sizes[k]), rows, D, w, o.c(), rb, re_)
+        """The sprintz_batch_item array, filled column by column with numpy in
+        a buffer that the ctypes array views (no per-item Python structs)."""
+        import numpy as np
+        n = len(rows_d_w_opts)
+        buf = np.zeros(n, dtype=_ITEM_DTYPE)
+        if n:
+            buf["src"] = srcs
+            buf["src_bytes"] = src_bytes
+            buf["dst"] = [d[0] for d in dsts]
+            buf["dst_cap"] = [d[1] for d in dsts]
+            buf["out_size"] = out_sizes
+            buf["rows"] = [t[0] for t in rows_d_w_opts]
+            buf["D"] = [t[1] for t in rows_d_w_opts]
+            buf["w"] = [t[2] for t in rows_d_w_opts]
+            opts = [t[3] for t in rows_d_w_opts]
+            first = opts[0]
+            if all(o is first or o == first for o in opts):
+                opts = [first] * n
+            for name in ("forecaster", "huffman", "group_blocks", "learn_shift", "chunk_rows", "huff_chunks"):
+                buf[name] = [getattr(o, name) for o in opts]
+            if ranges:
+                buf["row_begin"] = [r[0] for r in ranges]
+                buf["row_end"] = [r[1] for r in ranges]
+        arr = (_BatchItem * n).from_buffer(buf)
+        arr._keep = buf  # the numpy buffer backs the ctypes array
         return arr
 
     def batch_plan_run(self, arr, compress: int, stream=None, schedule: "Schedule | None" = None,
