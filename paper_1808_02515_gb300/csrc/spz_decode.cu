@@ -1051,15 +1051,19 @@ struct DecBatchItem {
 static_assert(sizeof(DecBatchItem) % 8 == 0, "descriptors are copied in 8-byte words");
 
 // One chunk group of a batch item through the lane decoder specialised for
-// its column count (a call per group keeps each variant's code apart).
+// its column count (a call per group keeps each variant's code apart).  The
+// warp's region arrives as an offset into the dynamic shared memory, so that
+// the callee addresses it as shared memory rather than through generic
+// pointers.
 template <int W, int DT>
-__device__ __noinline__ void decode_batch_group(const DecBatchItem &it, uint64_t grp, uint8_t *wsm) {
-  decode_group<W, DT>(it.p, it.rg, grp, wsm);
+__device__ __noinline__ void decode_batch_group(const DecBatchItem &it, uint64_t grp, uint32_t wsm_off) {
+  extern __shared__ __align__(16) uint8_t dsm[];
+  decode_group<W, DT>(it.p, it.rg, grp, dsm + wsm_off);
 }
 
 // Variant table: [w == 16][D] (D = 0: any column count up to 32).  One
 // indirect call site for every variant keeps the kernel's frame small.
-typedef void (*DecBatchGroupFn)(const DecBatchItem &, uint64_t, uint8_t *);
+typedef void (*DecBatchGroupFn)(const DecBatchItem &, uint64_t, uint32_t);
 #define SPZ_DEC_ROW(W)                                                                                  \
   {decode_batch_group<W, 0>,  decode_batch_group<W, 1>,  decode_batch_group<W, 2>,                      \
    decode_batch_group<W, 3>,  decode_batch_group<W, 4>,  decode_batch_group<W, 5>,                      \
@@ -1080,7 +1084,7 @@ __global__ void __launch_bounds__(kLaneThreads, 7) k_decode_batch(const DecBatch
   extern __shared__ __align__(16) uint8_t dsm[];
   __shared__ __align__(16) DecBatchItem s_it[kLaneWarps];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint8_t *wsm = dsm + (uint64_t)warp * per_warp;
+  const uint32_t wsm_off = warp * per_warp;
   constexpr uint32_t kWords = sizeof(DecBatchItem) / 8;
   uint32_t c = batch_home(classes);
   uint64_t e = 0;
@@ -1093,7 +1097,7 @@ __global__ void __launch_bounds__(kLaneThreads, 7) k_decode_batch(const DecBatch
     __syncwarp();
     const DecBatchItem &it = s_it[warp];
     const uint32_t D = it.p.g.D;
-    g_dec_batch_fns[it.p.g.w == 16][D <= 16 ? D : 0](it, grp, wsm);
+    g_dec_batch_fns[it.p.g.w == 16][D <= 16 ? D : 0](it, grp, wsm_off);
     __syncwarp();
   }
 }

@@ -1390,15 +1390,19 @@ static_assert(sizeof(EncBatchItem) % 8 == 0, "descriptors are copied in 8-byte w
 
 // One chunk group of a batch item, through the slot encoder specialised for
 // the item's column count (a call per group keeps each variant's code apart).
+// The warp's region arrives as an offset into the dynamic shared memory, so
+// that the callee addresses it as shared memory (32-bit addresses, shared
+// atomics) rather than through generic pointers.
 template <int W, int DT>
-__device__ __noinline__ void encode_batch_group(const EncBatchItem &it, uint32_t grp, uint8_t *wsm,
+__device__ __noinline__ void encode_batch_group(const EncBatchItem &it, uint32_t grp, uint32_t wsm_off,
                                                 uint8_t *wslots) {
-  encode_group_slots<W, DT>(it.p, it.cfg, grp, wsm, wslots);
+  extern __shared__ __align__(16) uint8_t smem[];
+  encode_group_slots<W, DT>(it.p, it.cfg, grp, smem + wsm_off, wslots);
 }
 
 // Variant table: [w == 16][D] (D = 0: any column count up to 32).  One
 // indirect call site for every variant keeps the kernel's frame small.
-typedef void (*EncBatchGroupFn)(const EncBatchItem &, uint32_t, uint8_t *, uint8_t *);
+typedef void (*EncBatchGroupFn)(const EncBatchItem &, uint32_t, uint32_t, uint8_t *);
 #define SPZ_ENC_ROW(W)                                                                                  \
   {encode_batch_group<W, 0>,  encode_batch_group<W, 1>,  encode_batch_group<W, 2>,                      \
    encode_batch_group<W, 3>,  encode_batch_group<W, 4>,  encode_batch_group<W, 5>,                      \
@@ -1423,7 +1427,7 @@ __global__ void __launch_bounds__(kEncLaneThreads, 7) k_encode_batch(const EncBa
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ __align__(16) EncBatchItem s_it[kEncLaneWarps];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint8_t *wsm = smem + (uint64_t)warp * region;
+  const uint32_t wsm_off = warp * region;
   const uint64_t gwarp = (uint64_t)blockIdx.x * kEncLaneWarps + warp;
   uint8_t *wslots = slots + gwarp * slot_region;
   constexpr uint32_t kWords = sizeof(EncBatchItem) / 8;
@@ -1438,7 +1442,7 @@ __global__ void __launch_bounds__(kEncLaneThreads, 7) k_encode_batch(const EncBa
     __syncwarp();
     const EncBatchItem &it = s_it[warp];
     const uint32_t D = it.p.g.D;
-    g_enc_batch_fns[it.p.g.w == 16][D <= 16 ? D : 0](it, grp, wsm, wslots);
+    g_enc_batch_fns[it.p.g.w == 16][D <= 16 ? D : 0](it, grp, wsm_off, wslots);
     __syncwarp();
   }
 }
