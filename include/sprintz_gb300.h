@@ -209,7 +209,9 @@ typedef struct {
  *   order           work order inside each (w, D) class of streams (the
  *                   classes come one after another, heaviest chunk groups
  *                   first): 1 = stream order, 2 = longest stream first,
- *                   3 = round robin over the class's streams. */
+ *                   3 = round robin over the class's streams.
+ * Defaults: 7 CTAs per SM; compress round robin without prefetch;
+ * decompress 2 ring segments, 8 KB prefetch, longest stream first. */
 typedef struct {
   uint32_t ctas_per_sm;
   uint32_t ring_segments;

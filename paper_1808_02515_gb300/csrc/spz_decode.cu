@@ -1312,6 +1312,17 @@ int plan_batch_decode(const sprintz_batch_item *items, uint32_t n, const LaunchC
     vD[i] = g.D;
     vgroups[i] = (d.p.c_end - d.p.c_begin + K - 1) / K;
   }
+  // streams whose rings leave room in the widest warp region (set by the
+  // narrowest streams) take larger segments: fewer segment changes per chunk
+  for (uint32_t i = 0; i < n; ++i) {
+    DecBatchItem &d = v[i];
+    if (!d.p.g.n_chunks) continue;
+    for (uint32_t ms = d.rg.seg * 2; ms <= 4096; ms *= 2) {
+      const LaneRing r = lane_ring_plan(d.p.g, cfg, d.rg.nseg, dec_staged((int)d.p.g.D), ms);
+      if (!r.per_warp || r.per_warp > region || r.nseg != d.rg.nseg) break;
+      d.rg = r;
+    }
+  }
   uint64_t n_work = 0;
   batch_work_list(vw, vD, vgroups, sched.order, (uint32_t)cfg.sm_count, work, &n_work);
   memset(pl, 0, sizeof(*pl));
