@@ -210,8 +210,9 @@ typedef struct {
  *                   classes come one after another, heaviest chunk groups
  *                   first): 1 = stream order, 2 = longest stream first,
  *                   3 = round robin over the class's streams.
- * Defaults: 7 CTAs per SM; compress round robin without prefetch;
- * decompress 2 ring segments, 8 KB prefetch, longest stream first. */
+ * Defaults: as many CTAs per SM as fit (7 compress, 6 decompress); compress
+ * round robin without prefetch; decompress 2 ring segments, 8 KB prefetch,
+ * longest stream first. */
 typedef struct {
   uint32_t ctas_per_sm;
   uint32_t ring_segments;

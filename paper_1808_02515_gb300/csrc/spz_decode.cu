@@ -1076,8 +1076,13 @@ __device__ DecBatchGroupFn g_dec_batch_fns[2][17] = {SPZ_DEC_ROW(8), SPZ_DEC_ROW
 
 // Batched decode: persistent warps take work entries (stream, chunk group),
 // one ticket per (w, D) class, from their SM's home class first; each warp
-// copies its item's descriptor into shared memory once per group.
-__global__ void __launch_bounds__(kLaneThreads, 7) k_decode_batch(const DecBatchItem *items,
+// copies its item's descriptor into shared memory once per group.  Bounded at
+// 6 CTAs per SM (80 registers): the per-D callees hold the stream's
+// descriptor fields in registers, which the single-stream kernels read from
+// the constant bank, and at 72 registers they reload some of them from local
+// memory inside the block loop (measured 2-3 % slower; 64 registers spill far
+// more and are 15 % slower).
+__global__ void __launch_bounds__(kLaneThreads, 6) k_decode_batch(const DecBatchItem *items,
                                                                  const BatchClasses *classes,
                                                                  const uint64_t *work, uint32_t *tickets,
                                                                  uint32_t per_warp) {

@@ -1984,7 +1984,7 @@ int launch_encode_fast(const Geom &g, const LaunchCfg &cfg, const uint8_t *src, 
 // 8 KB L2 prefetch window.
 sprintz_schedule batch_default_schedule(int compress) {
   sprintz_schedule s;
-  s.ctas_per_sm = 7;
+  s.ctas_per_sm = compress ? 7 : 6;  // as many as the kernels' register bounds allow
   s.ring_segments = 2;
   s.prefetch_bytes = compress ? 1 : 8192;
   s.order = compress ? 3 : 2;
