@@ -412,8 +412,16 @@ __global__ void __launch_bounds__(kHuffWarps * 32) k_huff_sizes(HuffEncParams p)
     uint64_t i0;
     uint32_t len;
     huff_sub_range(packed, k, &i0, &len);
+    // aligned words covering the sub-block's bytes (P has slack after its
+    // last byte), bytes outside it masked
     uint32_t bits = 0;
-    for (uint64_t i = i0 + lane; i < i0 + len; i += 32) bits += s_len[warp][body[i]];
+    const uintptr_t A = (uintptr_t)(body + i0), B = A + len;
+    for (uintptr_t q = (A & ~(uintptr_t)3) + 4 * (uintptr_t)lane; q < B; q += 128) {
+      const uint32_t v = *reinterpret_cast<const uint32_t *>(q);
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (q + t >= A && q + t < B) bits += s_len[warp][(v >> (8 * t)) & 255u];
+    }
     for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xFFFFFFFFu, bits, o);
     if (lane == 0) p.sub_off[(uint64_t)c * p.slots + k] = (uint32_t)run;
     run += (bits + 7) / 8;
@@ -530,14 +538,22 @@ __global__ void __launch_bounds__(kHuffEncWarps * 32) k_huff_encode(HuffEncParam
   uint32_t *sin = s_in[warp];
   for (uint32_t q = lane; q < nw; q += 32) sin[q + (q >> 4)] = w32[q];
   __syncwarp();
-  auto byte_at = [&](uint32_t j) {
-    const uint32_t x = j + lead, q = x >> 2;
-    return (sin[q + (q >> 4)] >> (8 * (x & 3))) & 255u;
-  };
-  const uint32_t per = (n + 31) / 32;
+  // each lane codes a run of `per` bytes, a multiple of 4, so that its bytes
+  // come four at a time from one funnel-shifted pair of words
+  const uint32_t per = ((n + 31) / 32 + 3) & ~3u;
   const uint32_t a = min(n, lane * per), b = min(n, a + per);
+  const uint32_t sh_lead = 8 * lead;
+  auto word4 = [&](uint32_t i) {  // bytes i .. i + 3 (i a multiple of 4)
+    const uint32_t q = i >> 2;
+    return __funnelshift_r(sin[q + (q >> 4)], sin[(q + 1) + ((q + 1) >> 4)], sh_lead);
+  };
   uint32_t nb = 0;
-  for (uint32_t i = a; i < b; ++i) nb += s_code[warp][byte_at(i)] >> 11;
+  for (uint32_t i = a; i < b; i += 4) {
+    const uint32_t w = word4(i), m = b - i;
+#pragma unroll
+    for (uint32_t t = 0; t < 4; ++t)
+      if (t < m) nb += s_code[warp][(w >> (8 * t)) & 255u] >> 11;
+  }
   uint32_t incl = nb;
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
@@ -554,10 +570,9 @@ __global__ void __launch_bounds__(kHuffEncWarps * 32) k_huff_encode(HuffEncParam
   uint32_t wi = bit0 >> 5, nacc = bit0 & 31;
   bool first_shared = nacc != 0;
   uint64_t acc = 0;
-  for (uint32_t i = a; i < b; ++i) {
-    const uint32_t e = s_code[warp][byte_at(i)];
-    acc |= (uint64_t)(e & 0x7FFu) << nacc;
-    nacc += e >> 11;
+  // two codes (at most 22 bits) join the accumulator (under 32 bits) before
+  // a full word can leave it
+  auto emit = [&]() {
     if (nacc >= 32) {
       if (first_shared) atomicOr(&buf[pad(wi)], (uint32_t)acc);
       else buf[pad(wi)] = (uint32_t)acc;
@@ -565,6 +580,18 @@ __global__ void __launch_bounds__(kHuffEncWarps * 32) k_huff_encode(HuffEncParam
       acc >>= 32;
       nacc -= 32;
       ++wi;
+    }
+  };
+  for (uint32_t i = a; i < b; i += 4) {
+    const uint32_t w = word4(i), m = b - i;
+#pragma unroll
+    for (uint32_t t = 0; t < 4; ++t) {
+      if (t < m) {
+        const uint32_t e = s_code[warp][(w >> (8 * t)) & 255u];
+        acc |= (uint64_t)(e & 0x7FFu) << nacc;
+        nacc += e >> 11;
+      }
+      if (t & 1) emit();
     }
   }
   if (b > a && nacc > 0) atomicOr(&buf[pad(wi)], (uint32_t)acc);
