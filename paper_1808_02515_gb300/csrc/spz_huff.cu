@@ -21,8 +21,9 @@
 // package-merge and builds the canonical code table; k_huff_sizes (a warp per
 // chunk) sums the coded bits of every sub-block; k_huff_decide (a CTA per
 // segment) chooses raw or coded and places the chunks inside the segment;
-// k_huff_scan places the segments; k_huff_encode (a warp per sub-block)
-// writes the coded bytes, the jump tables and the chunk table, and
+// k_huff_scan places the segments; k_huff_encode (persistent warps, each
+// over a contiguous range of sub-blocks, a sub-block at a time) writes the
+// coded bytes, the jump tables and the chunk table, and
 // k_huff_enc_finish the header and the raw tail.
 // Decode: k_huff_dec_prep (a CTA per segment) checks the table (lengths <= 11,
 // Kraft), builds its 11-bit lookup table and maps the segment's sub-blocks to
@@ -412,16 +413,8 @@ __global__ void __launch_bounds__(kHuffWarps * 32) k_huff_sizes(HuffEncParams p)
     uint64_t i0;
     uint32_t len;
     huff_sub_range(packed, k, &i0, &len);
-    // aligned words covering the sub-block's bytes (P has slack after its
-    // last byte), bytes outside it masked
     uint32_t bits = 0;
-    const uintptr_t A = (uintptr_t)(body + i0), B = A + len;
-    for (uintptr_t q = (A & ~(uintptr_t)3) + 4 * (uintptr_t)lane; q < B; q += 128) {
-      const uint32_t v = *reinterpret_cast<const uint32_t *>(q);
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if (q + t >= A && q + t < B) bits += s_len[warp][(v >> (8 * t)) & 255u];
-    }
+    for (uint64_t i = i0 + lane; i < i0 + len; i += 32) bits += s_len[warp][body[i]];
     for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xFFFFFFFFu, bits, o);
     if (lane == 0) p.sub_off[(uint64_t)c * p.slots + k] = (uint32_t)run;
     run += (bits + 7) / 8;
@@ -472,37 +465,36 @@ __global__ void __launch_bounds__(256) k_huff_decide(HuffEncParams p) {
   if (t == 0) p.seg_total[s] = s_carry;
 }
 
-// One warp per sub-block: its packed bytes are copied to shared memory with
-// coalesced word loads; lanes code contiguous runs of them, a warp scan of
-// their bit counts places them in a shared buffer (whole words stored, the
-// words two lanes share OR-ed), and the coded bytes go to the stream in
-// 4-byte stores.  Both shared buffers have a pad word after every 16, so
-// that lanes working about 16 words apart hit different banks.  The first
-// warp of a chunk writes its table entry, the others their jump-table
-// offsets.
-__global__ void __launch_bounds__(kHuffEncWarps * 32) k_huff_encode(HuffEncParams p) {
-  __shared__ uint16_t s_code[kHuffEncWarps][256];  // reversed code | length << 11
-  __shared__ uint32_t s_in[kHuffEncWarps][kHuffInWords];
-  __shared__ uint32_t s_buf[kHuffEncWarps][kHuffBufWords];
+// One sub-block slot (chunk c, sub-block k) for k_huff_encode: its packed
+// bytes are copied to shared memory with coalesced word loads; lanes code
+// contiguous runs of them, a warp scan of their bit counts places them in a
+// shared buffer (whole words stored, the words two lanes share OR-ed), and
+// the coded bytes go to the stream in 4-byte stores.  Both shared buffers
+// have a pad word after every 16, so that lanes working about 16 words apart
+// hit different banks.  Sub-block 0 writes the chunk's table entry, the
+// others their jump-table offsets.  s_code holds the code table of segment
+// *cur_s; it is loaded again only when the slot's segment differs.
+__device__ __forceinline__ void huff_encode_slot(const HuffEncParams &p, uint64_t slot, uint32_t lane,
+                                                 uint16_t *s_code, uint32_t *sin, uint32_t *buf,
+                                                 uint32_t *cur_s) {
   const Geom &g = p.g;
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint64_t slot = (uint64_t)blockIdx.x * kHuffEncWarps + warp;
-  const uint64_t c64 = slot / p.slots;
-  if (c64 >= g.n_chunks) return;
-  const uint32_t c = (uint32_t)c64, k = (uint32_t)(slot % p.slots);
+  const uint32_t c = (uint32_t)(slot / p.slots), k = (uint32_t)(slot % p.slots);
   const uint32_t s = c / g.huff_chunks;
-  // every per-slot load issued at once (all in bounds for any slot); the
-  // segment's code table follows into shared memory
+  // every per-slot load issued at once (all in bounds for any slot), with
+  // the segment's code table when it is a new one
   uint64_t off;
   uint32_t nrec, packed;
   p_entry(p, c, &off, &nrec, &packed);
   const bool raw = p.seg_raw[s] != 0;
   const uint64_t seg_base = p.seg_prefix[s], chunk_base = p.chunk_pos[c], coded = p.chunk_coded[c];
   const uint32_t start = p.sub_off[(uint64_t)c * p.slots + k];
-  const uint32_t *cs = p.codes + (uint64_t)s * 256;
+  const bool new_table = s != *cur_s;
   uint32_t ce[8];
+  if (new_table) {
+    const uint32_t *cs = p.codes + (uint64_t)s * 256;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) ce[i] = cs[lane + 32 * i];
+    for (int i = 0; i < 8; ++i) ce[i] = cs[lane + 32 * i];
+  }
   const uint32_t n_sub = huff_n_sub(packed);
   if (k >= n_sub) return;
   const uint64_t cpos = seg_base + chunk_base;  // from data_off
@@ -528,14 +520,16 @@ __global__ void __launch_bounds__(kHuffEncWarps * 32) k_huff_encode(HuffEncParam
   }
   const uint32_t jump = 4 * (n_sub - 1);
   if (k > 0 && lane < 4) d[4 * (k - 1) + lane] = (uint8_t)((start - jump) >> (8 * lane));
+  if (new_table) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i) s_code[warp][lane + 32 * i] = (uint16_t)((ce[i] & 0x7FFu) | ((ce[i] >> 16) << 11));
+    for (int i = 0; i < 8; ++i) s_code[lane + 32 * i] = (uint16_t)((ce[i] & 0x7FFu) | ((ce[i] >> 16) << 11));
+    *cur_s = s;
+  }
   // the sub-block's bytes: aligned words from up to 3 bytes before it to up
   // to 3 bytes after it (P has slack after its last byte)
   const uint32_t lead = (uint32_t)((uintptr_t)in & 3);
   const uint32_t *w32 = reinterpret_cast<const uint32_t *>((uintptr_t)in - lead);
   const uint32_t nw = (n + lead + 3) / 4;
-  uint32_t *sin = s_in[warp];
   for (uint32_t q = lane; q < nw; q += 32) sin[q + (q >> 4)] = w32[q];
   __syncwarp();
   // each lane codes a run of `per` bytes, a multiple of 4, so that its bytes
@@ -552,7 +546,7 @@ __global__ void __launch_bounds__(kHuffEncWarps * 32) k_huff_encode(HuffEncParam
     const uint32_t w = word4(i), m = b - i;
 #pragma unroll
     for (uint32_t t = 0; t < 4; ++t)
-      if (t < m) nb += s_code[warp][(w >> (8 * t)) & 255u] >> 11;
+      if (t < m) nb += s_code[(w >> (8 * t)) & 255u] >> 11;
   }
   uint32_t incl = nb;
   for (int o = 1; o < 32; o <<= 1) {
@@ -560,7 +554,6 @@ __global__ void __launch_bounds__(kHuffEncWarps * 32) k_huff_encode(HuffEncParam
     if (lane >= o) incl += y;
   }
   const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-  uint32_t *buf = s_buf[warp];
   auto pad = [](uint32_t w) { return w + (w >> 4); };
   for (uint32_t i = lane; i <= pad(total / 32 + 1); i += 32) buf[i] = 0;
   __syncwarp();
@@ -587,7 +580,7 @@ __global__ void __launch_bounds__(kHuffEncWarps * 32) k_huff_encode(HuffEncParam
 #pragma unroll
     for (uint32_t t = 0; t < 4; ++t) {
       if (t < m) {
-        const uint32_t e = s_code[warp][(w >> (8 * t)) & 255u];
+        const uint32_t e = s_code[(w >> (8 * t)) & 255u];
         acc |= (uint64_t)(e & 0x7FFu) << nacc;
         nacc += e >> 11;
       }
@@ -610,6 +603,23 @@ __global__ void __launch_bounds__(kHuffEncWarps * 32) k_huff_encode(HuffEncParam
     dw[m] = __funnelshift_r(buf[pad(w)], buf[pad(w + 1)], sh);
   }
   for (uint32_t i = hb + 4 * nout + lane; i < nbytes; i += 32) dd[i] = byte_of(i);
+}
+
+// Persistent warps, each over a contiguous range of sub-block slots (those of
+// one or two segments, so that the code table is mostly loaded once).
+__global__ void __launch_bounds__(kHuffEncWarps * 32) k_huff_encode(HuffEncParams p, uint64_t per_warp) {
+  __shared__ uint16_t s_code[kHuffEncWarps][256];  // reversed code | length << 11
+  __shared__ uint32_t s_in[kHuffEncWarps][kHuffInWords];
+  __shared__ uint32_t s_buf[kHuffEncWarps][kHuffBufWords];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t total = (uint64_t)p.g.n_chunks * p.slots;
+  const uint64_t first = ((uint64_t)blockIdx.x * kHuffEncWarps + warp) * per_warp;
+  const uint64_t last = umin64(total, first + per_warp);
+  uint32_t cur_s = 0xFFFFFFFFu;
+  for (uint64_t slot = first; slot < last; ++slot) {
+    huff_encode_slot(p, slot, lane, s_code[warp], s_in[warp], s_buf[warp], &cur_s);
+    __syncwarp();  // the warp's shared buffers are reused by the next slot
+  }
 }
 
 // Header and raw tail of the Huffman stream.
@@ -993,7 +1003,16 @@ int launch_encode_huffman(const Geom &g, const LaunchCfg &cfg, const uint8_t *sr
   const HuffEncLayout L = huff_enc_layout(g, cfg);
   if (ws_bytes < L.total) return SPRINTZ_ERR_WS_TOO_SMALL;
   const uint64_t hist_grid = (uint64_t)g.n_segments * L.slices;
-  const uint64_t enc_grid = ((uint64_t)g.n_chunks * L.slots + kHuffEncWarps - 1) / kHuffEncWarps;
+  // the encoder's persistent warps: as many as fit, each over an equal
+  // contiguous range of sub-block slots
+  int enc_occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&enc_occ, k_huff_encode, kHuffEncWarps * 32, 0) != cudaSuccess ||
+      enc_occ < 1)
+    enc_occ = 1;
+  const uint64_t enc_slots = std::max<uint64_t>(1, (uint64_t)g.n_chunks * L.slots);
+  const uint64_t enc_warps = std::min<uint64_t>(enc_slots, (uint64_t)cfg.sm_count * enc_occ * kHuffEncWarps);
+  const uint64_t enc_per_warp = (enc_slots + enc_warps - 1) / enc_warps;
+  const uint64_t enc_grid = ((enc_slots + enc_per_warp - 1) / enc_per_warp + kHuffEncWarps - 1) / kHuffEncWarps;
   if (hist_grid > 0x7FFFFFFFull || enc_grid > 0x7FFFFFFFull) return SPRINTZ_ERR_UNSUPPORTED;
   const Geom gp = plain_geom(g);
   uint8_t *P = ws + L.P;
@@ -1028,7 +1047,7 @@ int launch_encode_huffman(const Geom &g, const LaunchCfg &cfg, const uint8_t *sr
   k_huff_sizes<<<(g.n_chunks + kHuffWarps - 1) / kHuffWarps, kHuffWarps * 32, 0, stream>>>(hp);
   k_huff_decide<<<g.n_segments, 256, 0, stream>>>(hp);
   k_huff_scan<<<1, 1024, 0, stream>>>(hp.seg_total, hp.seg_prefix, g.n_segments);
-  k_huff_encode<<<(uint32_t)enc_grid, kHuffEncWarps * 32, 0, stream>>>(hp);
+  k_huff_encode<<<(uint32_t)enc_grid, kHuffEncWarps * 32, 0, stream>>>(hp, enc_per_warp);
   k_huff_enc_finish<<<1, 256, 0, stream>>>(hp);
   return cudaGetLastError() == cudaSuccess ? SPRINTZ_OK : SPRINTZ_ERR_CUDA;
 }
