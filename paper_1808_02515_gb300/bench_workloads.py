@@ -204,21 +204,29 @@ def run_serve(args, codec, dev, line, synth, spz):
     reqs = serve.poisson_requests(store, n_req, rate=rate, seed=4, append_frac=0.1, append_rows=8192,
                                   append_source=lambda sid, k: pool[(sid * 7 + k) % len(pool)])
     server = serve.Server(store, mem_budget=4 << 30, max_batch=512, n_slots=3)
-    stats = server.run(reqs, realtime=True)
+    stats = server.run(reqs, realtime=True, keep_results=False)
     warm = [r for r in reqs if r.t_arrival >= 1.0]
     lat = np.array([r.t_done - r.t_arrival for r in warm])
     rb = D * 2
     served = sum((r.b - r.a) * rb if r.kind == "range" else r.rows.shape[0] * rb for r in warm)
     span = max(r.t_done for r in warm) - min(r.t_arrival for r in warm)
+    # capacity: the same mix, every request arrived at once (closed loop)
+    reqs2 = serve.poisson_requests(store, n_req, rate=rate, seed=5, append_frac=0.1, append_rows=8192,
+                                   append_source=lambda sid, k: pool[(sid * 7 + k) % len(pool)])
+    b0 = server.batches
+    cap = server.run(reqs2, realtime=False, keep_results=False)
     line.update({
         "value": served / span / 1e9, "ms_per_step": None, "dtype": "u16",
         "config": {"workload": "serve_1000_streams_u16_D4_2^20rows_poisson_20k_req_s",
                    "rate_req_s": rate, "requests": len(reqs), "measured_requests": len(warm),
                    "mix": "90% range 1K-64K rows (log-uniform, uniform start), 10% append 8192 rows",
-                   "generator_s": gen_s, "mem_budget": 4 << 30, "slots": 3, "max_batch": 512},
+                   "generator_s": gen_s, "mem_budget": 4 << 30, "slots": 3, "max_batch": 512,
+                   "results": "each range's rows released once it completes (a consuming client)"},
         "serving": {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                     "gbs": served / span / 1e9, "batches": stats["batches"], "peak_mem": stats["peak_mem"],
-                    "wall_s": stats["wall_s"]}})
+                    "wall_s": stats["wall_s"],
+                    "closed_loop": {"requests": len(reqs2), "req_s": len(reqs2) / cap["wall_s"],
+                                    "gbs": cap["gbs"], "batches": cap["batches"] - b0}}})
 
 
 SWEEP_D = (1, 2, 3, 4, 5, 6, 8, 12, 16, 24, 32, 40, 48, 64, 80)

@@ -33,6 +33,12 @@ class Shard:
     size: int            # stream bytes
     info: spz.Info
     row0: int            # first row of the logical stream held here
+    ptr: int = 0         # the stream's device address
+    shape: tuple = ()    # (rows, D, w, Opts), as a batch item takes them
+
+    def __post_init__(self):
+        self.ptr = self.buf.data_ptr()
+        self.shape = (self.info.rows, self.info.D, self.info.w, self.info.opts)
 
 
 @dataclass
@@ -112,6 +118,7 @@ class Server:
         self.mem_used = 0
         self.peak_mem = 0
         self.batches = 0
+        self._caps = {}  # rows -> largest compressed size of an append of that many rows
 
     def _need(self, r: Request) -> int:
         rb = self.store.D * (self.store.w // 8)
@@ -122,31 +129,53 @@ class Server:
         n = r.rows.shape[0]
         return spz.max_compressed_size(n, self.store.D, self.store.w, self.store.opts) + 4096
 
+    def _cap(self, rows: int) -> int:
+        c = self._caps.get(rows)
+        if c is None:
+            c = self._caps[rows] = spz.max_compressed_size(rows, self.store.D, self.store.w, self.store.opts)
+        return c
+
     def _launch(self, slot: _Slot, reqs: list) -> None:
         torch = self.torch
         store = self.store
         codec = slot.codec
+        dev = f"cuda:{codec.device}"
+        rb = store.D * (store.w // 8)
         slot.reqs, slot.new_shards, slot.keep = reqs, [], []
         with torch.cuda.stream(slot.stream):
             ranges = [r for r in reqs if r.kind == "range"]
             if ranges:
-                streams, infos, sizes, rng, outs = [], [], [], [], []
+                # one output tensor for the batch's ranges, a view per request;
+                # the pieces go to the library as plain addresses
                 dt = torch.uint8 if store.w == 8 else torch.int16
+                out = torch.empty((sum(r.b - r.a for r in ranges), store.D), dtype=dt, device=dev)
+                base = out.data_ptr()
+                shapes, srcs, sizes, rng, dsts = [], [], [], [], []
+                row = 0
                 for r in ranges:
-                    r.result = torch.empty((r.b - r.a, store.D), dtype=dt, device=f"cuda:{codec.device}")
+                    n = r.b - r.a
+                    r.result = out[row:row + n]
                     for sh, la, lb, off in store.pieces(r.sid, r.a, r.b):
-                        streams.append(sh.buf)
-                        infos.append(sh.info)
+                        shapes.append(sh.shape)
+                        srcs.append(sh.ptr)
                         sizes.append(sh.size)
                         rng.append((la, lb))
-                        outs.append(r.result[off:off + (lb - la)])
-                _, ws = codec.decompress_ranges(streams, infos, sizes, rng, outs=outs,
-                                                stream=slot.stream)
-                slot.keep.append(ws)
+                        dsts.append((base + (row + off) * rb, (lb - la) * rb))
+                    row += n
+                if shapes:
+                    slot.keep.append(codec.decompress_ranges_into(shapes, srcs, sizes, rng, dsts,
+                                                                  stream=slot.stream))
             apps = [r for r in reqs if r.kind == "append"]
             if apps:
-                bufs, sizes, ws = codec.compress_batch([r.rows for r in apps], store.opts,
-                                                       stream=slot.stream)
+                # the batch's new shards share one buffer (256-byte aligned parts)
+                caps = [self._cap(r.rows.shape[0]) for r in apps]
+                offs, tot = [], 0
+                for c in caps:
+                    offs.append(tot)
+                    tot += (c + 255) & ~255
+                big = torch.empty(tot, dtype=torch.uint8, device=dev)
+                bufs, sizes, ws = codec.compress_batch([r.rows for r in apps], store.opts, stream=slot.stream,
+                                                       bufs=[big[o:o + c] for o, c in zip(offs, caps)])
                 slot.keep += [ws, sizes]
                 slot.new_shards = list(zip(apps, bufs, range(len(apps))))
                 slot.sizes = sizes
@@ -154,7 +183,7 @@ class Server:
             slot.event.record(slot.stream)
         self.batches += 1
 
-    def _finish(self, slot: _Slot, now: float) -> None:
+    def _finish(self, slot: _Slot, now: float, keep_results: bool = True) -> None:
         store = self.store
         if slot.new_shards:
             sz = slot.sizes.cpu().numpy()
@@ -173,11 +202,16 @@ class Server:
         for r in slot.reqs:
             r.t_done = now
             self.mem_used -= r.mem
+            if not keep_results and r.kind == "range":
+                r.result = None  # the client has taken its rows: their memory goes back to the pool
         slot.reqs, slot.new_shards, slot.keep, slot.event = [], [], [], None
 
-    def run(self, requests: list, realtime: bool = True) -> dict:
+    def run(self, requests: list, realtime: bool = True, keep_results: bool = True) -> dict:
         """Serve `requests` (sorted by arrival). With realtime=False every
-        request is taken as arrived at once (a closed-loop throughput run)."""
+        request is taken as arrived at once (a closed-loop throughput run).
+        keep_results=False drops each range request's rows once it has
+        completed (a client that consumes them), so that a long run does not
+        hold every result in device memory."""
         pending = collections.deque(requests)
         queue: collections.deque = collections.deque()
         t0 = time.perf_counter()
@@ -187,7 +221,7 @@ class Server:
                 queue.append(pending.popleft())
             for s in self.slots:
                 if s.event is not None and s.event.query():
-                    self._finish(s, time.perf_counter() - t0)
+                    self._finish(s, time.perf_counter() - t0, keep_results)
             free = [s for s in self.slots if s.event is None]
             if free and queue:
                 batch = []

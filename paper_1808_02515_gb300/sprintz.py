@@ -592,9 +592,16 @@ class Codec:
             shapes.append((info.rows, info.D, info.w, info.opts))
             srcs.append(s.data_ptr())
             dsts.append((y.data_ptr(), y.numel() * y.element_size()))
-        arr = self._items(shapes, srcs, list(sizes), dsts, [0] * len(streams), list(ranges))
-        ws = self.batch_plan_run(arr, 0, stream)
-        return res, ws
+        return res, self.decompress_ranges_into(shapes, srcs, sizes, ranges, dsts, stream)
+
+    def decompress_ranges_into(self, shapes, srcs, sizes, ranges, dsts, stream=None):
+        """Range requests given as plain values: each stream's (rows, D, w,
+        Opts), device address and byte size, its row range [a, b), and the
+        (device address, capacity in bytes) its rows go to. One batched
+        launch; returns the planned workspace (keep it until the launch has
+        completed)."""
+        arr = self._items(shapes, srcs, list(sizes), dsts, [0] * len(shapes), list(ranges))
+        return self.batch_plan_run(arr, 0, stream)
 
     def decompress_batch(self, streams, infos, sizes, stream=None, schedule=None, autotune=False, outs=None):
         """Decompress device streams (with their host-parsed infos and byte
