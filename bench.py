@@ -60,6 +60,7 @@ def parse(argv=None):
     ap.add_argument("--no-per-stream", action="store_true", help="batch: skip the per-stream launches")
     ap.add_argument("--no-delta", action="store_true", help="batch: skip the delta forecaster")
     ap.add_argument("--no-sensor", action="store_true", help="batch: skip the single-stream sensor series")
+    ap.add_argument("--no-graph", action="store_true", help="batch: skip the CUDA-graph replay of the step")
     ap.add_argument("--workload", default="batch",
                     choices=["batch", "sensor", "walk", "huffman", "serve", "fire_speed", "dsweep", "gsweep",
                              "quantize"])
@@ -616,8 +617,11 @@ def run_batch(args, rank, world, local):
         return dict(o=o, cc=cc, cd=cd, ws_c=ws_c, ws_d=ws_d, sizes=sizes, sz=sz, infos=infos, sched=sched,
                     C=sum(sz))
 
-    def timed(P, steps, evs=None):
-        """Mean compress and decompress ms per step over `steps` steps."""
+    step_ms = {}
+
+    def timed(P, steps, keep=False):
+        """Mean compress and decompress ms per step over `steps` steps (keep:
+        also their best and median into step_ms)."""
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
         for k in range(steps):
             ev[k][0].record(stream)
@@ -626,8 +630,12 @@ def run_batch(args, rank, world, local):
             P["cd"].batch_run(P["ws_d"])
             ev[k][2].record(stream)
         torch.cuda.synchronize()
-        return (statistics.mean(e[0].elapsed_time(e[1]) for e in ev),
-                statistics.mean(e[1].elapsed_time(e[2]) for e in ev))
+        enc = [e[0].elapsed_time(e[1]) for e in ev]
+        dec = [e[1].elapsed_time(e[2]) for e in ev]
+        if keep:
+            step_ms.update({"compress_best": min(enc), "compress_median": statistics.median(enc),
+                            "decompress_best": min(dec), "decompress_median": statistics.median(dec)})
+        return statistics.mean(enc), statistics.mean(dec)
 
     F = plans(1, "FIRE")
     with ClockSampler(local) as clk:
@@ -641,7 +649,7 @@ def run_batch(args, rank, world, local):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         h0 = time.monotonic()
         a.record(stream)
-        enc_ms, dec_ms = timed(F, args.steps)
+        enc_ms, dec_ms = timed(F, args.steps, keep=True)
         b.record(stream)
         torch.cuda.synchronize()
         clk.mark(h0, time.monotonic())
@@ -654,6 +662,41 @@ def run_batch(args, rank, world, local):
     if not wl.outputs_equal_inputs(torch):
         raise SystemExit("batched round trip mismatch after the timed steps")
     res = {"enc_ms": enc_ms, "dec_ms": dec_ms}
+
+    # the same step as one CUDA graph (both directions' memsets and kernels
+    # captured once), replayed `steps` times; single-rank runs only, so that a
+    # capture refused on one rank cannot leave the ranks' collectives apart
+    graph = None
+    if not args.no_graph and dist is None:
+        try:
+            side = torch.cuda.Stream(dev)
+            side.wait_stream(stream)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=side):
+                F["cc"].batch_run(F["ws_c"], stream=side)
+                F["cd"].batch_run(F["ws_d"], stream=side)
+            torch.cuda.synchronize()
+            g.replay()
+            torch.cuda.synchronize()
+            ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            cur = torch.cuda.current_stream(dev)
+            ga.record(cur)
+            for _ in range(args.steps):
+                g.replay()
+            gb.record(cur)
+            torch.cuda.synchronize()
+            F["cc"].check()
+            F["cd"].check()
+            if not wl.outputs_equal_inputs(torch):
+                raise SystemExit("batched round trip mismatch after the graph replays")
+            g_ms = ga.elapsed_time(gb) / args.steps
+            graph = {"ms_per_step": g_ms, "round_trip_gbs": total_gbs(U_total, g_ms),
+                     "graph_launches_per_step": 1, "steps": args.steps}
+            del g
+        except SystemExit:
+            raise
+        except Exception as exc:  # capture unsupported here: say so, keep the line
+            graph = {"error": f"{type(exc).__name__}: {exc}"[:200]}
 
     # per-stream launches of the same work (one context, one shared workspace)
     per_stream = None
@@ -747,7 +790,7 @@ def run_batch(args, rank, world, local):
                    "parallelism": f"{world} rank(s), each a contiguous byte-balanced range of the streams",
                    "schedules": F["sched"]},
         "compress_gbs": total_gbs(U_total, enc_max), "decompress_gbs": total_gbs(U_total, dec_max),
-        "compress_ms": enc_max, "decompress_ms": dec_max,
+        "compress_ms": enc_max, "decompress_ms": dec_max, "step_ms": step_ms,
         "roofline": {"bound": "hbm", "kernel": kern, "achieved": ach, "peak": peak, "peak_kind": peak_kind,
                      "unit": "GB/s", "frac": ach / peak, "frac_of_nominal_8tbs": ach / NOMINAL_HBM_GBS,
                      "traffic": traffic_bytes(kern),
@@ -766,6 +809,8 @@ def run_batch(args, rank, world, local):
         "gpu_launches": 4 * args.steps,
         "clocks": clk.summary(),
     }
+    if graph:
+        line["cuda_graph"] = graph
     if per_stream:
         line["per_stream_launches"] = per_stream
     if sensor:
