@@ -66,7 +66,8 @@ def parse(argv=None):
                              "quantize"])
     ap.add_argument("--streams", type=int, default=N_STREAMS, help="batch: number of streams")
     ap.add_argument("--huff-rows", type=int, default=1 << 28, help="huffman: rows of the accel series")
-    ap.add_argument("--e2e-lanes", type=int, default=4, help="end to end: CUDA streams taking slices in turn")
+    ap.add_argument("--e2e-lag", type=int, default=2,
+                    help="end to end: slices between a slice's samples going in and its packed bytes coming back")
     ap.add_argument("--e2e-slices", type=int, default=16, help="end to end: slices of the batch per step")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     return ap.parse_args(argv)
@@ -489,25 +490,27 @@ def run_e2e(wl, F, args, dev, local, dist, spz, torch, U_total):
     store / load round trip through the host), a batched decompress reading
     the packed streams, and one device-to-host copy of the decoded samples
     into the host buffer the inputs came from (the round trip is lossless,
-    so every step's input is again the workload).  Slices take CUDA streams
-    in turn, so one slice's copies overlap another's kernels and the two
-    copy directions overlap."""
+    so every step's input is again the workload).  The slices run as a
+    pipeline over four CUDA streams, one per copy direction, one for the
+    compressions (with their packs) and one for the decompressions, linked
+    by an event per slice and stage, so that both copy engines stay busy
+    while the kernels run between them: slice s's samples go in while slice
+    s - lag's packed bytes come back."""
     cr = wl.cudart
     in_sizes = [t.numel() for t in wl.in_bufs]
-    nl = max(1, args.e2e_lanes)
-    lanes = [torch.cuda.Stream(dev) for _ in range(nl)]
+    lag = max(1, args.e2e_lag)
+    s_h2d, s_d2h, s_enc, s_dec = [torch.cuda.Stream(dev) for _ in range(4)]
     sc = spz.Schedule(**{k: v for k, v in F["sched"]["compress"].items() if k != "tune_ms"})
     sd = spz.Schedule(**{k: v for k, v in F["sched"]["decompress"].items() if k != "tune_ms"})
     sz = F["sz"]
-    sl, packed = [], []
+    sl = []
     tot = [sum(sz[lo:hi]) for lo, hi in wl.slices]
     h_off, h_tot = _aligned_offsets(tot, 256)
     hc = PinnedBuffer(h_tot, cr)
     try:
         for s_i, (lo, hi) in enumerate(wl.slices):
-            ls = lanes[s_i % nl]
             cc, cd = spz.Codec(local), spz.Codec(local)
-            _, _, wsc = cc.compress_batch(wl.xs[lo:hi], F["o"], stream=ls, schedule=sc, bufs=wl.bufs[lo:hi],
+            _, _, wsc = cc.compress_batch(wl.xs[lo:hi], F["o"], stream=s_enc, schedule=sc, bufs=wl.bufs[lo:hi],
                                           sizes=F["sizes"][lo:hi])
             ptrs = torch.tensor([b.data_ptr() for b in wl.bufs[lo:hi]], dtype=torch.int64, device=dev)
             offs = torch.zeros(hi - lo + 1, dtype=torch.int64, device=dev)
@@ -516,44 +519,70 @@ def run_e2e(wl, F, args, dev, local, dist, spz, torch, U_total):
             # the same every step: the inputs are)
             o_host = np.concatenate([[0], np.cumsum(sz[lo:hi])]).astype(np.int64)
             views = [pk[int(o_host[k]):int(o_host[k + 1])] for k in range(hi - lo)]
-            cc.pack(ptrs, F["sizes"][lo:hi], pk, offs, stream=ls)  # the plan below runs once on them
-            _, wsd = cd.decompress_batch(views, F["infos"][lo:hi], sz[lo:hi], stream=ls, schedule=sd,
+            cc.pack(ptrs, F["sizes"][lo:hi], pk, offs, stream=s_enc)  # the plan below runs once on them
+            _, wsd = cd.decompress_batch(views, F["infos"][lo:hi], sz[lo:hi], stream=s_enc, schedule=sd,
                                          outs=wl.outs[lo:hi])
-            sl.append((ls, cc, cd, wsc, wsd, ptrs, offs, pk))
+            sl.append((cc, cd, wsc, wsd, ptrs, offs, pk))
         torch.cuda.synchronize()
         in_ptr = [t.data_ptr() for t in wl.in_bufs]
         out_ptr = [t.data_ptr() for t in wl.out_bufs]
         hin_ptr = [h.ctypes.data for h in wl.host]
         hc_ptr = hc.ptr.value
+        S = len(sl)
+        ev = {k: [torch.cuda.Event() for _ in range(S)] for k in ("in", "enc", "pkd", "pkh", "dec", "out")}
+
+        def stage_a(s):
+            """Samples in, compress and pack, packed bytes out."""
+            cc, _, wsc, _, ptrs, offs, pk = sl[s]
+            lo, hi = wl.slices[s]
+            cr.copy(in_ptr[s], hin_ptr[s], in_sizes[s], Cudart.H2D, s_h2d.cuda_stream)
+            ev["in"][s].record(s_h2d)
+            s_enc.wait_event(ev["in"][s])
+            s_enc.wait_event(ev["dec"][s])  # the previous step's decompress has read pk
+            cc.batch_run(wsc, stream=s_enc)
+            cc.pack(ptrs, F["sizes"][lo:hi], pk, offs, stream=s_enc)
+            ev["enc"][s].record(s_enc)
+            s_d2h.wait_event(ev["enc"][s])
+            cr.copy(hc_ptr + h_off[s], pk.data_ptr(), tot[s], Cudart.D2H, s_d2h.cuda_stream)
+            ev["pkd"][s].record(s_d2h)
+
+        def stage_b(s):
+            """Packed bytes back in, decompress, samples out."""
+            _, cd, _, wsd, _, _, pk = sl[s]
+            s_h2d.wait_event(ev["pkd"][s])
+            cr.copy(pk.data_ptr(), hc_ptr + h_off[s], tot[s], Cudart.H2D, s_h2d.cuda_stream)
+            ev["pkh"][s].record(s_h2d)
+            s_dec.wait_event(ev["pkh"][s])
+            s_dec.wait_event(ev["out"][s])  # the previous step's samples have left
+            cd.batch_run(wsd, stream=s_dec)
+            ev["dec"][s].record(s_dec)
+            s_d2h.wait_event(ev["dec"][s])
+            cr.copy(hin_ptr[s], out_ptr[s], in_sizes[s], Cudart.D2H, s_d2h.cuda_stream)
+            ev["out"][s].record(s_d2h)
 
         def step():
-            for s_i, (ls, cc, cd, wsc, wsd, ptrs, offs, pk) in enumerate(sl):
-                lo, hi = wl.slices[s_i]
-                sp = ls.cuda_stream
-                cr.copy(in_ptr[s_i], hin_ptr[s_i], in_sizes[s_i], Cudart.H2D, sp)
-                cc.batch_run(wsc, stream=ls)
-                cc.pack(ptrs, F["sizes"][lo:hi], pk, offs, stream=ls)
-                cr.copy(hc_ptr + h_off[s_i], pk.data_ptr(), tot[s_i], Cudart.D2H, sp)
-                cr.copy(pk.data_ptr(), hc_ptr + h_off[s_i], tot[s_i], Cudart.H2D, sp)
-                cd.batch_run(wsd, stream=ls)
-                cr.copy(hin_ptr[s_i], out_ptr[s_i], in_sizes[s_i], Cudart.D2H, sp)
+            for s in range(S + lag):
+                if s < S:
+                    stage_a(s)
+                if 0 <= s - lag < S:
+                    stage_b(s - lag)
 
         step()
         torch.cuda.synchronize()
         a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         n_e2e = 3
-        a2.record(lanes[0])
-        for ls in lanes[1:]:
-            ls.wait_event(a2)
+        a2.record(s_h2d)
+        for st in (s_d2h, s_enc, s_dec):
+            st.wait_event(a2)
         for _ in range(n_e2e):
             step()
-        for ls in lanes[1:]:
+        for st in (s_d2h, s_enc, s_dec):
             done = torch.cuda.Event()
-            done.record(ls)
-            lanes[0].wait_event(done)
-        b2.record(lanes[0])
+            done.record(st)
+            s_h2d.wait_event(done)
+        b2.record(s_h2d)
         torch.cuda.synchronize()
-        for _, cc, cd, *_ in sl:
+        for cc, cd, *_ in sl:
             cc.check()
             cd.check()
         if not all(torch.equal(torch.from_numpy(h).to(dev), t) for h, t in zip(wl.host, wl.in_bufs)):
@@ -563,12 +592,14 @@ def run_e2e(wl, F, args, dev, local, dist, spz, torch, U_total):
         return {"value": total_gbs(U_total, e2e_ms), "unit": "GB/s",
                 "h2d_bytes_per_step": sum(in_sizes) + C, "d2h_bytes_per_step": C + sum(in_sizes),
                 "ms_per_step": e2e_ms, "steps": n_e2e,
-                "pipelining": f"{len(sl)} slices on {nl} CUDA streams; pinned host buffers (cudaHostAlloc); "
+                "pipelining": f"{S} slices; one CUDA stream per copy direction, one for compress + pack, one "
+                              f"for decompress, an event per slice and stage; slice s's samples go in while "
+                              f"slice s - {lag}'s packed bytes come back; pinned host buffers (cudaHostAlloc); "
                               "per slice one copy of its samples each way and one of its packed compressed "
                               "streams each way (sprintz_pack); the decoded samples return into the host "
                               "buffer the inputs came from"}
     finally:
-        for _, cc, cd, *_ in sl:
+        for cc, cd, *_ in sl:
             cc.close()
             cd.close()
         hc.free()
