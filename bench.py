@@ -66,6 +66,8 @@ def parse(argv=None):
                              "quantize"])
     ap.add_argument("--streams", type=int, default=N_STREAMS, help="batch: number of streams")
     ap.add_argument("--huff-rows", type=int, default=1 << 28, help="huffman: rows of the accel series")
+    ap.add_argument("--e2e-lanes", type=int, default=4,
+                    help="end to end of the single-stream workloads: CUDA streams taking steps in turn")
     ap.add_argument("--e2e-lag", type=int, default=2,
                     help="end to end: slices between a slice's samples going in and its packed bytes coming back")
     ap.add_argument("--e2e-slices", type=int, default=16, help="end to end: slices of the batch per step")
